@@ -1,0 +1,305 @@
+"""Seeded synthetic brick-decomposed scenes: the inputs of the compositing path.
+
+This module only *produces* fragment tiles.  It contains none of the
+compositing arithmetic (no blending, sorting of fragments, accumulation or
+packing), so that both the FP64 oracle and the CUDA library can take their
+inputs from it without sharing any of the method's code.
+
+The scenes follow the data-parallel setting of Sec. 4.2 of the paper: the
+volume is split into a grid of disjoint bricks, one producer ("rank") per
+brick; each producer finds the tiles its brick projects to (a conservative
+screen-space rectangle refined by ray casting the box, as Listing 3 does) and
+emits one fragment tile per touched tile.  A fragment tile holds premultiplied
+RGBA and a per-pixel depth inside the brick's ray interval; pixels whose ray
+misses the brick are empty (RGBA 0, depth +inf).  The order key of a fragment
+is the distance from the eye to its brick's centre.
+
+Fragment tiles are stored row-major within the tile (pixel p = y*T + x) and
+the frame's tiles are numbered row-major (tile = ty * tilesX + tx).
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Camera:
+    kind: str                      # "ortho" or "persp"
+    W: int
+    H: int
+    eye: np.ndarray = None
+    forward: np.ndarray = None
+    right: np.ndarray = None
+    up: np.ndarray = None
+    vfov_deg: float = 60.0
+    ortho_lo: tuple = (0.0, 0.0)   # world (x, y) at pixel (0, 0) corner
+    ortho_hi: tuple = (1.0, 1.0)
+    ortho_z: float = 2.0           # eye plane, looking down -z
+
+    def rays(self, px, py):
+        """Ray origins/directions through pixel centres (px, py integer arrays)."""
+        px = np.asarray(px, dtype=np.float64) + 0.5
+        py = np.asarray(py, dtype=np.float64) + 0.5
+        if self.kind == "ortho":
+            x = self.ortho_lo[0] + (self.ortho_hi[0] - self.ortho_lo[0]) * px / self.W
+            y = self.ortho_lo[1] + (self.ortho_hi[1] - self.ortho_lo[1]) * py / self.H
+            o = np.stack([x, y, np.full_like(x, self.ortho_z)], axis=-1)
+            d = np.broadcast_to(np.array([0.0, 0.0, -1.0]), o.shape)
+            return o, d
+        th = np.tan(np.radians(self.vfov_deg) / 2)
+        aspect = self.W / self.H
+        u = (2.0 * px / self.W - 1.0) * th * aspect
+        v = (1.0 - 2.0 * py / self.H) * th
+        d = self.forward[None] + u[..., None] * self.right[None] + v[..., None] * self.up[None]
+        d = d / np.linalg.norm(d, axis=-1, keepdims=True)
+        o = np.broadcast_to(self.eye, d.shape)
+        return o, d
+
+    def project(self, pts):
+        """World points -> pixel coordinates (x, y); perspective assumes in front."""
+        pts = np.asarray(pts, dtype=np.float64)
+        if self.kind == "ortho":
+            x = (pts[:, 0] - self.ortho_lo[0]) / (self.ortho_hi[0] - self.ortho_lo[0]) * self.W
+            y = (pts[:, 1] - self.ortho_lo[1]) / (self.ortho_hi[1] - self.ortho_lo[1]) * self.H
+            return x, y, np.ones(len(pts), dtype=bool)
+        rel = pts - self.eye
+        zc = rel @ self.forward
+        th = np.tan(np.radians(self.vfov_deg) / 2)
+        aspect = self.W / self.H
+        u = (rel @ self.right) / np.maximum(zc, 1e-9) / (th * aspect)
+        v = (rel @ self.up) / np.maximum(zc, 1e-9) / th
+        x = (u + 1.0) * 0.5 * self.W
+        y = (1.0 - v) * 0.5 * self.H
+        return x, y, zc > 1e-6
+
+
+def look_at(eye, target, W, H, vfov_deg=60.0, world_up=(0.0, 1.0, 0.0)):
+    eye = np.asarray(eye, dtype=np.float64)
+    f = np.asarray(target, dtype=np.float64) - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(f, np.asarray(world_up, dtype=np.float64))
+    r /= np.linalg.norm(r)
+    u = np.cross(r, f)
+    return Camera("persp", W, H, eye=eye, forward=f, right=r, up=u, vfov_deg=vfov_deg)
+
+
+@dataclass
+class Scene:
+    """A set of fragment tiles for one frame (plus what is needed for more frames).
+
+    ``tile_ids``/``keys`` are in submission order; submission index = position.
+    ``rgba`` is premultiplied FP32 for frame 0 (shape (n, T*T, 4)); ``depth``
+    is FP32 (n, T*T).  ``base_rgb``/``alpha`` hold the unpremultiplied colour
+    and coverage so later frames can be drawn with colour jitter.
+    """
+    W: int
+    H: int
+    T: int
+    tile_ids: np.ndarray
+    keys: np.ndarray
+    rgba: np.ndarray
+    depth: np.ndarray
+    base_rgb: np.ndarray = None
+    alpha: np.ndarray = None
+    hit: np.ndarray = None
+    seed: int = 0
+    jitter_sigma: float = 0.0
+    info: dict = field(default_factory=dict)
+
+    @property
+    def n(self):
+        return len(self.tile_ids)
+
+    @property
+    def tiles_x(self):
+        return -(-self.W // self.T)
+
+    @property
+    def tiles_y(self):
+        return -(-self.H // self.T)
+
+    @property
+    def n_tiles(self):
+        return self.tiles_x * self.tiles_y
+
+    def in_frame_pixels(self):
+        """Per fragment: how many of its tile's pixels lie inside the frame."""
+        tx = self.tile_ids % self.tiles_x
+        ty = self.tile_ids // self.tiles_x
+        w = np.minimum(self.T, self.W - tx * self.T)
+        h = np.minimum(self.T, self.H - ty * self.T)
+        return (w * h).astype(np.int64)
+
+    def fragment_pixels(self) -> int:
+        return int(self.in_frame_pixels().sum())
+
+    def counts(self):
+        return np.bincount(self.tile_ids, minlength=self.n_tiles)
+
+    def frame_rgba(self, f: int) -> np.ndarray:
+        """Premultiplied FP32 RGBA of frame f (frame 0 is ``rgba``)."""
+        if f == 0 or self.jitter_sigma == 0.0:
+            return self.rgba
+        rng = np.random.default_rng([self.seed, 1000 + f])
+        j = rng.standard_normal(self.base_rgb.shape, dtype=np.float32) * np.float32(self.jitter_sigma)
+        return _premultiply(np.clip(self.base_rgb + j, 0.0, 1.0), self.alpha, self.hit)
+
+
+def _premultiply(rgb, alpha, hit):
+    out = np.empty(rgb.shape[:-1] + (4,), dtype=np.float32)
+    a = np.where(hit, alpha, 0.0).astype(np.float32)
+    out[..., :3] = rgb * a[..., None]
+    out[..., 3] = a
+    return out
+
+
+def brick_grid(grid, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    gx, gy, gz = grid
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    size = (hi - lo) / np.array(grid)
+    boxes = []
+    for k in range(gz):
+        for j in range(gy):
+            for i in range(gx):
+                bmin = lo + size * np.array([i, j, k])
+                boxes.append((bmin, bmin + size))
+    return boxes
+
+
+def _ray_box(o, d, bmin, bmax):
+    with np.errstate(divide="ignore", invalid="ignore"):
+        inv = 1.0 / d
+        t0 = (bmin - o) * inv
+        t1 = (bmax - o) * inv
+    t0 = np.nan_to_num(t0, nan=-np.inf)
+    t1 = np.nan_to_num(t1, nan=np.inf)
+    tmin = np.max(np.minimum(t0, t1), axis=-1)
+    tmax = np.min(np.maximum(t0, t1), axis=-1)
+    tin = np.maximum(tmin, 0.0)
+    return tin, tmax, tmax > tin
+
+
+def brick_scene(W, H, T, boxes, cam: Camera, seed=0, alpha="uniform", alpha_max=0.6,
+                jitter_sigma=0.0, max_per_tile=None, shuffle=True):
+    """Render every brick's fragment tiles (the producers of Sec. 4.2)."""
+    rng = np.random.default_rng(seed)
+    tiles_x, tiles_y = -(-W // T), -(-H // T)
+    tid_l, key_l, rgb_l, a_l, z_l, hit_l = [], [], [], [], [], []
+    ly, lx = np.meshgrid(np.arange(T), np.arange(T), indexing="ij")
+    lx = lx.reshape(-1)
+    ly = ly.reshape(-1)
+    for bmin, bmax in boxes:
+        corners = np.array([[x, y, z] for x in (bmin[0], bmax[0])
+                            for y in (bmin[1], bmax[1]) for z in (bmin[2], bmax[2])])
+        sx, sy, ok = cam.project(corners)
+        if not ok.all():
+            continue
+        x0 = int(np.floor(max(sx.min(), 0)) // T)
+        x1 = int(min(np.ceil(sx.max()), W) - 1) // T
+        y0 = int(np.floor(max(sy.min(), 0)) // T)
+        y1 = int(min(np.ceil(sy.max()), H) - 1) // T
+        if x1 < x0 or y1 < y0 or sx.max() <= 0 or sy.max() <= 0:
+            continue
+        centre = 0.5 * (bmin + bmax)
+        if cam.kind == "ortho":
+            key = float(cam.ortho_z - centre[2])
+        else:
+            key = float(np.linalg.norm(centre - cam.eye))
+        for ty in range(y0, y1 + 1):
+            for tx in range(x0, x1 + 1):
+                px = tx * T + lx
+                py = ty * T + ly
+                o, d = cam.rays(px, py)
+                tin, tout, hit = _ray_box(o, d, bmin, bmax)
+                hit &= (px < W) & (py < H)
+                if not hit.any():
+                    continue       # refined by ray casting the box (Listing 3)
+                tid_l.append(ty * tiles_x + tx)
+                key_l.append(key)
+                u = rng.random(len(px))
+                z = np.where(hit, tin + u * (tout - tin), np.inf).astype(np.float32)
+                if alpha == "beta":
+                    a = rng.beta(2.0, 5.0, len(px)).astype(np.float32)
+                else:
+                    a = (rng.random(len(px)) * alpha_max).astype(np.float32)
+                rgb = rng.random((len(px), 3)).astype(np.float32)
+                rgb_l.append(rgb)
+                a_l.append(a)
+                z_l.append(z)
+                hit_l.append(hit)
+    n = len(tid_l)
+    tile_ids = np.array(tid_l, dtype=np.int32)
+    keys = np.array(key_l, dtype=np.float32)
+    base_rgb = np.stack(rgb_l) if n else np.zeros((0, T * T, 3), np.float32)
+    alpha_a = np.stack(a_l) if n else np.zeros((0, T * T), np.float32)
+    depth = np.stack(z_l) if n else np.zeros((0, T * T), np.float32)
+    hit = np.stack(hit_l) if n else np.zeros((0, T * T), bool)
+    if max_per_tile is not None and n:
+        keep = np.ones(n, dtype=bool)
+        seen = {}
+        for i, t in enumerate(tile_ids):
+            seen[t] = seen.get(t, 0) + 1
+            keep[i] = seen[t] <= max_per_tile
+        tile_ids, keys = tile_ids[keep], keys[keep]
+        base_rgb, alpha_a, depth, hit = base_rgb[keep], alpha_a[keep], depth[keep], hit[keep]
+        n = len(tile_ids)
+    if shuffle and n:
+        perm = rng.permutation(n)           # arrival order is arbitrary (Sec. 3.1.1)
+        tile_ids, keys = tile_ids[perm], keys[perm]
+        base_rgb, alpha_a, depth, hit = base_rgb[perm], alpha_a[perm], depth[perm], hit[perm]
+    rgb0 = base_rgb
+    if jitter_sigma:
+        j = np.random.default_rng([seed, 1000]).standard_normal(base_rgb.shape, dtype=np.float32)
+        rgb0 = np.clip(base_rgb + j * np.float32(jitter_sigma), 0.0, 1.0)
+    rgba = _premultiply(rgb0, alpha_a, hit)
+    sc = Scene(W, H, T, tile_ids, keys, rgba, depth, base_rgb=base_rgb, alpha=alpha_a, hit=hit,
+               seed=seed, jitter_sigma=jitter_sigma)
+    c = sc.counts()
+    sc.info = {"fragments": n, "fragment_pixels": sc.fragment_pixels(),
+               "min_per_tile": int(c.min()) if len(c) else 0,
+               "max_per_tile": int(c.max()) if len(c) else 0,
+               "mean_per_tile": float(c.mean()) if len(c) else 0.0}
+    return sc
+
+
+# --- the workloads ------------------------------------------------------------
+def scene_single_frame_256(seed=0):
+    """256x256 frame, 64x64 tiles, 2x2x2 bricks of the unit cube, orthographic
+    camera looking down -z, alpha U(0, 0.6), zero background."""
+    cam = Camera("ortho", 256, 256)
+    return brick_scene(256, 256, 64, brick_grid((2, 2, 2)), cam, seed=seed,
+                       alpha="uniform", alpha_max=0.6)
+
+
+def orbit_camera(W, H, seed, radius=1.0, lo=(0, 0, 0), hi=(1, 1, 1), vfov=60.0):
+    rng = np.random.default_rng([seed, 7])
+    th = rng.uniform(0.0, 2.0 * np.pi)
+    el = rng.uniform(-0.35, 0.35)
+    c = 0.5 * (np.asarray(lo, float) + np.asarray(hi, float))
+    eye = c + radius * np.array([np.cos(th) * np.cos(el), np.sin(el), np.sin(th) * np.cos(el)])
+    return look_at(eye, c, W, H, vfov)
+
+
+def scene_data_parallel(W=2048, H=2048, T=64, grid=(4, 4, 4), seed=0, radius=1.0,
+                        jitter_sigma=0.02, extent=(1.0, 1.0, 1.0), max_per_tile=None):
+    """Perspective (60 deg) brick-grid frame with Beta(2,5) alpha and per-frame
+    colour jitter; the data-parallel frame of Sec. 4.2."""
+    hi = tuple(float(e) for e in extent)
+    cam = orbit_camera(W, H, seed, radius=radius, hi=hi)
+    return brick_scene(W, H, T, brick_grid(grid, hi=hi), cam, seed=seed, alpha="beta",
+                       jitter_sigma=jitter_sigma, max_per_tile=max_per_tile)
+
+
+def scene_2048(seed=0, jitter_sigma=0.02):
+    """2048x2048, 64x64 tiles, 4x4x4 bricks: the headline data-parallel frame."""
+    return scene_data_parallel(2048, 2048, 64, (4, 4, 4), seed=seed, jitter_sigma=jitter_sigma)
+
+
+def scene_4096x1024(seed=0):
+    """4096x1024, 64x64 tiles, 8x4x4 bricks of a 2x1x1 box (precision form)."""
+    return scene_data_parallel(4096, 1024, 64, (8, 4, 4), seed=seed, jitter_sigma=0.0,
+                               extent=(2.0, 1.0, 1.0), radius=1.2)

@@ -1,0 +1,71 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that the pins
+catch every one of them."""
+
+import numpy as np
+import pytest
+
+from oracle import dfb_oracle as o
+import tests.test_oracle_pins as pins
+
+
+def _wrong_sign(C, A, c, a):
+    t = 1.0 + A
+    return C + t[..., None] * c, A + t * a
+
+
+def _back_to_front_formula(C, A, c, a):
+    # treats the new fragment as being in front
+    return c + (1.0 - a)[..., None] * C, a + (1.0 - a) * A
+
+
+def _dropped_alpha_term(C, A, c, a):
+    t = 1.0 - A
+    return C + t[..., None] * c, A + a
+
+
+def _unsorted_accumulate(frames):
+    return sum(np.asarray(f, float) for f in frames) / max(len(frames) - 1, 1)
+
+
+def _population_variance(frames):
+    return np.var(np.stack(frames), axis=0)
+
+
+def _srgb_no_offset(x):
+    x = np.asarray(x, dtype=np.float64)
+    return np.where(x <= 0.0031308, 12.92 * x, 1.055 * np.power(np.maximum(x, 0.0), 1.0 / 2.4))
+
+
+MUTANTS = [
+    ("over_front_to_back", _wrong_sign, [pins.test_equal_layers_closed_form]),
+    ("over_front_to_back", _back_to_front_formula, [pins.test_golden_hand_derived_pixels]),
+    ("over_front_to_back", _dropped_alpha_term, [pins.test_equal_layers_closed_form]),
+    ("accumulate", _unsorted_accumulate, [pins.test_accumulate_fsum_and_constant]),
+    ("variance", _population_variance, [pins.test_variance_library_and_closed_forms]),
+    ("srgb_encode", _srgb_no_offset, [pins.test_srgb_pack_fixed_points]),
+]
+
+
+@pytest.mark.parametrize("name,bad,tests", MUTANTS, ids=[m[1].__name__ for m in MUTANTS])
+def test_pins_catch_mutant(monkeypatch, name, bad, tests):
+    monkeypatch.setattr(o, name, bad)
+    for t in tests:
+        with pytest.raises(AssertionError):
+            if t is pins.test_equal_layers_closed_form:
+                t(0.3, 5)
+            else:
+                t()
+
+
+def test_pins_catch_wrong_depth_tiebreak(monkeypatch):
+    real = np.lexsort
+
+    def lexsort_reverse_submit(keys, axis=-1):
+        keys = list(keys)
+        if len(keys) == 3:
+            keys[0] = -np.asarray(keys[0])       # submit index descending
+        return real(tuple(keys), axis=axis)
+
+    monkeypatch.setattr(o.np, "lexsort", lexsort_reverse_submit)
+    with pytest.raises(AssertionError):
+        pins.test_golden_hand_derived_pixels()
