@@ -1,0 +1,450 @@
+#!/usr/bin/env python
+"""Throughput of the DFB compositing path on one GB300.
+
+Workload: a 2048x2048 frame with 64x64 tiles (1024 tiles), 64 bricks in a
+4x4x4 grid seen by a 60-degree perspective camera on a seeded orbit, 2-14
+fragment tiles per image tile from the projected brick bounds, premultiplied
+FP32 RGBA with alpha Beta(2,5), per-pixel FP32 depth, and 16 frames of
+progressive accumulation (colour jitter N(0, 0.02)) with variance and sRGB
+RGBA8 output.  One step = the 16-frame accumulation: per frame, bulk setTile
+of every fragment tile, then end-of-frame (bucketing + per-pixel sort and
+blend + accumulate + variance + pack).  All 16 frames' fragment tiles are
+resident in HBM before timing; each frame reads ~458 MB of fragments, which is
+larger than the 129 MB L2, so no flush is needed between steps.
+
+Metric: composited fragment-pixels per second (whole job), plus the composite
+kernel's algorithmic HBM GB/s against the measured copy peak.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica of the workload on its
+own GPU (the path has no cross-GPU exchange on one box); the step time is the
+max over ranks and the value counts all ranks' fragment-pixels.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "composited fragment-pixels/s & HBM GB/s (% of peak) at 2048², FP32 vs FP16"
+UNIT = "fragment-pixels/s"
+N_FRAMES = 16
+WORKLOAD = ("2048x2048 frame, 64x64 tiles, 64 bricks (4x4x4 grid), 60-degree perspective orbit "
+            "camera (seed 0), 2-14 fragments per tile, FP32 premultiplied RGBA + FP32 depth, "
+            "per-pixel depth sort + front-to-back over, 16-frame progressive accumulation with "
+            "variance and sRGB RGBA8")
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline (the FP64 oracle, as it stands) -- worker must be importable
+# ----------------------------------------------------------------------------
+def _oracle_tile(args):
+    from oracle import dfb_oracle as o
+    rgba, depth, keys, sidx = args
+    return o.composite_tile(rgba.astype(np.float64), depth, keys, sidx, o.BLEND_DEPTH).shape[0]
+
+
+def cpu_oracle_rate(sc, rgba, n_tiles_sample, pool, min_seconds=0.0, max_passes=64):
+    """Fragment-pixels/s of the oracle compositing a seeded sample of tiles,
+    repeated until at least ``min_seconds`` of work has been timed."""
+    from oracle import dfb_oracle as o
+    lists, _, _ = o.bucket(sc.tile_ids, sc.keys, sc.n_tiles)
+    rng = np.random.default_rng(123)
+    tiles = rng.choice(sc.n_tiles, size=min(n_tiles_sample, sc.n_tiles), replace=False)
+    work, fpx = [], 0
+    for t in tiles:
+        idx = np.array(lists[t], dtype=np.int64)
+        work.append((rgba[idx], sc.depth[idx], sc.keys[idx], idx))
+        fpx += len(idx) * sc.T * sc.T
+    passes, dt = 0, 0.0
+    while passes < max_passes and (passes == 0 or dt < min_seconds):
+        t0 = time.perf_counter()
+        list(pool.map(_oracle_tile, work, chunksize=4))
+        dt += time.perf_counter() - t0
+        passes += 1
+    return fpx * passes / dt, fpx * passes, dt, len(tiles) * passes
+
+
+def make_pool():
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0))
+    return mp.get_context("spawn").Pool(cores), cores
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = max((num(r[2]) or 0) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [v for v in sm if v >= 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max((num(r[3]) or 0) for r in rows)}
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+def build_workload(seed, device):
+    import torch
+    from harness import scenes
+    sc = scenes.scene_2048(seed=seed, jitter_sigma=0.02)
+    base = torch.from_numpy(sc.base_rgb).to(device)
+    alpha = torch.from_numpy(np.where(sc.hit, sc.alpha, 0.0).astype(np.float32)).to(device)
+    depth = torch.from_numpy(sc.depth).to(device)
+    frames = []
+    g = torch.Generator(device=device)
+    for f in range(N_FRAMES):
+        g.manual_seed(seed * 1000 + f)
+        j = torch.randn(base.shape, generator=g, device=device, dtype=torch.float32) * 0.02
+        rgb = (base + j).clamp_(0.0, 1.0) * alpha[..., None]
+        frames.append(torch.cat([rgb, alpha[..., None]], dim=-1).contiguous())
+        del j, rgb
+    del base
+    return sc, frames, depth, alpha
+
+
+class Runner:
+    """One framebuffer handle + pointer tables for the 16 resident frames."""
+
+    def __init__(self, sc, frames, depth, dtype, where="device"):
+        from paper_2305_07083_gb300 import dfb as D
+        self.D = D
+        self.sc = sc
+        self.frames = frames
+        self.depth = depth
+        self.dtype = dtype
+        self.where = D.DFB_PTR_DEVICE if where == "device" else D.DFB_PTR_HOST
+        self.h = D.dfb_create_ex(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH, dtype, D.DFB_FLAGS_DEFAULT,
+                                 0, max(4096, sc.n))
+        P = sc.T * sc.T
+        rb = P * 4 * D.ELEMENT_BYTES[dtype]
+        self.tile_ids = np.ascontiguousarray(sc.tile_ids, np.int32)
+        self.keys = np.ascontiguousarray(sc.keys, np.float32)
+        self.rptr = [D.pool_pointers(fr, sc.n, rb) for fr in frames]
+        self.dptr = D.pool_pointers(depth, sc.n, P * 4)
+
+    def step(self, stream):
+        D = self.D
+        for f in range(N_FRAMES):
+            D.dfb_begin_frame(self.h, f > 0)
+            D.dfb_submit_tiles(self.h, self.tile_ids, self.keys, self.rptr[f], self.dptr, None,
+                               self.where)
+            D.dfb_end_frame(self.h, stream)
+
+    def close(self):
+        self.D.dfb_destroy(self.h)
+
+
+def timed(run, steps, warmup, stream, dist=None, sampler=None, read_back=None):
+    import torch
+    for _ in range(warmup):
+        run.step(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if sampler:
+        sampler.start()
+    run.D.dfb_read_timing(run.h, reset=True)
+    run.D.dfb_set_timing(run.h, True)
+    l0 = run.D.dfb_get_stats(run.h)["kernel_launches"]
+    e0.record(stream)
+    for _ in range(steps):
+        run.step(stream)
+        if read_back is not None:
+            read_back()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    run.D.dfb_set_timing(run.h, False)
+    tm = run.D.dfb_read_timing(run.h, reset=True)
+    clocks = sampler.stop() if sampler else None
+    if dist is not None:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = run.D.dfb_get_stats(run.h)["kernel_launches"] - l0
+    return ms, tm, clocks, launches
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("paper_2305_07083_gb300/csrc/dfb_kernels.cu", "paper_2305_07083_gb300/csrc/dfb_internal.h"):
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the oracle on host cores
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from harness import scenes
+    pool, cores = make_pool()
+    sc = scenes.scene_2048(seed=0, jitter_sigma=0.02)
+    sample_tiles = sc.n_tiles
+    for _ in range(args.warmup):
+        cpu_oracle_rate(sc, sc.rgba, 32, pool)
+    rates, fpx_tot, t_tot = [], 0, 0.0
+    for _ in range(args.steps):
+        r, fpx, dt, nt = cpu_oracle_rate(sc, sc.rgba, sample_tiles, pool)
+        rates.append(r)
+        fpx_tot += fpx
+        t_tot += dt
+    pool.close()
+    value = fpx_tot / t_tot
+    sample = ("all %d tiles of frame 0 of the workload per step (BLEND_DEPTH per-pixel sort + "
+              "over in FP64; accumulation, variance and pack not included), tiles spread over "
+              "%d spawned processes" % (sample_tiles, cores))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# main arm
+# ----------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-f16", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pool = cores = None
+    if rank == 0 and not args.no_cpu_baseline:
+        pool, cores = make_pool()          # spawned before the first CUDA call
+
+    import torch
+    from paper_2305_07083_gb300 import build, dfb as D
+    build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = tdist
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    sc, frames, depth, alpha = build_workload(0, dev)
+    fpx_frame = sc.fragment_pixels()
+    hbm_peak, peak_kind = peaks()
+
+    # ---- FP32 headline ----
+    run = Runner(sc, frames, depth, D.DFB_F32)
+    sampler = ClockSampler(local) if rank == 0 else None
+    ms, tm, clocks, launches = timed(run, args.steps, args.warmup, stream, dist, sampler)
+    st = D.dfb_get_stats(run.h)
+    ms_t = torch.tensor([ms], device=dev)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    ms_step = ms / args.steps
+    value = world * fpx_frame * N_FRAMES * args.steps / (ms / 1e3)
+    frames_timed = args.steps * N_FRAMES
+    comp_ms = tm["composite_ms"] / max(tm["launches"], 1)
+    # algorithmic bytes of one composite launch: fragment bytes + framebuffer
+    # state bytes, averaged over the 16 frames of a step (frame 1 writes the
+    # accumulation without reading it)
+    frag_b = st["fragment_bytes"]
+    px = st["frame_pixels"]
+    state_first = (16 + 32 + 4) * px
+    state_rest = (16 + 64 + 4) * px
+    state_avg = (state_first + (N_FRAMES - 1) * state_rest) / N_FRAMES
+    algo_bytes = frag_b + state_avg
+    achieved = algo_bytes / (comp_ms / 1e3) / 1e9
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frame": "2048x2048", "tile": 64, "bricks": 64,
+                   "frames_per_step": N_FRAMES, "fragments_per_frame": sc.n,
+                   "fragment_pixels_per_frame": fpx_frame,
+                   "mean_fragments_per_tile": round(sc.n / sc.n_tiles, 3),
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "inputs larger than L2 (%.0f MB of fragments per frame)" % (frag_b / 1e6)},
+        "gb_per_s_step": (algo_bytes * frames_timed) / (ms / 1e3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "peak_kind": peak_kind + " (copy, burst)",
+                     "traffic": ncu_traffic("composite_f32_2048.md"),
+                     "kernel": "k_composite<BLEND_DEPTH,F32>",
+                     "algorithmic_bytes_per_launch": algo_bytes,
+                     "avg_launch_ms": comp_ms, "bucket_ms_per_frame": tm["bucket_ms"] / max(tm["launches"], 1)},
+        "clocks": clocks,
+    }
+    D.dfb_sync(run.h)
+
+    # ---- e2e: host buffers through the C ABI, copies inside the timed region ----
+    if not args.no_e2e and rank == 0:
+        host_frames = [fr.cpu().pin_memory() for fr in frames]
+        host_depth = depth.cpu().pin_memory()
+        hrun = Runner(sc, host_frames, host_depth, D.DFB_F32, where="host")
+        out8 = torch.empty((sc.H, sc.W), dtype=torch.int32).pin_memory()
+
+        def read_back():
+            D.dfb_read_rgba8(hrun.h, out8)
+        e_steps = max(1, min(args.steps, 3))
+        ems, _, _, _ = timed(hrun, e_steps, 1, stream, None, None, read_back)
+        h2d = N_FRAMES * (host_frames[0].numel() * 4 + host_depth.numel() * 4)
+        out["e2e"] = {"value": fpx_frame * N_FRAMES * e_steps / (ems / 1e3), "unit": UNIT,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": sc.W * sc.H * 4,
+                      "steps": e_steps, "ms_per_step": ems / e_steps,
+                      "path": "dfb_submit_tiles(host pinned pointers) + dfb_end_frame + dfb_read_rgba8"}
+        hrun.close()
+        del host_frames, host_depth
+
+    # ---- FP16 storage (same frames converted by dfb_convert_tiles) ----
+    if not args.no_f16:
+        f16 = []
+        for fr in frames:
+            dst = torch.empty(fr.numel(), dtype=torch.float16, device=dev)
+            D.dfb_convert_tiles(fr, dst, None, sc.n, sc.T * sc.T, D.DFB_F16, stream)
+            f16.append(dst)
+        r16 = Runner(sc, f16, depth, D.DFB_F16)
+        ms16, tm16, _, _ = timed(r16, args.steps, args.warmup, stream, dist, None)
+        st16 = D.dfb_get_stats(r16.h)
+        c16 = tm16["composite_ms"] / max(tm16["launches"], 1)
+        ab16 = st16["fragment_bytes"] + state_avg
+        a16 = ab16 / (c16 / 1e3) / 1e9
+        out["variants"] = {"f16": {
+            "value": world * fpx_frame * N_FRAMES * args.steps / (ms16 / 1e3),
+            "ms_per_step": ms16 / args.steps, "speedup_vs_f32": ms / ms16,
+            "roofline": {"achieved": a16, "frac": a16 / hbm_peak, "avg_launch_ms": c16,
+                         "algorithmic_bytes_per_launch": ab16}}}
+        r16.close()
+        del f16
+    run.close()
+    out["gpu_launches"] = launches
+    out["gpu_launches_note"] = ("kernels launched by libdfb.so inside the timed FP32 region "
+                                "(per frame: 4 bucketing + 1 composite), counted by the library")
+
+    # ---- CPU baseline: the oracle on the host cores, bounded sample ----
+    if pool is not None:
+        rate, fpx, dt, nt = cpu_oracle_rate(sc, frames[0].cpu().numpy(), sc.n_tiles, pool,
+                                            min_seconds=10.0)
+        pool.close()
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": "frame 0 composited %d times (%d tile tasks, %d fragment-"
+                                         "pixels, %.1f s): BLEND_DEPTH FP64 per-pixel sort + over; "
+                                         "accumulation, variance and pack not included; %d spawned "
+                                         "processes" % (nt // sc.n_tiles, nt, fpx, dt, cores)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -303,3 +303,67 @@ def scene_4096x1024(seed=0):
     """4096x1024, 64x64 tiles, 8x4x4 bricks of a 2x1x1 box (precision form)."""
     return scene_data_parallel(4096, 1024, 64, (8, 4, 4), seed=seed, jitter_sigma=0.0,
                                extent=(2.0, 1.0, 1.0), radius=1.2)
+
+
+def random_scene(W, H, T, counts, seed=0, depth_levels=None, special_depths=False,
+                 alpha_max=1.0, equal_keys=False):
+    """Fragments with arbitrary (not brick-ordered) depths and keys.
+
+    ``counts`` gives the number of fragments of every tile (len = tiles).
+    ``depth_levels`` draws depths from a few integer levels (many ties);
+    ``special_depths`` sprinkles NaN, -0.0, +0.0 and +inf depths.
+    """
+    rng = np.random.default_rng(seed)
+    tiles_x, tiles_y = -(-W // T), -(-H // T)
+    counts = np.asarray(counts, dtype=np.int64)
+    assert len(counts) == tiles_x * tiles_y
+    tile_ids = np.repeat(np.arange(len(counts), dtype=np.int32), counts)
+    rng.shuffle(tile_ids)
+    n, P = len(tile_ids), T * T
+    if equal_keys:
+        keys = rng.integers(0, 3, n).astype(np.float32)
+    else:
+        keys = rng.uniform(0.0, 10.0, n).astype(np.float32)
+    a = (rng.random((n, P)) * alpha_max).astype(np.float32)
+    rgba = np.empty((n, P, 4), np.float32)
+    rgba[..., :3] = rng.random((n, P, 3)).astype(np.float32) * a[..., None]
+    rgba[..., 3] = a
+    if depth_levels:
+        depth = rng.integers(0, depth_levels, (n, P)).astype(np.float32)
+    else:
+        depth = rng.uniform(0.0, 10.0, (n, P)).astype(np.float32)
+    if special_depths and n:
+        u = rng.random((n, P))
+        depth[u < 0.05] = np.nan
+        depth[(u >= 0.05) & (u < 0.10)] = -0.0
+        depth[(u >= 0.10) & (u < 0.15)] = 0.0
+        depth[(u >= 0.15) & (u < 0.20)] = np.inf
+    sc = Scene(W, H, T, tile_ids, keys, rgba, depth, seed=seed)
+    sc.info = {"fragments": n}
+    return sc
+
+
+def store_rgba(rgba_f32, dtype):
+    """Storage form of FP32 fragment tiles, made with library casts.
+
+    dtype 0 FP32 (copy), 1 FP16 (numpy, round to nearest even), 2 BF16 (torch
+    CPU cast, bits as uint16), 3 FP8 e4m3 (one FP32 scale per tile =
+    amax/448, 1 for an all-zero tile; torch CPU cast of x/scale clamped to
+    +-448).  Returns (stored, scales or None).
+    """
+    x = np.ascontiguousarray(rgba_f32, dtype=np.float32)
+    if dtype == 0:
+        return x.copy(), None
+    if dtype == 1:
+        return x.astype(np.float16), None
+    import torch
+    t = torch.from_numpy(x)
+    if dtype == 2:
+        return t.to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16), None
+    n = x.shape[0]
+    amax = np.abs(x.reshape(n, -1)).max(axis=1) if n else np.zeros(0, np.float32)
+    scales = np.where(amax > 0, amax / np.float32(448.0), np.float32(1.0)).astype(np.float32)
+    q = (x / scales.reshape((-1,) + (1,) * (x.ndim - 1))).astype(np.float32)
+    q = np.clip(q, -448.0, 448.0)
+    codes = torch.from_numpy(q).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+    return codes, scales

@@ -1,0 +1,266 @@
+/*
+ * dfb.h - C ABI of a single-GPU Distributed FrameBuffer compositing library.
+ *
+ * The operations follow Usher et al., "Scalable Ray Tracing Using the
+ * Distributed FrameBuffer" (EuroVis 2019):
+ *   - a frame is bracketed by begin/end and fed tile by tile with setTile
+ *     (Sec. 3.1, "Tile Processing Pipeline");
+ *   - a tile carries RGBA colour and depth for TxT pixels (Listing 1, Tile);
+ *   - per tile, a dependency tree of generations tells the owner how many
+ *     inputs to wait for (Sec. 3.1.1, Listing 3: a generation-0 background
+ *     tile declares the number of generation-1 children);
+ *   - the AlphaBlend tile operation sorts every pixel's fragments by depth and
+ *     blends them (Sec. 4.2, Listing 4); with a rank-order tree the tiles are
+ *     blended in list order instead (Sec. 4.2);
+ *   - progressive refinement keeps accumulation and variance tiles
+ *     (Listing 1, TileOperation; Sec. 4.1.1 uses the variance to steer work);
+ *   - the finished tile is converted to the RGBA8 or RGBAF32 display format
+ *     (Sec. 3.1).
+ * The paper's ranks become fragment producers in one process; its per-tile
+ * owners become work items of CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: DFB_OK (0) or a negative DFB_ERR_* code.  No C++
+ *     exception crosses this interface.  dfb_error_string() names a code.
+ *   - Pixels: a fragment tile is T*T pixels, row-major inside the tile
+ *     (pixel p = y*T + x).  Frames are row-major images W*H.  Tiles are
+ *     numbered row-major: tile = ty * ceil(W/T) + tx.  Pixels of a submitted
+ *     tile that fall outside the frame (ragged right/bottom tiles) are ignored.
+ *   - Colour is premultiplied RGBA.  Depth is FP32 in every storage mode;
+ *     NaN depth is read as +inf and -0.0 as +0.0.  An empty fragment pixel is
+ *     RGBA 0 with depth +inf.
+ *   - Ownership: the caller owns every pointer it passes.  A device pointer
+ *     given to a submit call is borrowed until the work of the dfb_end_frame
+ *     call that consumes it has finished on its stream.  A host pointer is
+ *     copied before the submit call returns.  The handle owns the resident
+ *     framebuffers (colour, accumulation, variance, RGBA8).
+ *   - Threads: a handle must not be used by two threads at once.
+ */
+#ifndef DFB_H
+#define DFB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DFB_API __attribute__((visibility("default")))
+#else
+#define DFB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dfb_ctx* dfb_handle;
+
+/* Tile operation (compositing mode). */
+enum dfb_mode {
+  DFB_BLEND_DEPTH = 0,   /* per-pixel sort by (depth, key, submit index), then
+                            front-to-back "over" (Sec. 4.2, Listing 4)        */
+  DFB_BLEND_ORDERED = 1, /* "over" in (key, submit index) order for every
+                            pixel: the rank-order list tree of Sec. 4.2       */
+  DFB_ZCOMPOSITE = 2     /* nearest (depth, key, submit index) fragment wins,
+                            RGBA copied unchanged (depth compositing, Sec. 2.1)*/
+};
+
+/* Storage type of the submitted fragment RGBA (depth is always FP32). */
+enum dfb_dtype {
+  DFB_F32 = 0,     /* 4 x float32 per pixel, 16-byte aligned tiles          */
+  DFB_F16 = 1,     /* 4 x IEEE binary16 per pixel, 8-byte aligned           */
+  DFB_BF16 = 2,    /* 4 x bfloat16 per pixel, 8-byte aligned                */
+  DFB_FP8E4M3 = 3  /* 4 x e4m3 codes per pixel, 4-byte aligned; value =
+                      decode(code) * the fragment's FP32 scale               */
+};
+
+enum dfb_status {
+  DFB_OK = 0,
+  DFB_ERR_INVALID_ARG = -1, /* bad size, null or misaligned pointer, NaN key  */
+  DFB_ERR_TILE_RANGE = -2,  /* tile id outside [0, tiles)                      */
+  DFB_ERR_STATE = -3,       /* call not allowed in the handle's current state  */
+  DFB_ERR_INCOMPLETE = -4,  /* a tile's dependency tree is not complete         */
+  DFB_ERR_OOM = -5,         /* device or pinned allocation failed               */
+  DFB_ERR_TIMEOUT = -6,     /* a device-side wait gave up                        */
+  DFB_ERR_CUDA = -7         /* a CUDA call failed (including: no device)         */
+};
+
+/* Configuration flags. */
+#define DFB_FLAG_ACCUMULATE 1u  /* keep accumulation + variance buffers        */
+#define DFB_FLAG_WRITE_COLOR 2u /* write the float RGBA frame (RGBAF32 format)  */
+#define DFB_FLAG_PACK_RGBA8 4u  /* write the sRGB RGBA8 frame                   */
+#define DFB_FLAG_DEFER_ALLOC 8u /* allocate device memory at the first
+                                   dfb_end_frame instead of at creation         */
+#define DFB_FLAGS_DEFAULT (DFB_FLAG_ACCUMULATE | DFB_FLAG_WRITE_COLOR | DFB_FLAG_PACK_RGBA8)
+
+/* Where the pointers of a bulk submit live. */
+#define DFB_PTR_AUTO 0   /* ask the CUDA runtime for each pointer */
+#define DFB_PTR_DEVICE 1 /* all device (or managed) memory         */
+#define DFB_PTR_HOST 2   /* all host memory (pageable or pinned)   */
+
+typedef struct dfb_config {
+  int width;         /* frame width in pixels, >= 1                          */
+  int height;        /* frame height in pixels, >= 1                         */
+  int tile_size;     /* T: a power of two in [4, 256]                        */
+  int mode;          /* enum dfb_mode                                        */
+  int dtype;         /* enum dfb_dtype                                       */
+  unsigned flags;    /* DFB_FLAG_*                                           */
+  int kahan_after;   /* accumulated frames after which the running sum is
+                        Kahan-compensated; <= 0 selects 256                  */
+  int max_fragments; /* initial record capacity hint; <= 0 selects 4096      */
+} dfb_config;
+
+/* One submitted tile (the paper's Tile of Listing 1, data + tree fields). */
+typedef struct dfb_tile_desc {
+  int tile_id;        /* destination tile                                    */
+  float order_key;    /* e.g. distance from the eye to the brick centre      */
+  const void* rgba;   /* T*T*4 values of the handle's dtype                  */
+  const float* depth; /* T*T FP32 depths                                     */
+  float scale;        /* FP8 dequantisation scale (> 0, finite); else ignored */
+  int generation;     /* >= 1; rendered data tiles are generation 1          */
+  int children;       /* tiles this one adds to generation+1 (>= 0)          */
+} dfb_tile_desc;
+
+typedef struct dfb_frame_stats {
+  int64_t fragments;         /* tiles composited by the last frame            */
+  int64_t fragment_pixels;   /* sum over fragments of in-frame pixels          */
+  int64_t frame_pixels;      /* W * H                                          */
+  int64_t fragment_bytes;    /* algorithmic bytes of fragment data read        */
+  int64_t state_bytes;       /* algorithmic bytes of framebuffer state moved   */
+  int32_t accumulated;       /* frames in the accumulation (1 after a reset)   */
+  int32_t tiles;             /* tiles in the frame                             */
+  int64_t kernel_launches;   /* kernels this handle has launched in total      */
+} dfb_frame_stats;
+
+/* Create a framebuffer with DFB_FLAGS_DEFAULT and FP32 storage.
+   Errors: INVALID_ARG (sizes, mode, tile size), OOM, CUDA (no device). */
+DFB_API int dfb_create(int width, int height, int tile_size, int mode, dfb_handle* out);
+
+/* Create a framebuffer from a full configuration.  Same errors. */
+DFB_API int dfb_create_ex(const dfb_config* cfg, dfb_handle* out);
+
+/* Release the handle and its device memory (synchronises its last frame).
+   A null handle is accepted and ignored. */
+DFB_API int dfb_destroy(dfb_handle h);
+
+/* Background colour (unpremultiplied RGB and coverage A): the generation-0
+   background tile of Sec. 4.2, blended behind every pixel in the blend modes
+   and shown by empty tiles in DFB_ZCOMPOSITE.  Default (0,0,0,0). */
+DFB_API int dfb_set_background(dfb_handle h, float r, float g, float b, float a);
+
+/* Begin a frame (Sec. 3.1).  accumulate = 0 restarts the progressive
+   accumulation with this frame; non-zero adds this frame to it.
+   Errors: STATE if a frame is already open. */
+DFB_API int dfb_begin_frame(dfb_handle h, int accumulate);
+
+/* Declare the generation-0 tile of a tile's dependency tree with n_children
+   generation-1 inputs (Sec. 3.1.1, Listing 3).  Tiles with no declaration
+   composite whatever arrives.  Errors: STATE, TILE_RANGE, INVALID_ARG (n<0),
+   STATE if the tile already has a declaration this frame. */
+DFB_API int dfb_set_tile_children(dfb_handle h, int tile_id, int n_children);
+
+/* setTile for one rendered generation-1 tile (Sec. 3.1).  rgba/depth may be
+   host or device pointers.  Errors: STATE (no open frame), TILE_RANGE,
+   INVALID_ARG (NaN key, null/misaligned pointer, or an FP8 handle, whose
+   tiles need a scale: use dfb_submit_tile_ex), OOM, CUDA. */
+DFB_API int dfb_submit_tile(dfb_handle h, int tile_id, float order_key, const void* rgba,
+                    const float* depth);
+
+/* setTile with the tree fields and the FP8 scale.  Same errors. */
+DFB_API int dfb_submit_tile_ex(dfb_handle h, const dfb_tile_desc* tile);
+
+/* Bulk setTile of n generation-1 tiles (index i is submitted before i+1).
+   Arrays are host arrays of length n; scales may be NULL unless the dtype is
+   FP8.  `where` is a DFB_PTR_* hint.  The whole call is validated first and
+   nothing is submitted if any entry is invalid; the error of the first bad
+   entry is returned. */
+DFB_API int dfb_submit_tiles(dfb_handle h, int n, const int* tile_ids, const float* order_keys,
+                     const void* const* rgba, const float* const* depth,
+                     const float* scales, int where);
+
+/* Bulk setTile with the tree fields and scales: tiles[0..n) in order, with the
+   same all-or-nothing validation and `where` hint as dfb_submit_tiles. */
+DFB_API int dfb_submit_tiles_ex(dfb_handle h, int n, const dfb_tile_desc* tiles, int where);
+
+/* End the frame: check every declared dependency tree (INCOMPLETE if a
+   generation received more or fewer tiles than its parents declared; the
+   frame then stays open so the missing tiles can still be submitted), then
+   enqueue the compositing, accumulation, variance and pack kernels on
+   `stream` (a cudaStream_t; NULL = the legacy default stream) and return
+   without waiting.  Errors: STATE, INCOMPLETE, OOM, CUDA. */
+DFB_API int dfb_end_frame(dfb_handle h, void* stream);
+
+/* Composite the open frames of several handles with one persistent launch on
+   `stream`: the batched form of dfb_end_frame.  Every handle is validated
+   first; on any error nothing is launched and the first error is returned.
+   Handles must be distinct. */
+DFB_API int dfb_end_frames(const dfb_handle* hs, int n, void* stream);
+
+/* Wait for the last frame's work.  Errors: CUDA, TIMEOUT (a device queue
+   gave up; the frame's outputs are then undefined). */
+DFB_API int dfb_sync(dfb_handle h);
+
+/* Copy the finished frame as W*H*4 floats (RGBAF32 display format).  `out`
+   may be host memory (the call waits) or device memory (the copy is ordered
+   after the last frame on its stream).  Errors: STATE if no frame has been
+   composited or the colour buffer is disabled, CUDA. */
+DFB_API int dfb_read_color(dfb_handle h, float* out);
+
+/* Copy the normalised accumulation (sum of frames / frame count), W*H*4
+   floats.  Errors: STATE if accumulation is disabled or empty, CUDA. */
+DFB_API int dfb_read_accum(dfb_handle h, float* out);
+
+/* Copy the per-pixel sample variance (W*H*4 floats, ddof = 1, 0 after one
+   frame) and/or the per-tile variance (tiles floats: mean over in-frame
+   pixels of the RGB variances).  Either pointer may be NULL. */
+DFB_API int dfb_read_variance(dfb_handle h, float* per_pixel, float* per_tile);
+
+/* Copy the sRGB RGBA8 frame, W*H uint32 with bytes R,G,B,A in memory order. */
+DFB_API int dfb_read_rgba8(dfb_handle h, uint32_t* out);
+
+/* Statistics of the last composited frame. */
+DFB_API int dfb_get_stats(dfb_handle h, dfb_frame_stats* out);
+
+/* Tile grid of the handle. */
+DFB_API int dfb_get_tiles(dfb_handle h, int* tiles_x, int* tiles_y);
+
+/* Checkpoint of the progressive state: running sum, Kahan compensation and
+   M2 (each W*H*4 floats, host or device) and the frame count.  Load restores
+   it so accumulation resumes bit-identically. */
+DFB_API int dfb_save_accum(dfb_handle h, float* sum, float* comp, float* m2, int* frames);
+DFB_API int dfb_load_accum(dfb_handle h, const float* sum, const float* comp, const float* m2,
+                   int frames);
+
+/* Producer-side conversion of FP32 fragment tiles (device pointers) to a
+   storage dtype, on `stream`.  n_tiles tiles of tile_pixels pixels each.
+   DFB_F16/DFB_BF16: round to nearest even.  DFB_FP8E4M3: per tile,
+   scale = amax/448 (1 if the tile is all zero), code = e4m3(x / scale) with
+   round-to-nearest-even and saturation; scales (device, n_tiles floats)
+   receives the scales.  Errors: INVALID_ARG, CUDA. */
+DFB_API int dfb_convert_tiles(const float* src, void* dst, float* scales, int n_tiles,
+                      int tile_pixels, int dtype, void* stream);
+
+/* Per-stage device timing (tracing).  While enabled, every dfb_end_frame /
+   dfb_end_frames call records CUDA events around its bucketing kernels and its
+   composite kernel on the launch stream.  dfb_read_timing waits for the
+   recorded events, adds them up since the last reset and, if reset != 0,
+   starts a new sum.  For dfb_end_frames the batch is timed on its first
+   handle.  Errors: INVALID_ARG, CUDA. */
+typedef struct dfb_timing {
+  int32_t launches;     /* end-of-frame launches timed                        */
+  float bucket_ms;      /* total time of the bucketing kernels (K1)           */
+  float composite_ms;   /* total time of the composite kernel (K2/K3 + K4)    */
+} dfb_timing;
+DFB_API int dfb_set_timing(dfb_handle h, int enable);
+DFB_API int dfb_read_timing(dfb_handle h, dfb_timing* out, int reset);
+
+/* Human-readable name of a status code (static storage). */
+DFB_API const char* dfb_error_string(int status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+DFB_API int dfb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFB_H */

@@ -21,7 +21,8 @@ to the code; the list of readings is:
 * The background (the generation-0 tile of Sec. 4.2 / Listing 3) is blended
   behind every fragment as ``rgb*a`` with coverage ``a``.
 * Z-compositing (Sec. 2.1, "depth compositing") outputs the RGBA of the
-  nearest fragment unchanged; a tile with no fragment shows the background.
+  nearest fragment unchanged; a pixel no fragment covers (nearest depth +inf,
+  or no fragment at all) shows the premultiplied background.
 * The accumulation buffer of Listing 1 holds the running sum of frames; the
   displayed value is that sum divided by the frame count.  The variance
   buffer holds the per-pixel, per-channel sample variance (ddof = 1, 0 for a
@@ -196,7 +197,8 @@ def composite_tile(rgba, depth, keys, sidx, mode: int, bg=(0.0, 0.0, 0.0, 0.0)):
     and blend front to back (Sec. 4.2: "sorts the pixels by depth and blends
     them"), then the background.  BLEND_ORDERED: blend in (key, submit index)
     order for every pixel (Sec. 4.2, tree built as a list).  ZCOMPOSITE: the
-    RGBA of the per-pixel minimum of (depth, key, submit index).
+    RGBA of the per-pixel minimum of (depth, key, submit index), or the
+    premultiplied background where that depth is +inf.
     """
     rgba = np.asarray(rgba, dtype=np.float64)
     n = rgba.shape[0]
@@ -205,11 +207,8 @@ def composite_tile(rgba, depth, keys, sidx, mode: int, bg=(0.0, 0.0, 0.0, 0.0)):
     bg_c = bg[:3] * bg[3]
     out = np.zeros((P, 4), dtype=np.float64)
     if n == 0:
-        if mode == ZCOMPOSITE:
-            out[:] = bg
-        else:
-            out[:, :3] = bg_c
-            out[:, 3] = bg[3]
+        out[:, :3] = bg_c
+        out[:, 3] = bg[3]
         return out
     keys = np.array([canonical_key(k) for k in keys], dtype=np.float64)
     sidx = np.asarray(sidx, dtype=np.int64)
@@ -224,7 +223,11 @@ def composite_tile(rgba, depth, keys, sidx, mode: int, bg=(0.0, 0.0, 0.0, 0.0)):
         order = np.lexsort((S, K, z), axis=0)
     if mode == ZCOMPOSITE:
         win = order[0]
-        return rgba[win, pix].copy()
+        res = rgba[win, pix].copy()
+        empty = np.isinf(z[win, pix])
+        res[empty, :3] = bg_c
+        res[empty, 3] = bg[3]
+        return res
     C = np.zeros((P, 3), dtype=np.float64)
     A = np.zeros(P, dtype=np.float64)
     for j in range(n):

@@ -1,0 +1,1108 @@
+// Host side of the DFB C ABI (include/dfb.h): validation, per-tile dependency
+// trees, resident framebuffers, record upload and kernel launches.
+//
+// The paper's DFB runs setTile on every rank and routes tiles to their owners
+// through an MPI messaging layer (Sec. 3, 3.2).  Here every tile is owned by
+// this process: setTile appends a 32-byte record to the frame's list, and at
+// end-of-frame the list is uploaded once and bucketed by tile on the GPU.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "dfb_internal.h"
+
+namespace dfb {
+cudaError_t upload_srgb_table(const float* host256);
+}
+
+using dfb::FragRec;
+using dfb::FrameArgs;
+
+namespace {
+
+constexpr int kVersion = 10000;  // 1.0.0
+
+struct GenCount {
+  int received = 0;
+  int children = 0;
+};
+
+struct Arena {
+  // Device memory that receives tiles submitted from host pointers.  Chunks
+  // are never moved, so earlier pointers of a frame stay valid when it grows.
+  std::vector<char*> chunks;
+  std::vector<size_t> sizes;
+  size_t cur = 0;   // chunk in use
+  size_t used = 0;  // bytes used in chunk `cur`
+  void reset() { cur = 0; used = 0; }
+  char* take(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    while (cur < chunks.size()) {
+      if (used + bytes <= sizes[cur]) {
+        char* p = chunks[cur] + used;
+        used += bytes;
+        return p;
+      }
+      ++cur;
+      used = 0;
+    }
+    size_t sz = bytes > (size_t(256) << 20) ? bytes : (size_t(256) << 20);
+    char* p = nullptr;
+    if (cudaMalloc(&p, sz) != cudaSuccess) return nullptr;
+    chunks.push_back(p);
+    sizes.push_back(sz);
+    cur = chunks.size() - 1;
+    used = bytes;
+    return p;
+  }
+  void release() {
+    for (char* p : chunks) cudaFree(p);
+    chunks.clear();
+    sizes.clear();
+    reset();
+  }
+};
+
+int elt_bytes(int dtype) {
+  switch (dtype) {
+    case DFB_F32: return 4;
+    case DFB_F16: case DFB_BF16: return 2;
+    default: return 1;
+  }
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+std::mutex g_table_mu;
+unsigned long long g_table_devices = 0;  // bit d: table uploaded on device d
+
+}  // namespace
+
+struct dfb_ctx {
+  dfb_config cfg{};
+  int tilesX = 0, tilesY = 0, nTiles = 0, logT = 0, chunks = 0, tilePixels = 0;
+  size_t rgbaBytes = 0, depthBytes = 0;
+  int device = 0;
+  bool allocated = false;
+
+  // frame state
+  bool inFrame = false;
+  bool haveFrame = false;  // a frame has been composited
+  int accumN = 0;          // frames in the accumulation after the last frame
+  int pendingN = 0;        // frames in the accumulation after the open frame
+  float bg[4] = {0, 0, 0, 0};
+  std::vector<FragRec> recs;
+  std::vector<int> declared;             // gen-0 children per tile, -1 = none
+  std::vector<int> recvGen1, childGen1;  // generation-1 arrivals per tile
+  std::vector<std::vector<GenCount>> deeper;  // generations >= 2, per tile (lazy)
+  std::vector<int> touchedDeeper;
+  bool hostCopies = false;
+  int64_t launches = 0;  // kernels launched by this handle
+  dfb_frame_stats stats{};
+  dfb_frame_stats pendingStats{};
+
+  // device buffers
+  float4 *color = nullptr, *accum = nullptr, *comp = nullptr, *m2 = nullptr;
+  uint32_t* rgba8 = nullptr;
+  float *tileVar = nullptr, *varPartial = nullptr;
+  unsigned* tileDone = nullptr;
+  int *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
+  FragRec* dRecs = nullptr;
+  uint32_t *tmp = nullptr, *sorted = nullptr;
+  size_t recCap = 0;
+  float4* readTmp = nullptr;  // normalise / variance output for host reads
+  FragRec* hRecs[2] = {nullptr, nullptr};  // pinned staging (double buffered)
+  size_t hRecCap[2] = {0, 0};
+  cudaEvent_t hRecDone[2] = {nullptr, nullptr};
+  int hRecBuf = 0;
+  Arena arenas[2];           // alternate per frame so copies overlap compositing
+  cudaEvent_t arenaFree[2] = {nullptr, nullptr};  // last frame that read arena k done
+  bool arenaUsed[2] = {false, false};
+  int arenaIdx = 0;
+  cudaStream_t copyStream = nullptr;
+  cudaEvent_t copyDone = nullptr;
+  cudaEvent_t frameDone = nullptr;
+  cudaStream_t lastStream = nullptr;
+  bool lastStreamSet = false;
+
+  // tracing: ring of (bucket start, composite start, end) events
+  bool timing = false;
+  std::vector<cudaEvent_t> tev;  // 3 per slot
+  size_t tHead = 0, tCount = 0;
+  dfb_timing tSum{};
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DFB_OK;
+  if (e == cudaErrorMemoryAllocation) return DFB_ERR_OOM;
+  return DFB_ERR_CUDA;
+}
+
+int ensure_table(int dev) {
+  std::lock_guard<std::mutex> lk(g_table_mu);
+  if (dev < 64 && (g_table_devices >> dev) & 1ull) return DFB_OK;
+  float thr[256];
+  for (int c = 1; c <= 255; ++c) {
+    // linear value where code c begins: the inverse sRGB curve at (c-0.5)/255
+    const double v = (c - 0.5) / 255.0;
+    const double lin = v <= 0.04045 ? v / 12.92 : pow((v + 0.055) / 1.055, 2.4);
+    thr[c - 1] = (float)lin;
+  }
+  thr[255] = INFINITY;
+  const int st = cuda_status(dfb::upload_srgb_table(thr));
+  if (st == DFB_OK && dev < 64) g_table_devices |= (1ull << dev);
+  return st;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
+}
+
+int grow_records(dfb_ctx* h, size_t need) {
+  if (need <= h->recCap) return DFB_OK;
+  size_t cap = h->recCap ? h->recCap : 4096;
+  while (cap < need) cap *= 2;
+  // The previous frame may still read the old arrays.
+  if (h->lastStreamSet) cudaEventSynchronize(h->frameDone);
+  cudaFree(h->dRecs);
+  cudaFree(h->tmp);
+  cudaFree(h->sorted);
+  h->dRecs = nullptr;
+  h->tmp = h->sorted = nullptr;
+  h->recCap = 0;
+  cudaError_t e = dalloc(&h->dRecs, cap);
+  if (e == cudaSuccess) e = dalloc(&h->tmp, cap);
+  if (e == cudaSuccess) e = dalloc(&h->sorted, cap);
+  if (e != cudaSuccess) return cuda_status(e);
+  h->recCap = cap;
+  return DFB_OK;
+}
+
+int grow_staging(dfb_ctx* h, int buf, size_t need) {
+  if (need <= h->hRecCap[buf]) return DFB_OK;
+  size_t cap = h->hRecCap[buf] ? h->hRecCap[buf] : 4096;
+  while (cap < need) cap *= 2;
+  if (h->hRecs[buf]) cudaFreeHost(h->hRecs[buf]);
+  h->hRecs[buf] = nullptr;
+  h->hRecCap[buf] = 0;
+  cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&h->hRecs[buf]), sizeof(FragRec) * cap);
+  if (e != cudaSuccess) return DFB_ERR_OOM;
+  h->hRecCap[buf] = cap;
+  return DFB_OK;
+}
+
+void free_device(dfb_ctx* h) {
+  // Frees everything and leaves the pointers null, so a second call is a no-op.
+  auto fr = [](auto*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+  };
+  fr(h->color); fr(h->accum); fr(h->comp); fr(h->m2); fr(h->rgba8);
+  fr(h->tileVar); fr(h->varPartial); fr(h->tileDone);
+  fr(h->counts); fr(h->offsets); fr(h->cursor);
+  fr(h->dRecs); fr(h->tmp); fr(h->sorted); fr(h->readTmp);
+  h->recCap = 0;
+  for (int b = 0; b < 2; ++b) {
+    if (h->hRecs[b]) cudaFreeHost(h->hRecs[b]);
+    h->hRecs[b] = nullptr;
+    h->hRecCap[b] = 0;
+    if (h->hRecDone[b]) cudaEventDestroy(h->hRecDone[b]);
+    h->hRecDone[b] = nullptr;
+  }
+  for (int k = 0; k < 2; ++k) {
+    h->arenas[k].release();
+    if (h->arenaFree[k]) cudaEventDestroy(h->arenaFree[k]);
+    h->arenaFree[k] = nullptr;
+    h->arenaUsed[k] = false;
+  }
+  for (auto& e : h->tev)
+    if (e) cudaEventDestroy(e);
+  h->tev.clear();
+  h->tHead = h->tCount = 0;
+  if (h->copyStream) cudaStreamDestroy(h->copyStream);
+  if (h->copyDone) cudaEventDestroy(h->copyDone);
+  if (h->frameDone) cudaEventDestroy(h->frameDone);
+  h->copyStream = nullptr;
+  h->copyDone = h->frameDone = nullptr;
+  h->allocated = false;
+}
+
+int allocate(dfb_ctx* h) {
+  if (h->allocated) return DFB_OK;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return DFB_ERR_CUDA;
+  h->device = dev;
+  int st = ensure_table(dev);
+  if (st != DFB_OK) return st;
+  const size_t px = (size_t)h->cfg.width * h->cfg.height;
+  const unsigned f = h->cfg.flags;
+  if (f & DFB_FLAG_WRITE_COLOR) e = dalloc(&h->color, px);
+  if (e == cudaSuccess && (f & DFB_FLAG_ACCUMULATE)) {
+    e = dalloc(&h->accum, px);
+    if (e == cudaSuccess) e = dalloc(&h->comp, px);
+    if (e == cudaSuccess) e = dalloc(&h->m2, px);
+  }
+  if (e == cudaSuccess && (f & DFB_FLAG_PACK_RGBA8)) e = dalloc(&h->rgba8, px);
+  if (e == cudaSuccess) e = dalloc(&h->tileVar, h->nTiles);
+  if (e == cudaSuccess) e = dalloc(&h->varPartial, (size_t)h->nTiles * h->chunks);
+  if (e == cudaSuccess) e = dalloc(&h->tileDone, h->nTiles);
+  if (e == cudaSuccess) e = cudaMemset(h->tileDone, 0, sizeof(unsigned) * h->nTiles);
+  if (e == cudaSuccess) e = cudaMemset(h->tileVar, 0, sizeof(float) * h->nTiles);
+  if (e == cudaSuccess) e = dalloc(&h->counts, h->nTiles);
+  if (e == cudaSuccess) e = dalloc(&h->offsets, h->nTiles);
+  if (e == cudaSuccess) e = dalloc(&h->cursor, h->nTiles);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->copyStream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->copyDone, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->frameDone, cudaEventDisableTiming);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+    e = cudaEventCreateWithFlags(&h->hRecDone[b], cudaEventDisableTiming);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+    e = cudaEventCreateWithFlags(&h->arenaFree[b], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    free_device(h);
+    return cuda_status(e);
+  }
+  h->allocated = true;
+  size_t cap = h->cfg.max_fragments > 0 ? (size_t)h->cfg.max_fragments : 4096;
+  st = grow_records(h, cap);
+  if (st == DFB_OK) st = grow_staging(h, 0, cap);
+  if (st == DFB_OK) st = grow_staging(h, 1, cap);
+  return st;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int validate_tile(const dfb_ctx* h, const dfb_tile_desc* t) {
+  if (!t) return DFB_ERR_INVALID_ARG;
+  if (t->tile_id < 0 || t->tile_id >= h->nTiles) return DFB_ERR_TILE_RANGE;
+  if (isnan(t->order_key)) return DFB_ERR_INVALID_ARG;
+  if (!t->rgba || !t->depth) return DFB_ERR_INVALID_ARG;
+  const uintptr_t ra = (uintptr_t)t->rgba, da = (uintptr_t)t->depth;
+  const uintptr_t need = (uintptr_t)(4 * elt_bytes(h->cfg.dtype));
+  if ((ra % need) || (da % 4)) return DFB_ERR_INVALID_ARG;
+  if (t->generation < 1 || t->children < 0) return DFB_ERR_INVALID_ARG;
+  if (h->cfg.dtype == DFB_FP8E4M3 && !(t->scale > 0.0f && isfinite(t->scale)))
+    return DFB_ERR_INVALID_ARG;
+  return DFB_OK;
+}
+
+int64_t in_frame_pixels(const dfb_ctx* h, int tile) {
+  const int tx = tile % h->tilesX, ty = tile / h->tilesX;
+  const int64_t w = h->cfg.width - (int64_t)tx * h->cfg.tile_size;
+  const int64_t hh = h->cfg.height - (int64_t)ty * h->cfg.tile_size;
+  const int64_t T = h->cfg.tile_size;
+  return (w < T ? w : T) * (hh < T ? hh : T);
+}
+
+void note_tree(dfb_ctx* h, int tile, int gen, int children) {
+  if (gen == 1) {
+    h->recvGen1[tile] += 1;
+    h->childGen1[tile] += children;
+    return;
+  }
+  if (h->deeper.empty()) h->deeper.resize(h->nTiles);
+  auto& v = h->deeper[tile];
+  if (v.empty()) h->touchedDeeper.push_back(tile);
+  if ((int)v.size() < gen - 1) v.resize(gen - 1);
+  v[gen - 2].received += 1;
+  v[gen - 2].children += children;
+}
+
+// Copy host data of one or more tiles into the arena; returns device pointers.
+int append_records(dfb_ctx* h, int n, const dfb_tile_desc* tiles, int where) {
+  // Decide where each pointer lives and copy host tiles into the arena.
+  std::vector<const void*> dr(n), dd(n);
+  bool anyHost = false;
+  for (int i = 0; i < n; ++i) {
+    bool devR, devD;
+    if (where == DFB_PTR_DEVICE) devR = devD = true;
+    else if (where == DFB_PTR_HOST) devR = devD = false;
+    else {
+      devR = is_device_ptr(tiles[i].rgba);
+      devD = is_device_ptr(tiles[i].depth);
+    }
+    dr[i] = devR ? tiles[i].rgba : nullptr;
+    dd[i] = devD ? (const void*)tiles[i].depth : nullptr;
+    anyHost |= !devR || !devD;
+  }
+  if (anyHost) {
+    int st = allocate(h);
+    if (st != DFB_OK) return st;
+    Arena& arena = h->arenas[h->arenaIdx];
+    if (!h->hostCopies && h->arenaUsed[h->arenaIdx])
+      cudaStreamWaitEvent(h->copyStream, h->arenaFree[h->arenaIdx], 0);
+    // copy runs of source-contiguous tiles with one call each
+    for (int pass = 0; pass < 2; ++pass) {
+      const size_t bytes = pass == 0 ? h->rgbaBytes : h->depthBytes;
+      int i = 0;
+      while (i < n) {
+        const void* src0 = pass == 0 ? tiles[i].rgba : (const void*)tiles[i].depth;
+        const void* have = pass == 0 ? dr[i] : dd[i];
+        if (have) { ++i; continue; }
+        int j = i + 1;
+        while (j < n) {
+          const void* sj = pass == 0 ? tiles[j].rgba : (const void*)tiles[j].depth;
+          const void* hj = pass == 0 ? dr[j] : dd[j];
+          if (hj || (const char*)sj != (const char*)src0 + (size_t)(j - i) * bytes) break;
+          ++j;
+        }
+        char* dst = arena.take(bytes * (size_t)(j - i));
+        if (!dst) return DFB_ERR_OOM;
+        cudaError_t e = cudaMemcpyAsync(dst, src0, bytes * (size_t)(j - i),
+                                        cudaMemcpyHostToDevice, h->copyStream);
+        if (e != cudaSuccess) return cuda_status(e);
+        for (int k = i; k < j; ++k) {
+          if (pass == 0) dr[k] = dst + (size_t)(k - i) * bytes;
+          else dd[k] = dst + (size_t)(k - i) * bytes;
+        }
+        i = j;
+      }
+    }
+    cudaError_t e = cudaEventRecord(h->copyDone, h->copyStream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(h->copyDone);  // sources reusable now
+    if (e != cudaSuccess) return cuda_status(e);
+    h->hostCopies = true;
+  }
+  for (int i = 0; i < n; ++i) {
+    const dfb_tile_desc& t = tiles[i];
+    FragRec r;
+    r.rgba = dr[i];
+    r.depth = (const float*)dd[i];
+    r.tile = (uint32_t)t.tile_id;
+    r.key = dfb::ordered_bits_host(t.order_key);
+    r.scale = h->cfg.dtype == DFB_FP8E4M3 ? t.scale : 1.0f;
+    r.frame = 0;
+    h->recs.push_back(r);
+    note_tree(h, t.tile_id, t.generation, t.children);
+    const int64_t fpx = in_frame_pixels(h, t.tile_id);
+    h->pendingStats.fragments += 1;
+    h->pendingStats.fragment_pixels += fpx;
+  }
+  return DFB_OK;
+}
+
+int check_trees(const dfb_ctx* h) {
+  for (int t = 0; t < h->nTiles; ++t) {
+    if (h->declared[t] < 0) continue;
+    int expected = h->declared[t];
+    if (h->recvGen1[t] != expected) return DFB_ERR_INCOMPLETE;
+    int next = h->childGen1[t];
+    const std::vector<GenCount>* deeper = h->deeper.empty() ? nullptr : &h->deeper[t];
+    int g = 2;
+    while (true) {
+      const int have = (deeper && (int)deeper->size() >= g - 1) ? (*deeper)[g - 2].received : 0;
+      if (next == 0) {
+        // nothing more expected: no tile may sit in a deeper generation
+        if (deeper)
+          for (size_t k = g - 2; k < deeper->size(); ++k)
+            if ((*deeper)[k].received) return DFB_ERR_INCOMPLETE;
+        break;
+      }
+      if (have != next) return DFB_ERR_INCOMPLETE;
+      next = (*deeper)[g - 2].children;
+      ++g;
+    }
+  }
+  return DFB_OK;
+}
+
+void fill_frame_args(const dfb_ctx* h, FrameArgs& a, int tileBase, const int* counts,
+                     const int* offsets, const FragRec* recs, const uint32_t* sorted) {
+  a.W = h->cfg.width;
+  a.H = h->cfg.height;
+  a.T = h->cfg.tile_size;
+  a.logT = h->logT;
+  a.tilesX = h->tilesX;
+  a.nTiles = h->nTiles;
+  a.chunks = h->chunks;
+  a.tileBase = tileBase;
+  a.mode = h->cfg.mode;
+  a.dtype = h->cfg.dtype;
+  a.flags = h->cfg.flags & (DFB_FLAG_ACCUMULATE | DFB_FLAG_WRITE_COLOR | DFB_FLAG_PACK_RGBA8);
+  const int n = h->pendingN;
+  a.frameN = n;
+  const int ka = h->cfg.kahan_after;
+  a.kahan = n > ka ? 1 : 0;
+  a.kahanFirst = n == ka + 1 ? 1 : 0;
+  a.invN = 1.0f / (float)n;
+  a.invNm1 = n > 1 ? 1.0f / (float)(n - 1) : 0.0f;
+  a.bgR = h->bg[0] * h->bg[3];
+  a.bgG = h->bg[1] * h->bg[3];
+  a.bgB = h->bg[2] * h->bg[3];
+  a.bgA = h->bg[3];
+  a.recs = recs;
+  a.sorted = sorted;
+  a.counts = counts;
+  a.offsets = offsets;
+  a.color = h->color;
+  a.accum = h->accum;
+  a.comp = h->comp;
+  a.m2 = h->m2;
+  a.rgba8 = h->rgba8;
+  a.tileVar = h->tileVar;
+  a.varPartial = h->varPartial;
+  a.tileDone = h->tileDone;
+}
+
+void finish_stats(dfb_ctx* h) {
+  dfb_frame_stats& s = h->pendingStats;
+  const int64_t px = (int64_t)h->cfg.width * h->cfg.height;
+  s.frame_pixels = px;
+  s.tiles = h->nTiles;
+  s.accumulated = h->pendingN;
+  const int eb = elt_bytes(h->cfg.dtype);
+  const int64_t rgbaPx = 4 * eb;
+  if (h->cfg.mode == DFB_BLEND_ORDERED) s.fragment_bytes = s.fragment_pixels * rgbaPx;
+  else if (h->cfg.mode == DFB_BLEND_DEPTH) s.fragment_bytes = s.fragment_pixels * (rgbaPx + 4);
+  else s.fragment_bytes = s.fragment_pixels * 4 + px * rgbaPx;  // depth + one winner
+  int64_t st = 0;
+  const unsigned f = h->cfg.flags;
+  if (f & DFB_FLAG_WRITE_COLOR) st += 16;
+  if (f & DFB_FLAG_ACCUMULATE) {
+    const int n = h->pendingN;
+    st += n == 1 ? 32 : 64;  // sum and M2: write only on a reset, else read + write
+    if (n > h->cfg.kahan_after) st += (n == h->cfg.kahan_after + 1) ? 16 : 32;
+  }
+  if (f & DFB_FLAG_PACK_RGBA8) st += 4;
+  s.state_bytes = st * px;
+  s.kernel_launches = h->launches;
+}
+
+// Upload the open frame's records of handle h into staging slot, return pinned ptr.
+int stage_records(dfb_ctx* h, FragRec** out) {
+  const int buf = h->hRecBuf;
+  h->hRecBuf ^= 1;
+  cudaEventSynchronize(h->hRecDone[buf]);  // its previous upload has finished
+  int st = grow_staging(h, buf, h->recs.size());
+  if (st != DFB_OK) return st;
+  if (!h->recs.empty()) memcpy(h->hRecs[buf], h->recs.data(), sizeof(FragRec) * h->recs.size());
+  *out = h->hRecs[buf];
+  return buf;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char* dfb_error_string(int s) {
+  switch (s) {
+    case DFB_OK: return "ok";
+    case DFB_ERR_INVALID_ARG: return "invalid argument";
+    case DFB_ERR_TILE_RANGE: return "tile id out of range";
+    case DFB_ERR_STATE: return "call not allowed in the current state";
+    case DFB_ERR_INCOMPLETE: return "tile dependency tree incomplete";
+    case DFB_ERR_OOM: return "out of memory";
+    case DFB_ERR_TIMEOUT: return "device wait timed out";
+    case DFB_ERR_CUDA: return "CUDA error";
+    default: return "unknown status";
+  }
+}
+
+int dfb_version(void) { return kVersion; }
+
+int dfb_create_ex(const dfb_config* cfg, dfb_handle* out) {
+  if (!cfg || !out) return DFB_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int T = cfg->tile_size;
+  if (cfg->width < 1 || cfg->height < 1 || !is_pow2(T) || T < 4 || T > 256)
+    return DFB_ERR_INVALID_ARG;
+  if ((int64_t)cfg->width * cfg->height > (int64_t)1 << 31) return DFB_ERR_INVALID_ARG;
+  if (cfg->mode < DFB_BLEND_DEPTH || cfg->mode > DFB_ZCOMPOSITE) return DFB_ERR_INVALID_ARG;
+  if (cfg->dtype < DFB_F32 || cfg->dtype > DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;
+  if (cfg->flags & ~(DFB_FLAG_ACCUMULATE | DFB_FLAG_WRITE_COLOR | DFB_FLAG_PACK_RGBA8 |
+                     DFB_FLAG_DEFER_ALLOC))
+    return DFB_ERR_INVALID_ARG;
+  dfb_ctx* h = new (std::nothrow) dfb_ctx();
+  if (!h) return DFB_ERR_OOM;
+  h->cfg = *cfg;
+  if (h->cfg.kahan_after <= 0) h->cfg.kahan_after = 256;
+  h->tilesX = (cfg->width + T - 1) / T;
+  h->tilesY = (cfg->height + T - 1) / T;
+  h->nTiles = h->tilesX * h->tilesY;
+  h->logT = ilog2(T);
+  h->tilePixels = T * T;
+  h->chunks = (h->tilePixels + dfb::kItemPixels - 1) / dfb::kItemPixels;
+  h->rgbaBytes = (size_t)h->tilePixels * 4 * elt_bytes(cfg->dtype);
+  h->depthBytes = (size_t)h->tilePixels * 4;
+  h->declared.assign(h->nTiles, -1);
+  h->recvGen1.assign(h->nTiles, 0);
+  h->childGen1.assign(h->nTiles, 0);
+  if (!(cfg->flags & DFB_FLAG_DEFER_ALLOC)) {
+    const int st = allocate(h);
+    if (st != DFB_OK) {
+      free_device(h);
+      delete h;
+      return st;
+    }
+  }
+  *out = h;
+  return DFB_OK;
+}
+
+int dfb_create(int width, int height, int tile_size, int mode, dfb_handle* out) {
+  dfb_config c{};
+  c.width = width;
+  c.height = height;
+  c.tile_size = tile_size;
+  c.mode = mode;
+  c.dtype = DFB_F32;
+  c.flags = DFB_FLAGS_DEFAULT;
+  return dfb_create_ex(&c, out);
+}
+
+int dfb_destroy(dfb_handle h) {
+  if (!h) return DFB_OK;
+  if (h->allocated && h->lastStreamSet) cudaEventSynchronize(h->frameDone);
+  free_device(h);
+  delete h;
+  return DFB_OK;
+}
+
+int dfb_set_background(dfb_handle h, float r, float g, float b, float a) {
+  if (!h) return DFB_ERR_INVALID_ARG;
+  if (!isfinite(r) || !isfinite(g) || !isfinite(b) || !isfinite(a)) return DFB_ERR_INVALID_ARG;
+  h->bg[0] = r; h->bg[1] = g; h->bg[2] = b; h->bg[3] = a;
+  return DFB_OK;
+}
+
+int dfb_begin_frame(dfb_handle h, int accumulate) {
+  if (!h) return DFB_ERR_INVALID_ARG;
+  if (h->inFrame) return DFB_ERR_STATE;
+  h->inFrame = true;
+  h->recs.clear();
+  std::fill(h->declared.begin(), h->declared.end(), -1);
+  std::fill(h->recvGen1.begin(), h->recvGen1.end(), 0);
+  std::fill(h->childGen1.begin(), h->childGen1.end(), 0);
+  for (int t : h->touchedDeeper) h->deeper[t].clear();
+  h->touchedDeeper.clear();
+  h->hostCopies = false;
+  h->arenaIdx ^= 1;
+  h->arenas[h->arenaIdx].reset();
+  const bool acc = (h->cfg.flags & DFB_FLAG_ACCUMULATE) && accumulate && h->accumN > 0;
+  h->pendingN = acc ? h->accumN + 1 : 1;
+  h->pendingStats = dfb_frame_stats{};
+  return DFB_OK;
+}
+
+int dfb_set_tile_children(dfb_handle h, int tile_id, int n_children) {
+  if (!h) return DFB_ERR_INVALID_ARG;
+  if (!h->inFrame) return DFB_ERR_STATE;
+  if (tile_id < 0 || tile_id >= h->nTiles) return DFB_ERR_TILE_RANGE;
+  if (n_children < 0) return DFB_ERR_INVALID_ARG;
+  if (h->declared[tile_id] >= 0) return DFB_ERR_STATE;
+  h->declared[tile_id] = n_children;
+  return DFB_OK;
+}
+
+int dfb_submit_tile_ex(dfb_handle h, const dfb_tile_desc* tile) {
+  if (!h) return DFB_ERR_INVALID_ARG;
+  if (!h->inFrame) return DFB_ERR_STATE;
+  const int st = validate_tile(h, tile);
+  if (st != DFB_OK) return st;
+  return append_records(h, 1, tile, DFB_PTR_AUTO);
+}
+
+int dfb_submit_tile(dfb_handle h, int tile_id, float order_key, const void* rgba,
+                    const float* depth) {
+  dfb_tile_desc t;
+  t.tile_id = tile_id;
+  t.order_key = order_key;
+  t.rgba = rgba;
+  t.depth = depth;
+  t.scale = 1.0f;
+  t.generation = 1;
+  t.children = 0;
+  if (h && h->cfg.dtype == DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;  // needs a scale
+  return dfb_submit_tile_ex(h, &t);
+}
+
+int dfb_submit_tiles(dfb_handle h, int n, const int* tile_ids, const float* order_keys,
+                     const void* const* rgba, const float* const* depth, const float* scales,
+                     int where) {
+  if (!h || n < 0) return DFB_ERR_INVALID_ARG;
+  if (!h->inFrame) return DFB_ERR_STATE;
+  if (n == 0) return DFB_OK;
+  if (!tile_ids || !order_keys || !rgba || !depth) return DFB_ERR_INVALID_ARG;
+  if (where < DFB_PTR_AUTO || where > DFB_PTR_HOST) return DFB_ERR_INVALID_ARG;
+  const bool fp8 = h->cfg.dtype == DFB_FP8E4M3;
+  if (fp8 && !scales) return DFB_ERR_INVALID_ARG;
+  // validate everything first: nothing is submitted if an entry is bad
+  const uintptr_t ralign = (uintptr_t)(4 * elt_bytes(h->cfg.dtype));
+  for (int i = 0; i < n; ++i) {
+    if (tile_ids[i] < 0 || tile_ids[i] >= h->nTiles) return DFB_ERR_TILE_RANGE;
+    if (isnan(order_keys[i]) || !rgba[i] || !depth[i]) return DFB_ERR_INVALID_ARG;
+    if (((uintptr_t)rgba[i] % ralign) || ((uintptr_t)depth[i] % 4)) return DFB_ERR_INVALID_ARG;
+    if (fp8 && !(scales[i] > 0.0f && isfinite(scales[i]))) return DFB_ERR_INVALID_ARG;
+  }
+  if (where != DFB_PTR_DEVICE) {
+    std::vector<dfb_tile_desc> ts((size_t)n);
+    for (int i = 0; i < n; ++i)
+      ts[i] = dfb_tile_desc{tile_ids[i], order_keys[i], rgba[i], depth[i],
+                            scales ? scales[i] : 1.0f, 1, 0};
+    return append_records(h, n, ts.data(), where);
+  }
+  // device pointers: append directly
+  const size_t base = h->recs.size();
+  h->recs.resize(base + (size_t)n);
+  FragRec* out = h->recs.data() + base;
+  int64_t fpx = 0;
+  const int T = h->cfg.tile_size;
+  const int fullX = h->cfg.width / T, fullY = h->cfg.height / T;
+  for (int i = 0; i < n; ++i) {
+    const int t = tile_ids[i];
+    out[i].rgba = rgba[i];
+    out[i].depth = depth[i];
+    out[i].tile = (uint32_t)t;
+    out[i].key = dfb::ordered_bits_host(order_keys[i]);
+    out[i].scale = fp8 ? scales[i] : 1.0f;
+    out[i].frame = 0;
+    h->recvGen1[t] += 1;
+    const int tx = t % h->tilesX, ty = t / h->tilesX;
+    fpx += (tx < fullX && ty < fullY) ? (int64_t)T * T : in_frame_pixels(h, t);
+  }
+  h->pendingStats.fragments += n;
+  h->pendingStats.fragment_pixels += fpx;
+  return DFB_OK;
+}
+
+int dfb_submit_tiles_ex(dfb_handle h, int n, const dfb_tile_desc* tiles, int where) {
+  if (!h || n < 0) return DFB_ERR_INVALID_ARG;
+  if (!h->inFrame) return DFB_ERR_STATE;
+  if (n == 0) return DFB_OK;
+  if (!tiles || where < DFB_PTR_AUTO || where > DFB_PTR_HOST) return DFB_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const int st = validate_tile(h, &tiles[i]);
+    if (st != DFB_OK) return st;
+  }
+  return append_records(h, n, tiles, where);
+}
+
+int dfb_end_frame(dfb_handle h, void* stream) {
+  if (!h) return DFB_ERR_INVALID_ARG;
+  return dfb_end_frames(&h, 1, stream);
+}
+
+}  // extern "C"
+
+// ---- batched end-of-frame: shared by dfb_end_frame (n = 1) -----------------
+namespace {
+
+struct BatchRes {
+  // Resources of multi-frame launches (one per process and device).
+  int device = -1;
+  FragRec* dRecs = nullptr;
+  uint32_t *tmp = nullptr, *sorted = nullptr;
+  size_t recCap = 0;
+  int *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
+  size_t tileCap = 0;
+  FrameArgs* dFrames = nullptr;
+  int* dItemBase = nullptr;
+  size_t frameCap = 0;
+  unsigned* queue = nullptr;
+  FragRec* hRecs = nullptr;
+  size_t hRecCap = 0;
+  FrameArgs* hFrames = nullptr;
+  int* hItemBase = nullptr;
+  size_t hFrameCap = 0;
+  cudaEvent_t done = nullptr;
+  bool used = false;
+};
+
+std::mutex g_batch_mu;
+BatchRes g_batch[64];
+int g_ctas_per_sm = 0;
+
+int batch_reserve(BatchRes& b, size_t nRec, size_t nTiles, size_t nFrames) {
+  cudaError_t e = cudaSuccess;
+  if (!b.done) {
+    e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&b.queue, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b.queue, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (b.used) cudaEventSynchronize(b.done);  // last batch finished with the arrays
+  if (nRec > b.recCap) {
+    size_t cap = b.recCap ? b.recCap : 4096;
+    while (cap < nRec) cap *= 2;
+    cudaFree(b.dRecs); cudaFree(b.tmp); cudaFree(b.sorted); cudaFreeHost(b.hRecs);
+    b.dRecs = nullptr; b.tmp = b.sorted = nullptr; b.hRecs = nullptr; b.recCap = 0;
+    e = dalloc(&b.dRecs, cap);
+    if (e == cudaSuccess) e = dalloc(&b.tmp, cap);
+    if (e == cudaSuccess) e = dalloc(&b.sorted, cap);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b.hRecs), sizeof(FragRec) * cap);
+    if (e != cudaSuccess) return cuda_status(e);
+    b.recCap = cap;
+  }
+  if (nTiles > b.tileCap) {
+    size_t cap = b.tileCap ? b.tileCap : 4096;
+    while (cap < nTiles) cap *= 2;
+    cudaFree(b.counts); cudaFree(b.offsets); cudaFree(b.cursor);
+    b.counts = b.offsets = b.cursor = nullptr; b.tileCap = 0;
+    e = dalloc(&b.counts, cap);
+    if (e == cudaSuccess) e = dalloc(&b.offsets, cap);
+    if (e == cudaSuccess) e = dalloc(&b.cursor, cap);
+    if (e != cudaSuccess) return cuda_status(e);
+    b.tileCap = cap;
+  }
+  if (nFrames > b.frameCap) {
+    size_t cap = b.frameCap ? b.frameCap : 64;
+    while (cap < nFrames) cap *= 2;
+    cudaFree(b.dFrames); cudaFree(b.dItemBase); cudaFreeHost(b.hFrames); cudaFreeHost(b.hItemBase);
+    b.dFrames = nullptr; b.dItemBase = nullptr; b.hFrames = nullptr; b.hItemBase = nullptr;
+    b.frameCap = 0;
+    e = dalloc(&b.dFrames, cap);
+    if (e == cudaSuccess) e = dalloc(&b.dItemBase, cap + 1);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b.hFrames), sizeof(FrameArgs) * cap);
+    if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b.hItemBase), sizeof(int) * (cap + 1));
+    if (e != cudaSuccess) return cuda_status(e);
+    b.frameCap = cap;
+  }
+  return DFB_OK;
+}
+
+constexpr size_t kTimingSlots = 128;
+
+// Fold the oldest recorded slot into the running sums (waits for it).
+int harvest_one(dfb_ctx* h) {
+  const size_t slot = (h->tHead + kTimingSlots - h->tCount) % kTimingSlots;
+  cudaEvent_t* e = &h->tev[3 * slot];
+  cudaError_t r = cudaEventSynchronize(e[2]);
+  float b = 0.f, c = 0.f;
+  if (r == cudaSuccess) r = cudaEventElapsedTime(&b, e[0], e[1]);
+  if (r == cudaSuccess) r = cudaEventElapsedTime(&c, e[1], e[2]);
+  if (r != cudaSuccess) return cuda_status(r);
+  h->tSum.launches += 1;
+  h->tSum.bucket_ms += b;
+  h->tSum.composite_ms += c;
+  h->tCount -= 1;
+  return DFB_OK;
+}
+
+// Events of the next timing slot, or null when timing is off.
+cudaEvent_t* timing_slot(dfb_ctx* h) {
+  if (!h->timing) return nullptr;
+  if (h->tev.empty()) {
+    h->tev.assign(3 * kTimingSlots, nullptr);
+    for (auto& e : h->tev)
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  }
+  if (h->tCount == kTimingSlots && harvest_one(h) != DFB_OK) return nullptr;
+  cudaEvent_t* e = &h->tev[3 * h->tHead];
+  h->tHead = (h->tHead + 1) % kTimingSlots;
+  h->tCount += 1;
+  return e;
+}
+
+int end_one(dfb_ctx* h, cudaStream_t s) {
+  FragRec* staged = nullptr;
+  int st = grow_records(h, h->recs.size());
+  if (st != DFB_OK) return st;
+  const int buf = stage_records(h, &staged);
+  if (buf < 0) return buf;
+  const size_t n = h->recs.size();
+  cudaError_t e = cudaSuccess;
+  if (h->lastStreamSet && h->lastStream != s) e = cudaStreamWaitEvent(s, h->frameDone, 0);
+  if (e == cudaSuccess && h->hostCopies) e = cudaStreamWaitEvent(s, h->copyDone, 0);
+  if (e == cudaSuccess && n)
+    e = cudaMemcpyAsync(h->dRecs, staged, sizeof(FragRec) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(h->hRecDone[buf], s);
+  cudaEvent_t* ev = timing_slot(h);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess)
+    e = dfb::launch_bucket(h->dRecs, (int)n, h->nTiles, h->counts, h->offsets, h->cursor, h->tmp,
+                           h->sorted, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  FrameArgs a;
+  fill_frame_args(h, a, 0, h->counts, h->offsets, h->dRecs, h->sorted);
+  if (ev) e = cudaEventRecord(ev[1], s);
+  if (e == cudaSuccess) e = dfb::launch_composite(a, s);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+  if (e == cudaSuccess) e = cudaEventRecord(h->frameDone, s);
+  h->launches += (n ? 4 : 1) + 1;
+  return cuda_status(e);
+}
+
+int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return DFB_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  BatchRes& b = g_batch[dev];
+  size_t nRec = 0, nTiles = 0;
+  for (int i = 0; i < n; ++i) {
+    nRec += hs[i]->recs.size();
+    nTiles += (size_t)hs[i]->nTiles;
+  }
+  int st = batch_reserve(b, nRec, nTiles, (size_t)n);
+  if (st != DFB_OK) return st;
+  cudaError_t e = cudaSuccess;
+  size_t r = 0;
+  int tileBase = 0, items = 0;
+  const int dtype = hs[0]->cfg.dtype;
+  for (int i = 0; i < n; ++i) {
+    dfb_ctx* h = hs[i];
+    for (const FragRec& fr : h->recs) {
+      FragRec g = fr;
+      g.tile += (uint32_t)tileBase;
+      g.frame = (uint32_t)i;
+      b.hRecs[r++] = g;
+    }
+    fill_frame_args(h, b.hFrames[i], tileBase, b.counts, b.offsets, b.dRecs, b.sorted);
+    b.hItemBase[i] = items;
+    items += h->nTiles * h->chunks;
+    tileBase += h->nTiles;
+    if (h->lastStreamSet && h->lastStream != s && e == cudaSuccess)
+      e = cudaStreamWaitEvent(s, h->frameDone, 0);
+    if (h->hostCopies && e == cudaSuccess) e = cudaStreamWaitEvent(s, h->copyDone, 0);
+  }
+  b.hItemBase[n] = items;
+  if (e == cudaSuccess && nRec)
+    e = cudaMemcpyAsync(b.dRecs, b.hRecs, sizeof(FragRec) * nRec, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b.dFrames, b.hFrames, sizeof(FrameArgs) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b.dItemBase, b.hItemBase, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s);
+  cudaEvent_t* ev = timing_slot(hs[0]);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess)
+    e = dfb::launch_bucket(b.dRecs, (int)nRec, (int)nTiles, b.counts, b.offsets, b.cursor, b.tmp,
+                           b.sorted, s);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+  if (e == cudaSuccess)
+    e = dfb::launch_composite_batch(b.dFrames, b.dItemBase, n, items, dtype, b.queue,
+                                    g_ctas_per_sm, s);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+  if (e == cudaSuccess) e = cudaEventRecord(b.done, s);
+  b.used = true;
+  hs[0]->launches += (nRec ? 4 : 1) + 1;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventRecord(hs[i]->frameDone, s);
+  return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int dfb_end_frames(const dfb_handle* hs, int n, void* stream) {
+  if (!hs || n < 1) return DFB_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return DFB_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return DFB_ERR_INVALID_ARG;
+    if (!hs[i]->inFrame) return DFB_ERR_STATE;
+    if (n > 1 && hs[i]->cfg.dtype != hs[0]->cfg.dtype) return DFB_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    const int st = check_trees(hs[i]);
+    if (st != DFB_OK) return st;
+  }
+  for (int i = 0; i < n; ++i) {
+    const int st = allocate(hs[i]);
+    if (st != DFB_OK) return st;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int st = n == 1 ? end_one(hs[0], s) : end_batch(hs, n, s);
+  if (st != DFB_OK) return st;
+  for (int i = 0; i < n; ++i) {
+    dfb_ctx* h = hs[i];
+    if (h->hostCopies) {
+      cudaEventRecord(h->arenaFree[h->arenaIdx], s);
+      h->arenaUsed[h->arenaIdx] = true;
+    }
+    finish_stats(h);
+    h->stats = h->pendingStats;
+    h->accumN = h->pendingN;
+    h->inFrame = false;
+    h->haveFrame = true;
+    h->lastStream = s;
+    h->lastStreamSet = true;
+  }
+  return DFB_OK;
+}
+
+int dfb_sync(dfb_handle h) {
+  if (!h) return DFB_ERR_INVALID_ARG;
+  if (!h->lastStreamSet) return DFB_OK;
+  return cuda_status(cudaEventSynchronize(h->frameDone));
+}
+
+}  // extern "C"
+
+namespace {
+
+// Copy `bytes` from device buffer `src` to `out` (host or device) after the
+// last frame; host destinations wait for completion.
+int copy_out(dfb_ctx* h, void* out, const void* src, size_t bytes) {
+  cudaStream_t s = h->lastStream;
+  const bool dev = is_device_ptr(out);
+  cudaError_t e = cudaMemcpyAsync(out, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && !dev) e = cudaStreamSynchronize(s);
+  return cuda_status(e);
+}
+
+int ensure_read_tmp(dfb_ctx* h) {
+  if (h->readTmp) return DFB_OK;
+  return cuda_status(dalloc(&h->readTmp, (size_t)h->cfg.width * h->cfg.height));
+}
+
+}  // namespace
+
+extern "C" {
+
+int dfb_read_color(dfb_handle h, float* out) {
+  if (!h || !out) return DFB_ERR_INVALID_ARG;
+  if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_WRITE_COLOR)) return DFB_ERR_STATE;
+  return copy_out(h, out, h->color, sizeof(float4) * (size_t)h->cfg.width * h->cfg.height);
+}
+
+int dfb_read_rgba8(dfb_handle h, uint32_t* out) {
+  if (!h || !out) return DFB_ERR_INVALID_ARG;
+  if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_PACK_RGBA8)) return DFB_ERR_STATE;
+  return copy_out(h, out, h->rgba8, sizeof(uint32_t) * (size_t)h->cfg.width * h->cfg.height);
+}
+
+int dfb_read_accum(dfb_handle h, float* out) {
+  if (!h || !out) return DFB_ERR_INVALID_ARG;
+  if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
+  const int64_t px = (int64_t)h->cfg.width * h->cfg.height;
+  const bool dev = is_device_ptr(out);
+  float4* dst = (float4*)out;
+  if (!dev) {
+    const int st = ensure_read_tmp(h);
+    if (st != DFB_OK) return st;
+    dst = h->readTmp;
+  }
+  const int n = h->accumN;
+  cudaError_t e = dfb::launch_normalise(h->accum, h->comp, n > h->cfg.kahan_after ? 1 : 0,
+                                        1.0f / (float)n, dst, px, h->lastStream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev) return DFB_OK;
+  return copy_out(h, out, h->readTmp, sizeof(float4) * (size_t)px);
+}
+
+int dfb_read_variance(dfb_handle h, float* per_pixel, float* per_tile) {
+  if (!h) return DFB_ERR_INVALID_ARG;
+  if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
+  const int64_t px = (int64_t)h->cfg.width * h->cfg.height;
+  const int n = h->accumN;
+  const float invNm1 = n > 1 ? 1.0f / (float)(n - 1) : 0.0f;
+  if (per_pixel) {
+    const bool dev = is_device_ptr(per_pixel);
+    float4* dst = (float4*)per_pixel;
+    if (!dev) {
+      const int st = ensure_read_tmp(h);
+      if (st != DFB_OK) return st;
+      dst = h->readTmp;
+    }
+    cudaError_t e = dfb::launch_variance(h->m2, invNm1, dst, px, h->lastStream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!dev) {
+      const int st = copy_out(h, per_pixel, h->readTmp, sizeof(float4) * (size_t)px);
+      if (st != DFB_OK) return st;
+    }
+  }
+  if (per_tile) return copy_out(h, per_tile, h->tileVar, sizeof(float) * h->nTiles);
+  return DFB_OK;
+}
+
+int dfb_get_stats(dfb_handle h, dfb_frame_stats* out) {
+  if (!h || !out) return DFB_ERR_INVALID_ARG;
+  *out = h->stats;
+  return DFB_OK;
+}
+
+int dfb_get_tiles(dfb_handle h, int* tiles_x, int* tiles_y) {
+  if (!h || !tiles_x || !tiles_y) return DFB_ERR_INVALID_ARG;
+  *tiles_x = h->tilesX;
+  *tiles_y = h->tilesY;
+  return DFB_OK;
+}
+
+int dfb_save_accum(dfb_handle h, float* sum, float* comp, float* m2, int* frames) {
+  if (!h || !sum || !comp || !m2 || !frames) return DFB_ERR_INVALID_ARG;
+  if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
+  const size_t bytes = sizeof(float4) * (size_t)h->cfg.width * h->cfg.height;
+  int st = copy_out(h, sum, h->accum, bytes);
+  if (st == DFB_OK) {
+    if (h->accumN > h->cfg.kahan_after) st = copy_out(h, comp, h->comp, bytes);
+    else {
+      const bool dev = is_device_ptr(comp);
+      if (dev) st = cuda_status(cudaMemsetAsync(comp, 0, bytes, h->lastStream));
+      else memset(comp, 0, bytes);
+    }
+  }
+  if (st == DFB_OK) st = copy_out(h, m2, h->m2, bytes);
+  if (st == DFB_OK) *frames = h->accumN;
+  return st;
+}
+
+int dfb_load_accum(dfb_handle h, const float* sum, const float* comp, const float* m2,
+                   int frames) {
+  if (!h || !sum || !comp || !m2 || frames < 1) return DFB_ERR_INVALID_ARG;
+  if (h->inFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
+  int st = allocate(h);
+  if (st != DFB_OK) return st;
+  const size_t bytes = sizeof(float4) * (size_t)h->cfg.width * h->cfg.height;
+  cudaStream_t s = h->lastStreamSet ? h->lastStream : (cudaStream_t)0;
+  cudaError_t e = cudaMemcpyAsync(h->accum, sum, bytes, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->comp, comp, bytes, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->m2, m2, bytes, cudaMemcpyDefault, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_status(e);
+  h->accumN = frames;
+  h->haveFrame = true;
+  return DFB_OK;
+}
+
+int dfb_convert_tiles(const float* src, void* dst, float* scales, int n_tiles, int tile_pixels,
+                      int dtype, void* stream) {
+  if (!src || !dst || n_tiles < 0 || tile_pixels < 1) return DFB_ERR_INVALID_ARG;
+  if (dtype != DFB_F16 && dtype != DFB_BF16 && dtype != DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;
+  if (dtype == DFB_FP8E4M3 && !scales) return DFB_ERR_INVALID_ARG;
+  if (n_tiles == 0) return DFB_OK;
+  return cuda_status(dfb::launch_convert(src, dst, scales, n_tiles, tile_pixels, dtype,
+                                         (cudaStream_t)stream));
+}
+
+int dfb_set_timing(dfb_handle h, int enable) {
+  if (!h) return DFB_ERR_INVALID_ARG;
+  h->timing = enable != 0;
+  return DFB_OK;
+}
+
+int dfb_read_timing(dfb_handle h, dfb_timing* out, int reset) {
+  if (!h || !out) return DFB_ERR_INVALID_ARG;
+  while (h->tCount) {
+    const int st = harvest_one(h);
+    if (st != DFB_OK) return st;
+  }
+  *out = h->tSum;
+  if (reset) h->tSum = dfb_timing{};
+  return DFB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,213 @@
+"""The C ABI without a GPU: the library loads, exports every declared entry
+point, and its host-side logic (validation, frame state, per-tile dependency
+trees of Sec. 3.1.1) answers with the documented status codes.  No kernel is
+launched: every case here stops at a host-side check."""
+
+import ctypes as C
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2305_07083_gb300 import build, dfb as D
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _has_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build()
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "dfb.h")) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"DFB_API\s+[\w\s\*]+?\b(dfb_\w+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol():
+    syms = declared_symbols()
+    assert len(syms) >= 25
+    L = C.CDLL(D.LIB)
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_error_strings_and_version():
+    assert D.dfb_version() >= 10000
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+        assert D.dfb_error_string(code) not in ("", "unknown status")
+    assert D.dfb_error_string(-99) == "unknown status"
+
+
+@pytest.mark.parametrize("W,H,T,mode,dtype,flags", [
+    (0, 64, 16, 0, 0, 1), (64, -1, 16, 0, 0, 1), (64, 64, 12, 0, 0, 1), (64, 64, 2, 0, 0, 1),
+    (64, 64, 512, 0, 0, 1), (64, 64, 16, 3, 0, 1), (64, 64, 16, 0, 4, 1), (64, 64, 16, 0, 0, 64)])
+def test_create_rejects_bad_config(W, H, T, mode, dtype, flags):
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_create_ex(W, H, T, mode, dtype, flags)
+    assert e.value.code == D.DFB_ERR_INVALID_ARG
+
+
+def deferred(W=64, H=48, T=16, dtype=D.DFB_F32, mode=D.DFB_BLEND_DEPTH):
+    return D.dfb_create_ex(W, H, T, mode, dtype, D.DFB_FLAGS_DEFAULT | D.DFB_FLAG_DEFER_ALLOC)
+
+
+FAKE = 1 << 20      # aligned fake device addresses: never dereferenced here
+
+
+def submit(h, tiles, keys=None, rgba=None, depth=None, scales=None):
+    n = len(tiles)
+    keys = np.zeros(n, np.float32) if keys is None else keys
+    rgba = [FAKE + 4096 * i for i in range(n)] if rgba is None else rgba
+    depth = [FAKE * 2 + 4096 * i for i in range(n)] if depth is None else depth
+    D.dfb_submit_tiles(h, tiles, keys, rgba, depth, scales, D.DFB_PTR_DEVICE)
+
+
+def code_of(fn, *a):
+    with pytest.raises(D.DfbError) as e:
+        fn(*a)
+    return e.value.code
+
+
+def ex(h, rows, scale=1.0):
+    """dfb_submit_tiles_ex on fake device addresses; rows = (tile, key, gen, children)."""
+    D.dfb_submit_tiles_ex(h, [(t, k, FAKE, FAKE, scale, g, c) for t, k, g, c in rows],
+                          D.DFB_PTR_DEVICE)
+
+
+def test_frame_state_machine():
+    h = deferred()
+    try:
+        assert code_of(submit, h, [0]) == D.DFB_ERR_STATE           # no open frame
+        assert code_of(D.dfb_set_tile_children, h, 0, 1) == D.DFB_ERR_STATE
+        assert code_of(D.dfb_end_frame, h) == D.DFB_ERR_STATE
+        D.dfb_begin_frame(h, 0)
+        assert code_of(D.dfb_begin_frame, h, 0) == D.DFB_ERR_STATE  # already open
+        assert code_of(D.dfb_read_color, h, np.zeros(4, np.float32)) == D.DFB_ERR_STATE
+    finally:
+        D.dfb_destroy(h)
+
+
+def test_submit_validation():
+    h = deferred(dtype=D.DFB_F32)
+    try:
+        D.dfb_begin_frame(h, 0)
+        tx, ty = D.dfb_get_tiles(h)
+        assert (tx, ty) == (4, 3)
+        assert code_of(submit, h, [12]) == D.DFB_ERR_TILE_RANGE
+        assert code_of(submit, h, [-1]) == D.DFB_ERR_TILE_RANGE
+        assert code_of(submit, h, [0], np.array([math.nan], np.float32)) == D.DFB_ERR_INVALID_ARG
+        assert code_of(submit, h, [0], None, [FAKE + 4]) == D.DFB_ERR_INVALID_ARG   # rgba 16B
+        assert code_of(submit, h, [0], None, None, [FAKE + 2]) == D.DFB_ERR_INVALID_ARG
+        assert code_of(submit, h, [0], None, [0]) == D.DFB_ERR_INVALID_ARG          # null
+        assert code_of(ex, h, [(0, 0.0, 0, 0)]) == D.DFB_ERR_INVALID_ARG       # generation 0
+        assert code_of(ex, h, [(0, 0.0, 1, -1)]) == D.DFB_ERR_INVALID_ARG      # children < 0
+    finally:
+        D.dfb_destroy(h)
+    h8 = deferred(dtype=D.DFB_FP8E4M3)
+    try:
+        D.dfb_begin_frame(h8, 0)
+        assert code_of(D.dfb_submit_tile, h8, 0, 0.0, FAKE, FAKE) == D.DFB_ERR_INVALID_ARG
+        assert code_of(submit, h8, [0]) == D.DFB_ERR_INVALID_ARG                  # no scales
+        for bad in (0.0, -1.0, math.inf, math.nan):
+            assert code_of(submit, h8, [0], None, None, None,
+                           np.array([bad], np.float32)) == D.DFB_ERR_INVALID_ARG
+        submit(h8, [0], scales=np.array([0.5], np.float32))
+        # FP8 needs only 4-byte aligned RGBA
+        submit(h8, [0], rgba=[FAKE + 4], scales=np.array([0.5], np.float32))
+    finally:
+        D.dfb_destroy(h8)
+
+
+def test_dependency_tree_counts():
+    """Sec. 3.1.1: the children declared by a generation give the number of
+    tiles expected in the next; completion needs every generation."""
+    h = deferred()
+    try:
+        D.dfb_begin_frame(h, 0)
+        D.dfb_set_tile_children(h, 5, 3)
+        assert code_of(D.dfb_set_tile_children, h, 5, 1) == D.DFB_ERR_STATE   # declared twice
+        assert code_of(D.dfb_set_tile_children, h, 99, 1) == D.DFB_ERR_TILE_RANGE
+        assert code_of(D.dfb_set_tile_children, h, 1, -2) == D.DFB_ERR_INVALID_ARG
+        submit(h, [5, 5])
+        assert code_of(D.dfb_end_frame, h) == D.DFB_ERR_INCOMPLETE            # 2 of 3
+        submit(h, [5, 5])
+        assert code_of(D.dfb_end_frame, h) == D.DFB_ERR_INCOMPLETE            # 4 of 3
+    finally:
+        D.dfb_destroy(h)
+
+
+def test_multi_generation_tree():
+    h = deferred()
+    try:
+        D.dfb_begin_frame(h, 0)
+        D.dfb_set_tile_children(h, 2, 2)
+        # generation 1: two tiles, declaring 1 + 2 children in generation 2;
+        # arrival order across generations is arbitrary
+        ex(h, [(2, 2.0, 2, 0), (2, 0.0, 1, 1), (2, 3.0, 2, 0), (2, 1.0, 1, 2)])
+        assert code_of(D.dfb_end_frame, h) == D.DFB_ERR_INCOMPLETE            # 2 of 3 in gen 2
+        ex(h, [(2, 4.0, 2, 0)])
+        # a stray generation-3 tile nobody declared
+        ex(h, [(2, 5.0, 3, 0)])
+        assert code_of(D.dfb_end_frame, h) == D.DFB_ERR_INCOMPLETE
+    finally:
+        D.dfb_destroy(h)
+
+
+def test_bulk_submit_is_all_or_nothing():
+    h = deferred()
+    try:
+        D.dfb_begin_frame(h, 0)
+        D.dfb_set_tile_children(h, 0, 2)
+        assert code_of(submit, h, [0, 0, 77]) == D.DFB_ERR_TILE_RANGE
+        # nothing from the rejected call was kept: still 0 of 2 received
+        submit(h, [0])
+        assert code_of(D.dfb_end_frame, h) == D.DFB_ERR_INCOMPLETE
+    finally:
+        D.dfb_destroy(h)
+
+
+@pytest.mark.skipif(_has_gpu(), reason="would launch kernels on the fake addresses")
+def test_complete_multi_generation_tree_passes_host_checks():
+    h = deferred()
+    try:
+        D.dfb_begin_frame(h, 0)
+        D.dfb_set_tile_children(h, 2, 2)
+        ex(h, [(2, 2.0, 2, 0), (2, 0.0, 1, 1), (2, 3.0, 2, 0), (2, 1.0, 1, 2), (2, 4.0, 2, 0)])
+        assert code_of(D.dfb_end_frame, h) == D.DFB_ERR_CUDA   # trees fine; no device here
+    finally:
+        D.dfb_destroy(h)
+
+
+@pytest.mark.skipif(_has_gpu(), reason="would launch kernels on the fake addresses")
+def test_complete_frame_without_device_reports_cuda_error():
+    h = deferred()
+    try:
+        D.dfb_begin_frame(h, 0)
+        D.dfb_set_tile_children(h, 0, 1)
+        submit(h, [0])
+        assert code_of(D.dfb_end_frame, h) == D.DFB_ERR_CUDA
+        # the frame stays open, so it can still be ended once a device is present
+        assert code_of(D.dfb_begin_frame, h, 0) == D.DFB_ERR_STATE
+    finally:
+        D.dfb_destroy(h)
+
+
+def test_null_handle_and_pointers():
+    L = D.lib()
+    assert L.dfb_destroy(None) == 0
+    assert L.dfb_begin_frame(None, 0) == D.DFB_ERR_INVALID_ARG
+    assert L.dfb_create_ex(None, None) == D.DFB_ERR_INVALID_ARG
+    assert L.dfb_end_frames(None, 1, None) == D.DFB_ERR_INVALID_ARG
+    assert L.dfb_convert_tiles(None, None, None, 1, 16, 1, None) == D.DFB_ERR_INVALID_ARG

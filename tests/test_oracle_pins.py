@@ -118,7 +118,12 @@ def test_background_behind_all():
     np.testing.assert_array_equal(empty, np.tile([0.25, 0.25, 0.25, 0.5], (4, 1)))
     ez = o.composite_tile(np.zeros((0, 4, 4)), np.zeros((0, 4)), [], [], o.ZCOMPOSITE,
                           bg=(0.5, 0.5, 0.5, 0.5))
-    np.testing.assert_array_equal(ez, np.tile([0.5, 0.5, 0.5, 0.5], (4, 1)))
+    np.testing.assert_array_equal(ez, np.tile([0.25, 0.25, 0.25, 0.5], (4, 1)))
+    # a pixel that no fragment covers (depth +inf) shows the background in Z mode
+    rg = np.array([[[0.0, 0.0, 0.0, 0.0], [0.5, 0.0, 0.0, 0.5]]])
+    zz = o.composite_tile(rg, np.array([[np.inf, 1.0]], np.float32), [0.0], [0], o.ZCOMPOSITE,
+                          bg=(1.0, 1.0, 1.0, 0.5))
+    np.testing.assert_array_equal(zz, [[0.5, 0.5, 0.5, 0.5], [0.5, 0.0, 0.0, 0.5]])
 
 
 # --- ordering ----------------------------------------------------------------
@@ -166,8 +171,9 @@ def test_zcomposite_brute_force():
             z = float(depth[i, p])
             z = math.inf if math.isnan(z) else (0.0 if z == 0 else z)
             cand.append((z, float(keys[i]), i))
-        best = min(cand)[2]
-        np.testing.assert_array_equal(out[p], rgba[best, p])
+        zb, _, best = min(cand)
+        want = rgba[best, p] if zb != math.inf else np.zeros(4)
+        np.testing.assert_array_equal(out[p], want)
 
 
 def test_depth_sort_ties_and_nan_brute_force():
