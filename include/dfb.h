@@ -81,7 +81,9 @@ enum dfb_status {
   DFB_ERR_INCOMPLETE = -4,  /* a tile's dependency tree is not complete         */
   DFB_ERR_OOM = -5,         /* device or pinned allocation failed               */
   DFB_ERR_TIMEOUT = -6,     /* a device-side wait gave up                        */
-  DFB_ERR_CUDA = -7         /* a CUDA call failed (including: no device)         */
+  DFB_ERR_CUDA = -7,        /* a CUDA call failed (including: no device)         */
+  DFB_ERR_CAPACITY = -8     /* request larger than dfb_composite_noalloc's fixed
+                               scratch (see its limits below)                   */
 };
 
 /* Configuration flags. */
@@ -252,6 +254,38 @@ typedef struct dfb_timing {
 } dfb_timing;
 DFB_API int dfb_set_timing(dfb_handle h, int enable);
 DFB_API int dfb_read_timing(dfb_handle h, dfb_timing* out, int reset);
+
+/* Composite one frame in a single call that allocates no memory at all.
+   The paper has no counterpart: it is an interface for callers that must not
+   call cudaMalloc -- e.g. an in-situ simulation or renderer that reserves the
+   whole GPU and hands out memory only from its own pool, or real-time code in
+   which a cudaMalloc/cudaFree could synchronise the device and miss a frame
+   deadline.  The handle-based path above allocates framebuffers and scratch,
+   so such callers use this instead.
+   Inputs are those of dfb_submit_tiles (host arrays of length n; rgba/depth
+   are DEVICE pointers to T*T-pixel tiles of `dtype`; scales only for FP8),
+   plus an optional unpremultiplied background (4 floats, NULL = 0).  Outputs
+   are caller-owned DEVICE buffers: color_out (W*H*4 floats) and/or rgba8_out
+   (W*H uint32, sRGB of the frame colour); either may be NULL, not both.
+   There is no accumulation or variance (those need resident state).
+   Scratch: a fixed device array of about 5.3 MB inside the library, held by
+   every GPU that loads it until the process exits.  Limits: n <= 65536
+   fragment tiles and ceil(W/T)*ceil(H/T) <= 65536 tiles; larger requests
+   return DFB_ERR_CAPACITY before any GPU work.  The first call on a device
+   looks up the array's device address (and uploads the sRGB table) with that
+   device current; make that first call before any stream capture.  All calls
+   share the one array, which keeps the previous call's contents (the call
+   clears what must start at zero): calls whose GPU work overlaps -- on two
+   streams, or from two threads -- race and must be serialised by the caller.
+   The call returns once the host arrays have been copied; the GPU work is
+   then queued on `stream`.  Errors: INVALID_ARG (sizes, NaN key, null or
+   misaligned pointer, outputs not device memory), TILE_RANGE, CAPACITY,
+   CUDA. */
+DFB_API int dfb_composite_noalloc(int width, int height, int tile_size, int mode, int dtype,
+                                  int n, const int* tile_ids, const float* order_keys,
+                                  const void* const* rgba, const float* const* depth,
+                                  const float* scales, const float* background,
+                                  float* color_out, uint32_t* rgba8_out, void* stream);
 
 /* Human-readable name of a status code (static storage). */
 DFB_API const char* dfb_error_string(int status);

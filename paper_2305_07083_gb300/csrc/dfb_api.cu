@@ -167,6 +167,18 @@ int ensure_table(int dev) {
   return st;
 }
 
+}  // namespace
+
+// Uploads the sRGB code boundaries to the current device once (no allocation).
+cudaError_t dfb::ensure_tables() {
+  int dev = 0;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  return ensure_table(dev) == DFB_OK ? cudaSuccess : cudaErrorUnknown;
+}
+
+namespace {
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
@@ -519,6 +531,7 @@ const char* dfb_error_string(int s) {
     case DFB_ERR_OOM: return "out of memory";
     case DFB_ERR_TIMEOUT: return "device wait timed out";
     case DFB_ERR_CUDA: return "CUDA error";
+    case DFB_ERR_CAPACITY: return "request exceeds the fixed scratch of dfb_composite_noalloc";
     default: return "unknown status";
   }
 }

@@ -1,0 +1,220 @@
+// dfb_composite_noalloc: one frame composited without allocating memory.
+//
+// Who needs this: callers that are not allowed to call cudaMalloc.  Examples
+// are an in-situ simulation or renderer that reserves the whole device up
+// front and hands out memory only from its own pool; real-time code where a
+// cudaMalloc / cudaFree may synchronise the device and break a frame
+// deadline; and code running where the CUDA runtime forbids allocation.  The
+// handle-based path (dfb_create ... dfb_end_frame) allocates its framebuffers
+// and bucketing scratch, so those callers cannot use it.
+//
+// This entry point keeps all its scratch (fragment records and the per-tile
+// bucketing arrays) in one file-scope device array of fixed size, g_scratch,
+// and writes only to the caller's output buffers.  It reuses the bucketing and
+// composite kernels of the handle path unchanged.
+#include <math.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "dfb_internal.h"
+
+namespace {
+
+using dfb::FragRec;
+using dfb::FrameArgs;
+
+constexpr int kMaxFragments = 65536;  // fragment tiles per call
+constexpr int kMaxTiles = 65536;      // tiles per frame
+
+// Layout of g_scratch (each region 256-byte aligned):
+//   FragRec  recs[kMaxFragments]      32 B each
+//   int      tileIn[kMaxFragments]    raw inputs copied from the caller
+//   float    keyIn[kMaxFragments]
+//   uint64   rgbaIn[kMaxFragments]
+//   uint64   depthIn[kMaxFragments]
+//   float    scaleIn[kMaxFragments]
+//   uint32   tmp[kMaxFragments], sorted[kMaxFragments]
+//   int      counts[kMaxTiles], offsets[kMaxTiles], cursor[kMaxTiles]
+constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+constexpr size_t kOffRecs = 0;
+constexpr size_t kOffTileIn = align256(kOffRecs + sizeof(FragRec) * kMaxFragments);
+constexpr size_t kOffKeyIn = align256(kOffTileIn + sizeof(int) * kMaxFragments);
+constexpr size_t kOffRgbaIn = align256(kOffKeyIn + sizeof(float) * kMaxFragments);
+constexpr size_t kOffDepthIn = align256(kOffRgbaIn + sizeof(uint64_t) * kMaxFragments);
+constexpr size_t kOffScaleIn = align256(kOffDepthIn + sizeof(uint64_t) * kMaxFragments);
+constexpr size_t kOffTmp = align256(kOffScaleIn + sizeof(float) * kMaxFragments);
+constexpr size_t kOffSorted = align256(kOffTmp + sizeof(uint32_t) * kMaxFragments);
+constexpr size_t kOffCounts = align256(kOffSorted + sizeof(uint32_t) * kMaxFragments);
+constexpr size_t kOffOffsets = align256(kOffCounts + sizeof(int) * kMaxTiles);
+constexpr size_t kOffCursor = align256(kOffOffsets + sizeof(int) * kMaxTiles);
+constexpr size_t kScratchBytes = align256(kOffCursor + sizeof(int) * kMaxTiles);  // ~5.3 MB
+
+// The scratch itself.  Every GPU that loads the library holds it until the
+// process exits.  In host code `g_scratch` names a host-side stand-in, not the
+// device memory, so host code must only use the address that
+// cudaGetSymbolAddress returns for the current device.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// Device address of g_scratch per device, looked up once with that device
+// current (the first call on a device does it).
+std::mutex g_mu;
+void* g_addr[64] = {};
+
+int scratch_for_current_device(unsigned char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DFB_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return DFB_ERR_CUDA;
+    if (dfb::ensure_tables() != cudaSuccess) return DFB_ERR_CUDA;  // sRGB code boundaries
+    g_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_addr[dev]);
+  return DFB_OK;
+}
+
+// Build the 32-byte fragment records from the raw per-fragment inputs.
+__global__ void k_pack_records(const int* __restrict__ tileIn, const float* __restrict__ keyIn,
+                               const uint64_t* __restrict__ rgbaIn,
+                               const uint64_t* __restrict__ depthIn,
+                               const float* __restrict__ scaleIn, int useScale, int n,
+                               FragRec* __restrict__ recs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t u = __float_as_uint(keyIn[i]);
+  if (u == 0x80000000u) u = 0u;
+  FragRec r;
+  r.rgba = reinterpret_cast<const void*>(rgbaIn[i]);
+  r.depth = reinterpret_cast<const float*>(depthIn[i]);
+  r.tile = (uint32_t)tileIn[i];
+  r.key = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  r.scale = useScale ? scaleIn[i] : 1.0f;
+  r.frame = 0u;
+  recs[i] = r;
+}
+
+int elt_bytes(int dtype) {
+  return dtype == DFB_F32 ? 4 : (dtype == DFB_FP8E4M3 ? 1 : 2);
+}
+
+bool device_accessible(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int mode, int dtype,
+                                     int n, const int* tile_ids, const float* order_keys,
+                                     const void* const* rgba, const float* const* depth,
+                                     const float* scales, const float* background,
+                                     float* color_out, uint32_t* rgba8_out, void* stream) {
+  // ---- validation (host only) ----
+  const int T = tile_size;
+  if (width < 1 || height < 1 || T < 4 || T > 256 || (T & (T - 1))) return DFB_ERR_INVALID_ARG;
+  if (mode < DFB_BLEND_DEPTH || mode > DFB_ZCOMPOSITE) return DFB_ERR_INVALID_ARG;
+  if (dtype < DFB_F32 || dtype > DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!tile_ids || !order_keys || !rgba || !depth))) return DFB_ERR_INVALID_ARG;
+  if (dtype == DFB_FP8E4M3 && n > 0 && !scales) return DFB_ERR_INVALID_ARG;
+  if (!color_out && !rgba8_out) return DFB_ERR_INVALID_ARG;
+  const int tilesX = (width + T - 1) / T, tilesY = (height + T - 1) / T;
+  if ((int64_t)tilesX * tilesY > kMaxTiles || n > kMaxFragments) return DFB_ERR_CAPACITY;
+  const int nTiles = tilesX * tilesY;
+  const uintptr_t ralign = (uintptr_t)(4 * elt_bytes(dtype));
+  for (int i = 0; i < n; ++i) {
+    if (tile_ids[i] < 0 || tile_ids[i] >= nTiles) return DFB_ERR_TILE_RANGE;
+    if (isnan(order_keys[i]) || !rgba[i] || !depth[i]) return DFB_ERR_INVALID_ARG;
+    if (((uintptr_t)rgba[i] % ralign) || ((uintptr_t)depth[i] % 4)) return DFB_ERR_INVALID_ARG;
+    if (dtype == DFB_FP8E4M3 && !(scales[i] > 0.0f && isfinite(scales[i])))
+      return DFB_ERR_INVALID_ARG;
+  }
+  float bg[4] = {0.f, 0.f, 0.f, 0.f};
+  if (background)
+    for (int c = 0; c < 4; ++c) {
+      if (!isfinite(background[c])) return DFB_ERR_INVALID_ARG;
+      bg[c] = background[c];
+    }
+  if ((color_out && !device_accessible(color_out)) ||
+      (rgba8_out && !device_accessible(rgba8_out)))
+    return DFB_ERR_INVALID_ARG;
+
+  unsigned char* base = nullptr;
+  int st = scratch_for_current_device(&base);
+  if (st != DFB_OK) return st;
+  FragRec* recs = reinterpret_cast<FragRec*>(base + kOffRecs);
+  int* tileIn = reinterpret_cast<int*>(base + kOffTileIn);
+  float* keyIn = reinterpret_cast<float*>(base + kOffKeyIn);
+  uint64_t* rgbaIn = reinterpret_cast<uint64_t*>(base + kOffRgbaIn);
+  uint64_t* depthIn = reinterpret_cast<uint64_t*>(base + kOffDepthIn);
+  float* scaleIn = reinterpret_cast<float*>(base + kOffScaleIn);
+  uint32_t* tmp = reinterpret_cast<uint32_t*>(base + kOffTmp);
+  uint32_t* sorted = reinterpret_cast<uint32_t*>(base + kOffSorted);
+  int* counts = reinterpret_cast<int*>(base + kOffCounts);
+  int* offsets = reinterpret_cast<int*>(base + kOffOffsets);
+  int* cursor = reinterpret_cast<int*>(base + kOffCursor);
+  static_assert(sizeof(void*) == sizeof(uint64_t), "64-bit pointers");
+
+  // ---- inputs into the scratch (plain copies; the host arrays may be pageable) ----
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  const bool fp8 = dtype == DFB_FP8E4M3;
+  if (n > 0) {
+    e = cudaMemcpyAsync(tileIn, tile_ids, sizeof(int) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(keyIn, order_keys, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(rgbaIn, rgba, sizeof(void*) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(depthIn, depth, sizeof(void*) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && fp8)
+      e = cudaMemcpyAsync(scaleIn, scales, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    // the caller may reuse its host arrays once this call returns
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+      k_pack_records<<<(n + 255) / 256, 256, 0, s>>>(tileIn, keyIn, rgbaIn, depthIn, scaleIn,
+                                                     fp8 ? 1 : 0, n, recs);
+      e = cudaGetLastError();
+    }
+  }
+  // ---- bucketing (clears the per-tile counts itself) and compositing ----
+  if (e == cudaSuccess)
+    e = dfb::launch_bucket(recs, n, nTiles, counts, offsets, cursor, tmp, sorted, s);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? DFB_ERR_OOM : DFB_ERR_CUDA;
+
+  FrameArgs a{};
+  a.W = width;
+  a.H = height;
+  a.T = T;
+  int logT = 0;
+  while ((1 << logT) < T) ++logT;
+  a.logT = logT;
+  a.tilesX = tilesX;
+  a.nTiles = nTiles;
+  a.chunks = (T * T + dfb::kItemPixels - 1) / dfb::kItemPixels;
+  a.tileBase = 0;
+  a.mode = mode;
+  a.dtype = dtype;
+  // no accumulation: the per-tile variance scratch of the handle path is unused
+  a.flags = (color_out ? DFB_FLAG_WRITE_COLOR : 0u) | (rgba8_out ? DFB_FLAG_PACK_RGBA8 : 0u);
+  a.frameN = 1;
+  a.invN = 1.0f;
+  a.invNm1 = 0.0f;
+  a.bgR = bg[0] * bg[3];
+  a.bgG = bg[1] * bg[3];
+  a.bgB = bg[2] * bg[3];
+  a.bgA = bg[3];
+  a.recs = recs;
+  a.sorted = sorted;
+  a.counts = counts;
+  a.offsets = offsets;
+  a.color = reinterpret_cast<float4*>(color_out);
+  a.rgba8 = rgba8_out;
+  e = dfb::launch_composite(a, s);
+  return e == cudaSuccess ? DFB_OK : DFB_ERR_CUDA;
+}

@@ -20,7 +20,7 @@ DFB_BLEND_DEPTH, DFB_BLEND_ORDERED, DFB_ZCOMPOSITE = 0, 1, 2
 DFB_F32, DFB_F16, DFB_BF16, DFB_FP8E4M3 = 0, 1, 2, 3
 DFB_OK = 0
 DFB_ERR_INVALID_ARG, DFB_ERR_TILE_RANGE, DFB_ERR_STATE, DFB_ERR_INCOMPLETE = -1, -2, -3, -4
-DFB_ERR_OOM, DFB_ERR_TIMEOUT, DFB_ERR_CUDA = -5, -6, -7
+DFB_ERR_OOM, DFB_ERR_TIMEOUT, DFB_ERR_CUDA, DFB_ERR_CAPACITY = -5, -6, -7, -8
 DFB_FLAG_ACCUMULATE, DFB_FLAG_WRITE_COLOR, DFB_FLAG_PACK_RGBA8, DFB_FLAG_DEFER_ALLOC = 1, 2, 4, 8
 DFB_FLAGS_DEFAULT = DFB_FLAG_ACCUMULATE | DFB_FLAG_WRITE_COLOR | DFB_FLAG_PACK_RGBA8
 DFB_PTR_AUTO, DFB_PTR_DEVICE, DFB_PTR_HOST = 0, 1, 2
@@ -98,6 +98,8 @@ def lib():
         "dfb_convert_tiles": (C.c_int, [P, P, P, C.c_int, C.c_int, C.c_int, P]),
         "dfb_set_timing": (C.c_int, [H, C.c_int]),
         "dfb_read_timing": (C.c_int, [H, C.POINTER(dfb_timing), C.c_int]),
+        "dfb_composite_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                            P, P, P, P, P, P, P, P, P]),
         "dfb_error_string": (C.c_char_p, [C.c_int]),
         "dfb_version": (C.c_int, []),
     }
@@ -280,3 +282,23 @@ def dfb_read_timing(h, reset=True) -> dict:
     t = dfb_timing()
     _check(lib().dfb_read_timing(h, C.byref(t), int(reset)), "dfb_read_timing")
     return {"launches": t.launches, "bucket_ms": t.bucket_ms, "composite_ms": t.composite_ms}
+
+
+def dfb_composite_noalloc(width, height, tile_size, mode, dtype, tile_ids, order_keys, rgba_ptrs,
+                          depth_ptrs, scales=None, background=None, color_out=None,
+                          rgba8_out=None, stream=None):
+    """One frame without any allocation; outputs are caller-owned device buffers."""
+    tid = np.ascontiguousarray(tile_ids, dtype=np.int32)
+    key = np.ascontiguousarray(order_keys, dtype=np.float32)
+    rp = np.ascontiguousarray(rgba_ptrs, dtype=np.uint64)
+    dp = np.ascontiguousarray(depth_ptrs, dtype=np.uint64)
+    sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float32)
+    bg = None if background is None else np.ascontiguousarray(background, dtype=np.float32)
+    n = len(tid)
+    if not (len(key) == len(rp) == len(dp) == n) or (sc is not None and len(sc) != n):
+        raise ValueError("array lengths differ")
+    st = lib().dfb_composite_noalloc(
+        width, height, tile_size, mode, dtype, n, tid.ctypes.data, key.ctypes.data,
+        rp.ctypes.data, dp.ctypes.data, None if sc is None else sc.ctypes.data,
+        None if bg is None else bg.ctypes.data, _ptr(color_out), _ptr(rgba8_out), _stream(stream))
+    return _check(st, "dfb_composite_noalloc")
