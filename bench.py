@@ -143,7 +143,7 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # workload
 # ----------------------------------------------------------------------------
-def build_workload(seed, device):
+def build_workload(seed, device, n_frames=None):
     import torch
     from harness import scenes
     sc = scenes.scene_2048(seed=seed, jitter_sigma=0.02)
@@ -152,7 +152,7 @@ def build_workload(seed, device):
     depth = torch.from_numpy(sc.depth).to(device)
     frames = []
     g = torch.Generator(device=device)
-    for f in range(N_FRAMES):
+    for f in range(n_frames or N_FRAMES):
         g.manual_seed(seed * 1000 + f)
         j = torch.randn(base.shape, generator=g, device=device, dtype=torch.float32) * 0.02
         rgb = (base + j).clamp_(0.0, 1.0) * alpha[..., None]
@@ -165,7 +165,7 @@ def build_workload(seed, device):
 class Runner:
     """One framebuffer handle + pointer tables for the 16 resident frames."""
 
-    def __init__(self, sc, frames, depth, dtype, where="device"):
+    def __init__(self, sc, frames, depth, dtype, where="device", tune=None):
         from paper_2305_07083_gb300 import dfb as D
         self.D = D
         self.sc = sc
@@ -175,6 +175,8 @@ class Runner:
         self.where = D.DFB_PTR_DEVICE if where == "device" else D.DFB_PTR_HOST
         self.h = D.dfb_create_ex(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH, dtype, D.DFB_FLAGS_DEFAULT,
                                  0, max(4096, sc.n))
+        if tune:
+            D.dfb_set_tuning(self.h, *tune)
         P = sc.T * sc.T
         rb = P * 4 * D.ELEMENT_BYTES[dtype]
         self.tile_ids = np.ascontiguousarray(sc.tile_ids, np.int32)
@@ -186,8 +188,8 @@ class Runner:
         D = self.D
         for f in range(N_FRAMES):
             D.dfb_begin_frame(self.h, f > 0)
-            D.dfb_submit_tiles(self.h, self.tile_ids, self.keys, self.rptr[f], self.dptr, None,
-                               self.where)
+            D.dfb_submit_tiles(self.h, self.tile_ids, self.keys, self.rptr[f % len(self.rptr)],
+                               self.dptr, None, self.where)
             D.dfb_end_frame(self.h, stream)
 
     def close(self):
@@ -311,6 +313,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f16", action="store_true")
+    ap.add_argument("--tune", default=None,
+                    help="composite launch shape 'ringKB,ctasPerSm' (default: the library's)")
+    ap.add_argument("--frames", type=int, default=N_FRAMES,
+                    help="distinct resident frames (the 16-frame step cycles through them); "
+                         "fewer frames only to keep profiler captures small")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -336,12 +343,13 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    sc, frames, depth, alpha = build_workload(0, dev)
+    sc, frames, depth, alpha = build_workload(0, dev, max(1, min(args.frames, N_FRAMES)))
     fpx_frame = sc.fragment_pixels()
     hbm_peak, peak_kind = peaks()
 
     # ---- FP32 headline ----
-    run = Runner(sc, frames, depth, D.DFB_F32)
+    tune = tuple(int(v) for v in args.tune.split(",")) if args.tune else None
+    run = Runner(sc, frames, depth, D.DFB_F32, tune=tune)
     sampler = ClockSampler(local) if rank == 0 else None
     ms, tm, clocks, launches = timed(run, args.steps, args.warmup, stream, dist, sampler)
     st = D.dfb_get_stats(run.h)
@@ -411,7 +419,7 @@ def main():
             dst = torch.empty(fr.numel(), dtype=torch.float16, device=dev)
             D.dfb_convert_tiles(fr, dst, None, sc.n, sc.T * sc.T, D.DFB_F16, stream)
             f16.append(dst)
-        r16 = Runner(sc, f16, depth, D.DFB_F16)
+        r16 = Runner(sc, f16, depth, D.DFB_F16, tune=tune)
         ms16, tm16, _, _ = timed(r16, args.steps, args.warmup, stream, dist, None)
         st16 = D.dfb_get_stats(r16.h)
         c16 = tm16["composite_ms"] / max(tm16["launches"], 1)

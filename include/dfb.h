@@ -65,11 +65,11 @@ enum dfb_mode {
 };
 
 /* Storage type of the submitted fragment RGBA (depth is always FP32). */
-enum dfb_dtype {
-  DFB_F32 = 0,     /* 4 x float32 per pixel, 16-byte aligned tiles          */
-  DFB_F16 = 1,     /* 4 x IEEE binary16 per pixel, 8-byte aligned           */
-  DFB_BF16 = 2,    /* 4 x bfloat16 per pixel, 8-byte aligned                */
-  DFB_FP8E4M3 = 3  /* 4 x e4m3 codes per pixel, 4-byte aligned; value =
+enum dfb_dtype {   /* every RGBA tile and depth plane must be 16-byte aligned */
+  DFB_F32 = 0,     /* 4 x float32 per pixel                                 */
+  DFB_F16 = 1,     /* 4 x IEEE binary16 per pixel                           */
+  DFB_BF16 = 2,    /* 4 x bfloat16 per pixel                                */
+  DFB_FP8E4M3 = 3  /* 4 x e4m3 codes per pixel; value =
                       decode(code) * the fragment's FP32 scale               */
 };
 
@@ -268,9 +268,9 @@ DFB_API int dfb_read_timing(dfb_handle h, dfb_timing* out, int reset);
    are caller-owned DEVICE buffers: color_out (W*H*4 floats) and/or rgba8_out
    (W*H uint32, sRGB of the frame colour); either may be NULL, not both.
    There is no accumulation or variance (those need resident state).
-   Scratch: a fixed device array of about 5.3 MB inside the library, held by
+   Scratch: a fixed device array of about 15 MB inside the library, held by
    every GPU that loads it until the process exits.  Limits: n <= 65536
-   fragment tiles and ceil(W/T)*ceil(H/T) <= 65536 tiles; larger requests
+   fragment tiles and ceil(W/T)*ceil(H/T) <= 16384 tiles; larger requests
    return DFB_ERR_CAPACITY before any GPU work.  The first call on a device
    looks up the array's device address (and uploads the sRGB table) with that
    device current; make that first call before any stream capture.  All calls
@@ -286,6 +286,22 @@ DFB_API int dfb_composite_noalloc(int width, int height, int tile_size, int mode
                                   const void* const* rgba, const float* const* depth,
                                   const float* scales, const float* background,
                                   float* color_out, uint32_t* rgba8_out, void* stream);
+
+/* Launch shape of this handle's composite kernel: shared-memory ring size per
+   CTA in KB (how many work items are in flight) and persistent CTAs per SM
+   (1 or 2).  0, 0 restores the library default.  Values that do not fit the
+   device are clamped at launch.  Errors: INVALID_ARG. */
+DFB_API int dfb_set_tuning(dfb_handle h, int ring_kb, int ctas_per_sm);
+
+/* Bound on every wait inside the composite kernel (default 2 s).  A wait
+   that runs out makes the kernel give up, and the next dfb_sync (or host
+   read) returns DFB_ERR_TIMEOUT.  Errors: INVALID_ARG (<= 0 or > 3600). */
+DFB_API int dfb_set_wait_limit(dfb_handle h, double seconds);
+
+/* Fault injection for tests of the timeout path: the next end-of-frame
+   launch of this handle never fills work item `item` (-1: off), so its
+   consumers' wait runs out after the wait limit.  Errors: INVALID_ARG. */
+DFB_API int dfb_inject_stall(dfb_handle h, int item);
 
 /* Human-readable name of a status code (static storage). */
 DFB_API const char* dfb_error_string(int status);

@@ -16,8 +16,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdfb.so")
-SOURCES = ["dfb_kernels.cu", "dfb_api.cu", "dfb_noalloc.cu"]
-HEADERS = [os.path.join(CSRC, "dfb_internal.h"), os.path.join(ROOT, "include", "dfb.h")]
+SOURCES = ["dfb_composite.cu", "dfb_kernels.cu", "dfb_api.cu", "dfb_noalloc.cu"]
+HEADERS = [os.path.join(CSRC, "dfb_internal.h"), os.path.join(CSRC, "dfb_device.cuh"),
+           os.path.join(ROOT, "include", "dfb.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -23,6 +23,15 @@ cudaError_t upload_srgb_table(const float* host256);
 using dfb::FragRec;
 using dfb::FrameArgs;
 
+// What one frame uploads ahead of its records: the frame's arguments and the
+// work-item prefix of a one-frame launch.  A multiple of 32 bytes so the
+// records that follow stay aligned.
+struct FrameHeader {
+  FrameArgs fa;
+  int itemBase[2];
+};
+constexpr size_t kHdrBytes = (sizeof(FrameHeader) + 31) / 32 * 32;
+
 namespace {
 
 constexpr int kVersion = 10000;  // 1.0.0
@@ -116,13 +125,20 @@ struct dfb_ctx {
   float4 *color = nullptr, *accum = nullptr, *comp = nullptr, *m2 = nullptr;
   uint32_t* rgba8 = nullptr;
   float *tileVar = nullptr, *varPartial = nullptr;
-  unsigned* tileDone = nullptr;
   int *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
-  FragRec* dRecs = nullptr;
-  uint32_t *tmp = nullptr, *sorted = nullptr;
+  unsigned char* dStage = nullptr;  // [FrameHeader][FragRec x recCap], uploaded per frame
+  FragRec* dRecs = nullptr;         // = dStage + sizeof(FrameHeader)
+  uint32_t* tmp = nullptr;
+  FragRec* srecs = nullptr;         // records sorted per tile (bucketing output)
+  dfb::TileBlock* blocks = nullptr; // per-tile count/offset/first records
   size_t recCap = 0;
+  unsigned* errFlag = nullptr;      // device error word of this handle's launches
+  unsigned* lastErr = nullptr;      // error word the last launch touching this handle used
+  dfb::TuneParams tune{0, 0};       // {0,0}: the library default
+  unsigned long long waitNs = 2000000000ull;  // bound on every device-side wait
+  int stallItem = -1;               // fault injection for tests (next launch only)
   float4* readTmp = nullptr;  // normalise / variance output for host reads
-  FragRec* hRecs[2] = {nullptr, nullptr};  // pinned staging (double buffered)
+  unsigned char* hRecs[2] = {nullptr, nullptr};  // pinned staging (double buffered)
   size_t hRecCap[2] = {0, 0};
   cudaEvent_t hRecDone[2] = {nullptr, nullptr};
   int hRecBuf = 0;
@@ -185,21 +201,24 @@ cudaError_t dalloc(T** p, size_t count) {
 }
 
 int grow_records(dfb_ctx* h, size_t need) {
-  if (need <= h->recCap) return DFB_OK;
+  if (need <= h->recCap && h->dStage) return DFB_OK;
   size_t cap = h->recCap ? h->recCap : 4096;
   while (cap < need) cap *= 2;
   // The previous frame may still read the old arrays.
   if (h->lastStreamSet) cudaEventSynchronize(h->frameDone);
-  cudaFree(h->dRecs);
+  cudaFree(h->dStage);
   cudaFree(h->tmp);
-  cudaFree(h->sorted);
+  cudaFree(h->srecs);
+  h->dStage = nullptr;
   h->dRecs = nullptr;
-  h->tmp = h->sorted = nullptr;
+  h->tmp = nullptr;
+  h->srecs = nullptr;
   h->recCap = 0;
-  cudaError_t e = dalloc(&h->dRecs, cap);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&h->dStage), kHdrBytes + sizeof(FragRec) * cap);
   if (e == cudaSuccess) e = dalloc(&h->tmp, cap);
-  if (e == cudaSuccess) e = dalloc(&h->sorted, cap);
+  if (e == cudaSuccess) e = dalloc(&h->srecs, cap);
   if (e != cudaSuccess) return cuda_status(e);
+  h->dRecs = reinterpret_cast<FragRec*>(h->dStage + kHdrBytes);
   h->recCap = cap;
   return DFB_OK;
 }
@@ -211,7 +230,8 @@ int grow_staging(dfb_ctx* h, int buf, size_t need) {
   if (h->hRecs[buf]) cudaFreeHost(h->hRecs[buf]);
   h->hRecs[buf] = nullptr;
   h->hRecCap[buf] = 0;
-  cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&h->hRecs[buf]), sizeof(FragRec) * cap);
+  cudaError_t e =
+      cudaMallocHost(reinterpret_cast<void**>(&h->hRecs[buf]), kHdrBytes + sizeof(FragRec) * cap);
   if (e != cudaSuccess) return DFB_ERR_OOM;
   h->hRecCap[buf] = cap;
   return DFB_OK;
@@ -224,9 +244,10 @@ void free_device(dfb_ctx* h) {
     p = nullptr;
   };
   fr(h->color); fr(h->accum); fr(h->comp); fr(h->m2); fr(h->rgba8);
-  fr(h->tileVar); fr(h->varPartial); fr(h->tileDone);
+  fr(h->tileVar); fr(h->varPartial);
   fr(h->counts); fr(h->offsets); fr(h->cursor);
-  fr(h->dRecs); fr(h->tmp); fr(h->sorted); fr(h->readTmp);
+  fr(h->dStage); fr(h->tmp); fr(h->srecs); fr(h->readTmp); fr(h->errFlag); fr(h->blocks);
+  h->dRecs = nullptr;
   h->recCap = 0;
   for (int b = 0; b < 2; ++b) {
     if (h->hRecs[b]) cudaFreeHost(h->hRecs[b]);
@@ -262,18 +283,20 @@ int allocate(dfb_ctx* h) {
   int st = ensure_table(dev);
   if (st != DFB_OK) return st;
   const size_t px = (size_t)h->cfg.width * h->cfg.height;
+  const size_t tpx = (size_t)h->nTiles * h->tilePixels;  // tile-major state covers whole tiles
   const unsigned f = h->cfg.flags;
   if (f & DFB_FLAG_WRITE_COLOR) e = dalloc(&h->color, px);
   if (e == cudaSuccess && (f & DFB_FLAG_ACCUMULATE)) {
-    e = dalloc(&h->accum, px);
-    if (e == cudaSuccess) e = dalloc(&h->comp, px);
-    if (e == cudaSuccess) e = dalloc(&h->m2, px);
+    e = dalloc(&h->accum, tpx);
+    if (e == cudaSuccess) e = dalloc(&h->comp, tpx);
+    if (e == cudaSuccess) e = dalloc(&h->m2, tpx);
   }
+  if (e == cudaSuccess) e = dalloc(&h->blocks, h->nTiles);
   if (e == cudaSuccess && (f & DFB_FLAG_PACK_RGBA8)) e = dalloc(&h->rgba8, px);
   if (e == cudaSuccess) e = dalloc(&h->tileVar, h->nTiles);
-  if (e == cudaSuccess) e = dalloc(&h->varPartial, (size_t)h->nTiles * h->chunks);
-  if (e == cudaSuccess) e = dalloc(&h->tileDone, h->nTiles);
-  if (e == cudaSuccess) e = cudaMemset(h->tileDone, 0, sizeof(unsigned) * h->nTiles);
+  if (e == cudaSuccess) e = dalloc(&h->varPartial, (size_t)h->nTiles * ((h->tilePixels + 31) / 32));
+  if (e == cudaSuccess) e = dalloc(&h->errFlag, 1);
+  if (e == cudaSuccess) e = cudaMemset(h->errFlag, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(h->tileVar, 0, sizeof(float) * h->nTiles);
   if (e == cudaSuccess) e = dalloc(&h->counts, h->nTiles);
   if (e == cudaSuccess) e = dalloc(&h->offsets, h->nTiles);
@@ -311,9 +334,8 @@ int validate_tile(const dfb_ctx* h, const dfb_tile_desc* t) {
   if (t->tile_id < 0 || t->tile_id >= h->nTiles) return DFB_ERR_TILE_RANGE;
   if (isnan(t->order_key)) return DFB_ERR_INVALID_ARG;
   if (!t->rgba || !t->depth) return DFB_ERR_INVALID_ARG;
-  const uintptr_t ra = (uintptr_t)t->rgba, da = (uintptr_t)t->depth;
-  const uintptr_t need = (uintptr_t)(4 * elt_bytes(h->cfg.dtype));
-  if ((ra % need) || (da % 4)) return DFB_ERR_INVALID_ARG;
+  // tiles are streamed with bulk copies, which need 16-byte aligned sources
+  if (((uintptr_t)t->rgba % 16) || ((uintptr_t)t->depth % 16)) return DFB_ERR_INVALID_ARG;
   if (t->generation < 1 || t->children < 0) return DFB_ERR_INVALID_ARG;
   if (h->cfg.dtype == DFB_FP8E4M3 && !(t->scale > 0.0f && isfinite(t->scale)))
     return DFB_ERR_INVALID_ARG;
@@ -440,15 +462,9 @@ int check_trees(const dfb_ctx* h) {
   return DFB_OK;
 }
 
-void fill_frame_args(const dfb_ctx* h, FrameArgs& a, int tileBase, const int* counts,
-                     const int* offsets, const FragRec* recs, const uint32_t* sorted) {
-  a.W = h->cfg.width;
-  a.H = h->cfg.height;
-  a.T = h->cfg.tile_size;
-  a.logT = h->logT;
-  a.tilesX = h->tilesX;
-  a.nTiles = h->nTiles;
-  a.chunks = h->chunks;
+void fill_frame_args(const dfb_ctx* h, FrameArgs& a, int tileBase, const FragRec* srecs,
+                     const dfb::TileBlock* blocks) {
+  dfb::frame_geometry(a, h->cfg.width, h->cfg.height, h->cfg.tile_size);
   a.tileBase = tileBase;
   a.mode = h->cfg.mode;
   a.dtype = h->cfg.dtype;
@@ -464,10 +480,8 @@ void fill_frame_args(const dfb_ctx* h, FrameArgs& a, int tileBase, const int* co
   a.bgG = h->bg[1] * h->bg[3];
   a.bgB = h->bg[2] * h->bg[3];
   a.bgA = h->bg[3];
-  a.recs = recs;
-  a.sorted = sorted;
-  a.counts = counts;
-  a.offsets = offsets;
+  a.srecs = srecs;
+  a.blocks = blocks;
   a.color = h->color;
   a.accum = h->accum;
   a.comp = h->comp;
@@ -475,7 +489,14 @@ void fill_frame_args(const dfb_ctx* h, FrameArgs& a, int tileBase, const int* co
   a.rgba8 = h->rgba8;
   a.tileVar = h->tileVar;
   a.varPartial = h->varPartial;
-  a.tileDone = h->tileDone;
+}
+
+dfb::TuneParams tune_of(const dfb_ctx* h) {
+  return h->tune.ringKB ? h->tune : dfb::default_tune(h->cfg.dtype);
+}
+
+dfb::LaunchCtl ctl_of(const dfb_ctx* h) {
+  return dfb::LaunchCtl{h->waitNs, h->stallItem, h->errFlag};
 }
 
 void finish_stats(dfb_ctx* h) {
@@ -502,15 +523,17 @@ void finish_stats(dfb_ctx* h) {
   s.kernel_launches = h->launches;
 }
 
-// Upload the open frame's records of handle h into staging slot, return pinned ptr.
+// Copy the open frame's records behind the header slot of a pinned staging
+// buffer; returns the slot index and the buffer start.
 int stage_records(dfb_ctx* h, FragRec** out) {
   const int buf = h->hRecBuf;
   h->hRecBuf ^= 1;
   cudaEventSynchronize(h->hRecDone[buf]);  // its previous upload has finished
   int st = grow_staging(h, buf, h->recs.size());
   if (st != DFB_OK) return st;
-  if (!h->recs.empty()) memcpy(h->hRecs[buf], h->recs.data(), sizeof(FragRec) * h->recs.size());
-  *out = h->hRecs[buf];
+  if (!h->recs.empty())
+    memcpy(h->hRecs[buf] + kHdrBytes, h->recs.data(), sizeof(FragRec) * h->recs.size());
+  *out = reinterpret_cast<FragRec*>(h->hRecs[buf]);
   return buf;
 }
 
@@ -559,7 +582,7 @@ int dfb_create_ex(const dfb_config* cfg, dfb_handle* out) {
   h->nTiles = h->tilesX * h->tilesY;
   h->logT = ilog2(T);
   h->tilePixels = T * T;
-  h->chunks = (h->tilePixels + dfb::kItemPixels - 1) / dfb::kItemPixels;
+  h->chunks = h->tilePixels < dfb::kItemPixels ? 1 : h->tilePixels / dfb::kItemPixels;
   h->rgbaBytes = (size_t)h->tilePixels * 4 * elt_bytes(cfg->dtype);
   h->depthBytes = (size_t)h->tilePixels * 4;
   h->declared.assign(h->nTiles, -1);
@@ -665,11 +688,10 @@ int dfb_submit_tiles(dfb_handle h, int n, const int* tile_ids, const float* orde
   const bool fp8 = h->cfg.dtype == DFB_FP8E4M3;
   if (fp8 && !scales) return DFB_ERR_INVALID_ARG;
   // validate everything first: nothing is submitted if an entry is bad
-  const uintptr_t ralign = (uintptr_t)(4 * elt_bytes(h->cfg.dtype));
   for (int i = 0; i < n; ++i) {
     if (tile_ids[i] < 0 || tile_ids[i] >= h->nTiles) return DFB_ERR_TILE_RANGE;
     if (isnan(order_keys[i]) || !rgba[i] || !depth[i]) return DFB_ERR_INVALID_ARG;
-    if (((uintptr_t)rgba[i] % ralign) || ((uintptr_t)depth[i] % 4)) return DFB_ERR_INVALID_ARG;
+    if (((uintptr_t)rgba[i] % 16) || ((uintptr_t)depth[i] % 16)) return DFB_ERR_INVALID_ARG;
     if (fp8 && !(scales[i] > 0.0f && isfinite(scales[i]))) return DFB_ERR_INVALID_ARG;
   }
   if (where != DFB_PTR_DEVICE) {
@@ -727,46 +749,41 @@ namespace {
 
 struct BatchRes {
   // Resources of multi-frame launches (one per process and device).
-  int device = -1;
   FragRec* dRecs = nullptr;
-  uint32_t *tmp = nullptr, *sorted = nullptr;
+  uint32_t* tmp = nullptr;
+  FragRec* srecs = nullptr;
   size_t recCap = 0;
   int *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
+  dfb::TileBlock* blocks = nullptr;
   size_t tileCap = 0;
   FrameArgs* dFrames = nullptr;
   int* dItemBase = nullptr;
   size_t frameCap = 0;
-  unsigned* queue = nullptr;
   FragRec* hRecs = nullptr;
-  size_t hRecCap = 0;
   FrameArgs* hFrames = nullptr;
   int* hItemBase = nullptr;
-  size_t hFrameCap = 0;
   cudaEvent_t done = nullptr;
   bool used = false;
 };
 
 std::mutex g_batch_mu;
 BatchRes g_batch[64];
-int g_ctas_per_sm = 0;
 
 int batch_reserve(BatchRes& b, size_t nRec, size_t nTiles, size_t nFrames) {
   cudaError_t e = cudaSuccess;
   if (!b.done) {
     e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&b.queue, sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(b.queue, 0, sizeof(unsigned));
     if (e != cudaSuccess) return cuda_status(e);
   }
   if (b.used) cudaEventSynchronize(b.done);  // last batch finished with the arrays
   if (nRec > b.recCap) {
     size_t cap = b.recCap ? b.recCap : 4096;
     while (cap < nRec) cap *= 2;
-    cudaFree(b.dRecs); cudaFree(b.tmp); cudaFree(b.sorted); cudaFreeHost(b.hRecs);
-    b.dRecs = nullptr; b.tmp = b.sorted = nullptr; b.hRecs = nullptr; b.recCap = 0;
+    cudaFree(b.dRecs); cudaFree(b.tmp); cudaFree(b.srecs); cudaFreeHost(b.hRecs);
+    b.dRecs = nullptr; b.tmp = nullptr; b.srecs = nullptr; b.hRecs = nullptr; b.recCap = 0;
     e = dalloc(&b.dRecs, cap);
     if (e == cudaSuccess) e = dalloc(&b.tmp, cap);
-    if (e == cudaSuccess) e = dalloc(&b.sorted, cap);
+    if (e == cudaSuccess) e = dalloc(&b.srecs, cap);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b.hRecs), sizeof(FragRec) * cap);
     if (e != cudaSuccess) return cuda_status(e);
     b.recCap = cap;
@@ -774,11 +791,12 @@ int batch_reserve(BatchRes& b, size_t nRec, size_t nTiles, size_t nFrames) {
   if (nTiles > b.tileCap) {
     size_t cap = b.tileCap ? b.tileCap : 4096;
     while (cap < nTiles) cap *= 2;
-    cudaFree(b.counts); cudaFree(b.offsets); cudaFree(b.cursor);
-    b.counts = b.offsets = b.cursor = nullptr; b.tileCap = 0;
+    cudaFree(b.counts); cudaFree(b.offsets); cudaFree(b.cursor); cudaFree(b.blocks);
+    b.counts = b.offsets = b.cursor = nullptr; b.blocks = nullptr; b.tileCap = 0;
     e = dalloc(&b.counts, cap);
     if (e == cudaSuccess) e = dalloc(&b.offsets, cap);
     if (e == cudaSuccess) e = dalloc(&b.cursor, cap);
+    if (e == cudaSuccess) e = dalloc(&b.blocks, cap);
     if (e != cudaSuccess) return cuda_status(e);
     b.tileCap = cap;
   }
@@ -831,6 +849,18 @@ cudaEvent_t* timing_slot(dfb_ctx* h) {
   return e;
 }
 
+// After the last frame's work has finished: report (and clear) a timed-out
+// device-side wait of the launch that served this handle.
+int take_device_error(dfb_ctx* h) {
+  if (!h->lastErr) return DFB_OK;
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpy(&v, h->lastErr, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (!v) return DFB_OK;
+  e = cudaMemset(h->lastErr, 0, sizeof(unsigned));
+  return e != cudaSuccess ? cuda_status(e) : DFB_ERR_TIMEOUT;
+}
+
 int end_one(dfb_ctx* h, cudaStream_t s) {
   FragRec* staged = nullptr;
   int st = grow_records(h, h->recs.size());
@@ -838,25 +868,35 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
   const int buf = stage_records(h, &staged);
   if (buf < 0) return buf;
   const size_t n = h->recs.size();
+  // header: the frame's arguments + the item prefix of a one-frame launch
+  FrameHeader* hdr = reinterpret_cast<FrameHeader*>(staged);
+  fill_frame_args(h, hdr->fa, 0, h->srecs, h->blocks);
+  hdr->itemBase[0] = 0;
+  hdr->itemBase[1] = h->nTiles * hdr->fa.chunks;
+  const int items = hdr->itemBase[1];
+  FrameArgs* dFa = reinterpret_cast<FrameArgs*>(h->dStage);
+  const int* dItemBase = reinterpret_cast<const int*>(h->dStage + offsetof(FrameHeader, itemBase));
   cudaError_t e = cudaSuccess;
   if (h->lastStreamSet && h->lastStream != s) e = cudaStreamWaitEvent(s, h->frameDone, 0);
   if (e == cudaSuccess && h->hostCopies) e = cudaStreamWaitEvent(s, h->copyDone, 0);
-  if (e == cudaSuccess && n)
-    e = cudaMemcpyAsync(h->dRecs, staged, sizeof(FragRec) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->dStage, staged, kHdrBytes + sizeof(FragRec) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaEventRecord(h->hRecDone[buf], s);
   cudaEvent_t* ev = timing_slot(h);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], s);
   if (e == cudaSuccess)
     e = dfb::launch_bucket(h->dRecs, (int)n, h->nTiles, h->counts, h->offsets, h->cursor, h->tmp,
-                           h->sorted, s);
-  if (e != cudaSuccess) return cuda_status(e);
-  FrameArgs a;
-  fill_frame_args(h, a, 0, h->counts, h->offsets, h->dRecs, h->sorted);
-  if (ev) e = cudaEventRecord(ev[1], s);
-  if (e == cudaSuccess) e = dfb::launch_composite(a, s);
+                           h->srecs, h->blocks, s);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+  if (e == cudaSuccess)
+    e = dfb::launch_composite(dFa, dItemBase, 1, items, h->nTiles,
+                              (h->cfg.flags & DFB_FLAG_ACCUMULATE) != 0, h->cfg.dtype, tune_of(h),
+                              ctl_of(h), s);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
   if (e == cudaSuccess) e = cudaEventRecord(h->frameDone, s);
-  h->launches += (n ? 4 : 1) + 1;
+  h->launches += (n ? 4 : 2) + ((h->cfg.flags & DFB_FLAG_ACCUMULATE) ? 2 : 1);
+  h->lastErr = h->errFlag;
+  h->stallItem = -1;
   return cuda_status(e);
 }
 
@@ -876,17 +916,19 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
   size_t r = 0;
   int tileBase = 0, items = 0;
   const int dtype = hs[0]->cfg.dtype;
+  bool anyAcc = false;
   for (int i = 0; i < n; ++i) {
     dfb_ctx* h = hs[i];
+    anyAcc |= (h->cfg.flags & DFB_FLAG_ACCUMULATE) != 0;
     for (const FragRec& fr : h->recs) {
       FragRec g = fr;
       g.tile += (uint32_t)tileBase;
       g.frame = (uint32_t)i;
       b.hRecs[r++] = g;
     }
-    fill_frame_args(h, b.hFrames[i], tileBase, b.counts, b.offsets, b.dRecs, b.sorted);
+    fill_frame_args(h, b.hFrames[i], tileBase, b.srecs, b.blocks);
     b.hItemBase[i] = items;
-    items += h->nTiles * h->chunks;
+    items += h->nTiles * b.hFrames[i].chunks;
     tileBase += h->nTiles;
     if (h->lastStreamSet && h->lastStream != s && e == cudaSuccess)
       e = cudaStreamWaitEvent(s, h->frameDone, 0);
@@ -903,16 +945,20 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], s);
   if (e == cudaSuccess)
     e = dfb::launch_bucket(b.dRecs, (int)nRec, (int)nTiles, b.counts, b.offsets, b.cursor, b.tmp,
-                           b.sorted, s);
+                           b.srecs, b.blocks, s);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
   if (e == cudaSuccess)
-    e = dfb::launch_composite_batch(b.dFrames, b.dItemBase, n, items, dtype, b.queue,
-                                    g_ctas_per_sm, s);
+    e = dfb::launch_composite(b.dFrames, b.dItemBase, n, items, tileBase, anyAcc, dtype,
+                              tune_of(hs[0]), ctl_of(hs[0]), s);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
   if (e == cudaSuccess) e = cudaEventRecord(b.done, s);
   b.used = true;
-  hs[0]->launches += (nRec ? 4 : 1) + 1;
-  for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventRecord(hs[i]->frameDone, s);
+  hs[0]->launches += (nRec ? 4 : 2) + (anyAcc ? 2 : 1);
+  hs[0]->stallItem = -1;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(hs[i]->frameDone, s);
+    hs[i]->lastErr = hs[0]->errFlag;
+  }
   return cuda_status(e);
 }
 
@@ -960,7 +1006,8 @@ int dfb_end_frames(const dfb_handle* hs, int n, void* stream) {
 int dfb_sync(dfb_handle h) {
   if (!h) return DFB_ERR_INVALID_ARG;
   if (!h->lastStreamSet) return DFB_OK;
-  return cuda_status(cudaEventSynchronize(h->frameDone));
+  const int st = cuda_status(cudaEventSynchronize(h->frameDone));
+  return st != DFB_OK ? st : take_device_error(h);
 }
 
 }  // extern "C"
@@ -974,7 +1021,8 @@ int copy_out(dfb_ctx* h, void* out, const void* src, size_t bytes) {
   const bool dev = is_device_ptr(out);
   cudaError_t e = cudaMemcpyAsync(out, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && !dev) e = cudaStreamSynchronize(s);
-  return cuda_status(e);
+  if (e != cudaSuccess) return cuda_status(e);
+  return dev ? DFB_OK : take_device_error(h);
 }
 
 int ensure_read_tmp(dfb_ctx* h) {
@@ -1010,8 +1058,9 @@ int dfb_read_accum(dfb_handle h, float* out) {
     dst = h->readTmp;
   }
   const int n = h->accumN;
-  cudaError_t e = dfb::launch_normalise(h->accum, h->comp, n > h->cfg.kahan_after ? 1 : 0,
-                                        1.0f / (float)n, dst, px, h->lastStream);
+  cudaError_t e = dfb::launch_tiles_to_image(h->accum, n > h->cfg.kahan_after ? h->comp : nullptr,
+                                             1.0f / (float)n, dst, h->cfg.width, h->cfg.height,
+                                             h->cfg.tile_size, h->lastStream);
   if (e != cudaSuccess) return cuda_status(e);
   if (dev) return DFB_OK;
   return copy_out(h, out, h->readTmp, sizeof(float4) * (size_t)px);
@@ -1031,7 +1080,8 @@ int dfb_read_variance(dfb_handle h, float* per_pixel, float* per_tile) {
       if (st != DFB_OK) return st;
       dst = h->readTmp;
     }
-    cudaError_t e = dfb::launch_variance(h->m2, invNm1, dst, px, h->lastStream);
+    cudaError_t e = dfb::launch_tiles_to_image(h->m2, nullptr, invNm1, dst, h->cfg.width,
+                                               h->cfg.height, h->cfg.tile_size, h->lastStream);
     if (e != cudaSuccess) return cuda_status(e);
     if (!dev) {
       const int st = copy_out(h, per_pixel, h->readTmp, sizeof(float4) * (size_t)px);
@@ -1055,20 +1105,36 @@ int dfb_get_tiles(dfb_handle h, int* tiles_x, int* tiles_y) {
   return DFB_OK;
 }
 
+// Tile-major state buffer -> caller's row-major image (host or device).
+int state_out(dfb_ctx* h, float* out, const float4* src) {
+  const bool dev = is_device_ptr(out);
+  float4* dst = dev ? reinterpret_cast<float4*>(out) : nullptr;
+  if (!dev) {
+    const int st = ensure_read_tmp(h);
+    if (st != DFB_OK) return st;
+    dst = h->readTmp;
+  }
+  cudaError_t e = dfb::launch_tiles_to_image(src, nullptr, 1.0f, dst, h->cfg.width, h->cfg.height,
+                                             h->cfg.tile_size, h->lastStream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (dev) return DFB_OK;
+  return copy_out(h, out, h->readTmp, sizeof(float4) * (size_t)h->cfg.width * h->cfg.height);
+}
+
 int dfb_save_accum(dfb_handle h, float* sum, float* comp, float* m2, int* frames) {
   if (!h || !sum || !comp || !m2 || !frames) return DFB_ERR_INVALID_ARG;
   if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
   const size_t bytes = sizeof(float4) * (size_t)h->cfg.width * h->cfg.height;
-  int st = copy_out(h, sum, h->accum, bytes);
+  int st = state_out(h, sum, h->accum);
   if (st == DFB_OK) {
-    if (h->accumN > h->cfg.kahan_after) st = copy_out(h, comp, h->comp, bytes);
+    if (h->accumN > h->cfg.kahan_after) st = state_out(h, comp, h->comp);
     else {
       const bool dev = is_device_ptr(comp);
       if (dev) st = cuda_status(cudaMemsetAsync(comp, 0, bytes, h->lastStream));
       else memset(comp, 0, bytes);
     }
   }
-  if (st == DFB_OK) st = copy_out(h, m2, h->m2, bytes);
+  if (st == DFB_OK) st = state_out(h, m2, h->m2);
   if (st == DFB_OK) *frames = h->accumN;
   return st;
 }
@@ -1078,12 +1144,19 @@ int dfb_load_accum(dfb_handle h, const float* sum, const float* comp, const floa
   if (!h || !sum || !comp || !m2 || frames < 1) return DFB_ERR_INVALID_ARG;
   if (h->inFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
   int st = allocate(h);
+  if (st == DFB_OK) st = ensure_read_tmp(h);
   if (st != DFB_OK) return st;
   const size_t bytes = sizeof(float4) * (size_t)h->cfg.width * h->cfg.height;
   cudaStream_t s = h->lastStreamSet ? h->lastStream : (cudaStream_t)0;
-  cudaError_t e = cudaMemcpyAsync(h->accum, sum, bytes, cudaMemcpyDefault, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->comp, comp, bytes, cudaMemcpyDefault, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->m2, m2, bytes, cudaMemcpyDefault, s);
+  const float* srcs[3] = {sum, comp, m2};
+  float4* dsts[3] = {h->accum, h->comp, h->m2};
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+    e = cudaMemcpyAsync(h->readTmp, srcs[i], bytes, cudaMemcpyDefault, s);
+    if (e == cudaSuccess)
+      e = dfb::launch_image_to_tiles(h->readTmp, dsts[i], h->cfg.width, h->cfg.height,
+                                     h->cfg.tile_size, s);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_status(e);
   h->accumN = frames;
@@ -1115,6 +1188,26 @@ int dfb_read_timing(dfb_handle h, dfb_timing* out, int reset) {
   }
   *out = h->tSum;
   if (reset) h->tSum = dfb_timing{};
+  return DFB_OK;
+}
+
+int dfb_set_tuning(dfb_handle h, int ring_kb, int ctas_per_sm) {
+  if (!h || ring_kb < 0 || ring_kb > 227 || ctas_per_sm < 0 || ctas_per_sm > 2)
+    return DFB_ERR_INVALID_ARG;
+  if ((ring_kb == 0) != (ctas_per_sm == 0)) return DFB_ERR_INVALID_ARG;
+  h->tune = dfb::TuneParams{ring_kb, ctas_per_sm};
+  return DFB_OK;
+}
+
+int dfb_set_wait_limit(dfb_handle h, double seconds) {
+  if (!h || !(seconds > 0.0) || seconds > 3600.0) return DFB_ERR_INVALID_ARG;
+  h->waitNs = (unsigned long long)(seconds * 1e9);
+  return DFB_OK;
+}
+
+int dfb_inject_stall(dfb_handle h, int item) {
+  if (!h || item < -1) return DFB_ERR_INVALID_ARG;
+  h->stallItem = item;
   return DFB_OK;
 }
 

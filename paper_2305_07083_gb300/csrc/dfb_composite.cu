@@ -1,0 +1,687 @@
+// Composite kernel of the DFB path (K2/K3 with the fused K4 epilogue) for
+// sm_103a: a persistent, warp-specialised, bulk-copy pipeline.
+//
+// Per pixel it computes the AlphaBlend tile operation of Sec. 4.2 /
+// Listing 4 (sort the pixel's fragments by depth -- ties by order key, then
+// submit index -- and blend them front to back with the premultiplied "over"
+// operator, then the generation-0 background of Listing 3), the ordered
+// "list" form of Sec. 4.2 (blend in key order), or depth compositing
+// (Sec. 2.1: the nearest fragment's RGBA).  The epilogue updates the
+// progressive accumulation and variance tiles of Listing 1 (running sum,
+// Kahan-compensated past a threshold; Welford M2; per-tile variance for
+// Sec. 4.1.1) and writes the RGBA8 display format of Sec. 3.1.
+//
+// The work is bound by HBM bandwidth (~0.4 flop per byte), so the design goal
+// is to keep enough bytes in flight:
+//   * CTA = 2 consumer groups of 8 warps (one pixel per thread, 256 pixels =
+//     one work item; the groups take alternate items) + 1 producer warp.
+//     CTAs are persistent and walk the work items of all frames of the
+//     launch with a static stride.
+//   * The producer warp fetches each item's tile block (fragment count,
+//     list offset and sorted records, written by the bucketing) with one bulk
+//     copy kMetaQ items ahead, so locating an item's fragments needs no
+//     dependent global loads.  It then issues one-dimensional bulk copies
+//     (cp.async.bulk, the TMA engine) of each fragment's depth slab and RGBA
+//     slab straight into a shared-memory ring, completing on the item's
+//     mbarrier.  Items take only the ring bytes they need (n fragments x slab
+//     size), so the ring holds as many items in flight as their sizes allow,
+//     up to kSlots.
+//   * The accumulation state (sum, M2, Kahan compensation) is stored
+//     tile-major, so an item's state is one contiguous run per buffer that
+//     the producer streams into the same ring space; consumers read every
+//     input from shared memory: they sort and blend, run the epilogue, then
+//     release the ring space.
+//   * Items with more than kStageFragments fragments are streamed from HBM
+//     by the consumers in rounds of a per-pixel sort window (held in ring
+//     space the item reserves).
+//   * The epilogue writes one variance partial per warp with plain stores;
+//     a small second kernel sums each tile's partials in a fixed order.
+// Every wait is bounded in time; on expiry the kernel sets an error bit,
+// drains its own bulk copies and returns.
+#include "dfb_device.cuh"
+#include "dfb_internal.h"
+
+namespace dfb {
+
+// sRGB code boundaries: code c (1..255) starts at linear value g_srgb_thr[c-1];
+// g_srgb_thr[255] = +inf.  Uploaded by the host from the inverse of the
+// IEC 61966-2-1 curve evaluated in double.
+__device__ float g_srgb_thr[256];
+
+cudaError_t upload_srgb_table(const float* host256) {
+  return cudaMemcpyToSymbol(g_srgb_thr, host256, sizeof(float) * 256);
+}
+
+namespace {
+
+constexpr int kP = kItemPixels;          // pixels per item = threads of a consumer group
+constexpr int kCW = kP / 32;             // warps of a consumer group
+constexpr int kGroups = 2;               // consumer groups: items k, k+1 in parallel
+constexpr int kThreads = kGroups * kP + 32;  // + the producer warp
+constexpr int kN = kStageFragments;
+constexpr int kSlots = 16;               // items in flight at most
+constexpr int kMetaQ = 8;                // tile blocks fetched ahead
+constexpr uint32_t kWindowBytes = kSortWindow * kP * 8;
+
+struct ItemMeta {
+  int frame, tile, chunk, n, off, staged;
+  uint32_t start;      // byte offset of the item's data in the ring
+  uint32_t stateOff;   // offset of the item's state rows from `start`
+  unsigned long long end;  // producer's head position after this item
+  const void* rgba[kN];
+  float scale[kN];
+};
+static_assert(sizeof(ItemMeta) <= 256, "item meta");
+
+// Shared memory: [sRGB table 1 KB][barriers 512 B][flags 128 B][metas 4 KB]
+//                [tile-block queue][ring]
+constexpr int kOffBars = 1024;
+constexpr int kOffFlags = kOffBars + 512;
+constexpr int kOffMetas = kOffFlags + 128;
+constexpr int kOffQueue = kOffMetas + kSlots * 256;
+constexpr int kHeader = kOffQueue + kMetaQ * (int)sizeof(TileBlock);
+static_assert((2 * kSlots + kMetaQ) * 8 <= 512, "barrier space");
+static_assert(kOffQueue % 128 == 0 && kHeader % 128 == 0, "alignment");
+
+template <int DT>
+struct Bytes {
+  static constexpr int px = PxBytes<DT>::value;
+  // largest item the ring must hold: a staged item or a sort window, plus
+  // three rows of framebuffer state (sum, M2, Kahan compensation)
+  static constexpr uint32_t frag =
+      (uint32_t)kN * kP * (4 + px) > kWindowBytes ? (uint32_t)kN * kP * (4 + px) : kWindowBytes;
+  static constexpr uint32_t maxItem = frag + 3u * kP * 16u;
+};
+
+__device__ __forceinline__ int find_frame(const int* itemBase, int nFrames, int item) {
+  int lo = 0, hi = nFrames - 1;  // last frame whose first item <= item
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(itemBase + mid) <= item) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Bounded wait on an mbarrier phase.  Returns false when the wait expired or
+// another role of the CTA has given up.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, const LaunchCtl& ctl,
+                                           volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t spin = 1;; ++spin) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((spin & 63) == 0) {
+      if (*abort) return false;
+      if (global_ns() - t0 > ctl.waitNs) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void give_up(const LaunchCtl& ctl, volatile int* abort) {
+  *abort = 1;
+  atomicOr(ctl.err, 1u);
+}
+
+// Insert k into the sorted per-thread window kb[0..m-1] (stride kP),
+// shifting larger keys up one slot; slot m must be free.
+__device__ __forceinline__ void window_insert(uint64_t* kb, int m, uint64_t k) {
+  int j = m - 1;
+  while (j >= 0) {
+    const uint64_t v = kb[j * kP];
+    if (v < k) break;
+    kb[(j + 1) * kP] = v;
+    --j;
+  }
+  kb[(j + 1) * kP] = k;
+}
+
+// Where a work item lies: frame, frame-local tile, chunk, global tile.
+struct ItemLoc {
+  int f, tile, chunk, gt;
+};
+
+__device__ __forceinline__ ItemLoc locate(const FrameArgs* frames, const int* itemBase,
+                                          int nFrames, int item) {
+  ItemLoc L;
+  L.f = find_frame(itemBase, nFrames, item);
+  const FrameArgs* A = frames + L.f;
+  const int local = item - __ldg(itemBase + L.f);
+  L.tile = local >> A->logChunks;
+  L.chunk = local & (A->chunks - 1);
+  L.gt = A->tileBase + L.tile;
+  return L;
+}
+
+// ---------------------------------------------------------------------------
+// producer warp
+// ---------------------------------------------------------------------------
+template <int DT>
+__device__ void producer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
+                         int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
+                         uint32_t ringBytes, ItemMeta* metas, TileBlock* queue, uint64_t* fullB,
+                         uint64_t* emptyB, uint64_t* queueB, volatile int* abort) {
+  constexpr int px = Bytes<DT>::px;
+  const int lane = threadIdx.x & 31;
+  unsigned long long head = 0, tail = 0;  // monotonic ring positions
+  int tailItem = 0;                       // oldest item not known to be released
+  uint32_t armed = 0, armedPar = 0;       // per ring slot: armed / parity of last arm
+  uint32_t qArmed = 0, qPar = 0;          // per queue slot
+  // tile block of local item kk -> queue slot kk % kMetaQ (lane 0)
+  auto fetch = [&](int kk) {
+    const int it = blockIdx.x + kk * (int)gridDim.x;
+    if (it >= totalItems || lane != 0) return;
+    const ItemLoc L = locate(frames, itemBase, nFrames, it);
+    const int q = kk % kMetaQ;
+    fence_proxy_async();  // the slot's previous block was read through the generic proxy
+    mbar_arrive_expect_tx(&queueB[q], (uint32_t)sizeof(TileBlock));
+    bulk_g2s(queue + q, frames[L.f].blocks + L.gt, (uint32_t)sizeof(TileBlock), &queueB[q]);
+    qArmed |= 1u << q;
+    qPar = (qPar & ~(1u << q)) | ((uint32_t)((kk / kMetaQ) & 1) << q);
+  };
+  for (int kk = 0; kk < kMetaQ; ++kk) fetch(kk);
+  bool ok = true;
+  int k = 0;
+  for (int item = blockIdx.x; item < totalItems; item += gridDim.x, ++k) {
+    const int q = k % kMetaQ;
+    if (!wait_phase(&queueB[q], (uint32_t)(k / kMetaQ) & 1u, ctl, abort)) {
+      ok = false;
+      break;
+    }
+    const TileBlock* blk = queue + q;
+    const int n = blk->n, off = blk->off;
+    FragRec r{};
+    if (lane < n && lane < kN) r = blk->recs[lane];
+    __syncwarp();
+    fetch(k + kMetaQ);  // every lane has read the slot
+    const ItemLoc cur = locate(frames, itemBase, nFrames, item);
+    const FrameArgs* A = frames + cur.f;
+    const int P = A->P, mode = A->mode, T = A->T;
+    const bool staged = n <= kN;
+    const uint32_t dBytes = mode != DFB_BLEND_ORDERED ? (uint32_t)P * 4u : 0u;
+    const uint32_t cBytes = mode != DFB_ZCOMPOSITE ? (uint32_t)P * px : 0u;
+    const uint32_t fragBytes = staged ? (uint32_t)n * (dBytes + cBytes)
+                                      : (mode == DFB_BLEND_DEPTH ? kWindowBytes : 0u);
+    // accumulation state of the item's pixels: one contiguous run per buffer
+    const bool loadState = (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1;
+    const int nState = loadState ? (A->kahan && !A->kahanFirst ? 3 : 2) : 0;
+    const uint32_t stateBytes = (uint32_t)P * 16u;
+    const uint32_t data = (staged ? (uint32_t)n * (dBytes + cBytes) : 0u) + nState * stateBytes;
+    const uint32_t need = fragBytes + (uint32_t)nState * stateBytes;  // multiple of 16
+    // ring space: no item straddles the end of the ring
+    if ((uint32_t)(head % ringBytes) + need > ringBytes) head += ringBytes - head % ringBytes;
+    const int s = k % kSlots;
+    while (tailItem < k && (tailItem <= k - kSlots || head + need - tail > ringBytes)) {
+      const int qq = tailItem % kSlots;
+      if (!wait_phase(&emptyB[qq], (uint32_t)(tailItem / kSlots) & 1u, ctl, abort)) {
+        ok = false;
+        break;
+      }
+      tail = metas[qq].end;
+      ++tailItem;
+    }
+    if (!ok) break;
+    if (tailItem == k) tail = head;  // nothing outstanding: the padding is free too
+    const uint32_t start = (uint32_t)(head % ringBytes);
+    head += need;
+    ItemMeta* meta = metas + s;
+    if (lane < n && lane < kN) {
+      meta->rgba[lane] = r.rgba;
+      meta->scale[lane] = r.scale;
+    }
+    if (lane == 0) {
+      meta->frame = cur.f;
+      meta->tile = cur.tile;
+      meta->chunk = cur.chunk;
+      meta->n = n;
+      meta->off = off;
+      meta->staged = staged ? 1 : 0;
+      meta->start = start;
+      meta->stateOff = fragBytes;
+      meta->end = head;
+    }
+    __syncwarp();
+    if (item != ctl.stallItem) {  // test fault injection: never signal this item
+      if (lane == 0) mbar_arrive_expect_tx(&fullB[s], data);
+      armed |= 1u << s;
+      armedPar = (armedPar & ~(1u << s)) | ((uint32_t)((k / kSlots) & 1) << s);
+      __syncwarp();
+      unsigned char* base = ring + start;
+      const size_t p0 = (size_t)cur.chunk * P;
+      if (staged && lane < n) {
+        if (dBytes) bulk_g2s(base + lane * dBytes, r.depth + p0, dBytes, &fullB[s]);
+        if (cBytes)
+          bulk_g2s(base + n * dBytes + lane * cBytes,
+                   static_cast<const unsigned char*>(r.rgba) + p0 * px, cBytes, &fullB[s]);
+      }
+      if (lane < nState) {
+        // state runs: [sum | M2 | comp], P pixels of 16 bytes each
+        const float4* src = lane == 0 ? A->accum : (lane == 1 ? A->m2 : A->comp);
+        bulk_g2s(base + fragBytes + lane * stateBytes, src + (size_t)cur.tile * T * T + p0,
+                 stateBytes, &fullB[s]);
+      }
+    }
+  }
+  if (!ok && lane == 0) give_up(ctl, abort);
+  // Leave no bulk copy in flight into this CTA's shared memory.
+  auto drain = [&](uint64_t* bars, uint32_t mask, uint32_t par, int count) {
+    for (int qq = 0; qq < count; ++qq)
+      if (mask & (1u << qq)) {
+        const uint64_t t0 = global_ns();
+        while (!mbar_try_wait(&bars[qq], (par >> qq) & 1u)) {
+          if (global_ns() - t0 > ctl.waitNs) {
+            if (lane == 0) atomicOr(ctl.err, 2u);
+            break;
+          }
+        }
+      }
+  };
+  drain(fullB, armed, armedPar, kSlots);
+  qArmed = __shfl_sync(0xffffffffu, qArmed, 0);
+  qPar = __shfl_sync(0xffffffffu, qPar, 0);
+  drain(queueB, qArmed, qPar, kMetaQ);
+}
+
+// ---------------------------------------------------------------------------
+// consumer warps: one pixel per thread
+// ---------------------------------------------------------------------------
+// Returns false only in DFB_ZCOMPOSITE for a pixel no fragment covers.
+template <int DT>
+__device__ __forceinline__ bool composite_staged(int mode, int n, int P, const unsigned char* base,
+                                                 const ItemMeta* meta, int t, int p,
+                                                 float& c0, float& c1, float& c2, float& al) {
+  constexpr int px = Bytes<DT>::px;
+  const float* sD = reinterpret_cast<const float*>(base);
+  const int dStride = mode != DFB_BLEND_ORDERED ? P : 0;  // floats per depth slab
+  const unsigned char* sC = base + (size_t)n * dStride * 4;
+  if (mode == DFB_BLEND_ORDERED) {
+    for (int i = 0; i < n; ++i) over(Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]), c0, c1, c2, al);
+  } else if (mode == DFB_ZCOMPOSITE) {
+    uint64_t best = ~0ull;
+    for (int i = 0; i < n; ++i) {
+      const uint64_t k = ((uint64_t)depth_bits(sD[i * P + t]) << 32) | (uint32_t)i;
+      best = k < best ? k : best;
+    }
+    if (n == 0 || (uint32_t)(best >> 32) == kInfBits) return false;
+    const int i = (int)(uint32_t)best;
+    const float4 f = Px<DT>::global(meta->rgba[i], p, meta->scale[i]);
+    c0 = f.x; c1 = f.y; c2 = f.z; al = f.w;
+  } else {
+    // Insertion sort of fragment indices (4-bit slots of `perm`) by depth
+    // key.  The list arrives in key order, so ties stay in (key, submit
+    // index) order, and for bricks whose key order is their depth order
+    // every step is an append.  Fragments empty at this pixel (depth +inf,
+    // which sort after every finite depth) go to a second list kept in list
+    // order and blended last, so they never cause an insertion.
+    uint64_t perm = 0, infs = 0;
+    int m = 0, mi = 0;
+    uint32_t lastKey = 0;
+    for (int i = 0; i < n; ++i) {
+      const uint32_t key = depth_bits(sD[i * P + t]);
+      const bool isInf = key == kInfBits;
+      const bool app = !isInf && (m == 0 || key >= lastKey);
+      if (!isInf && !app) {
+        // rare: depth order differs from key order at this pixel
+        int j = m - 1;
+        while (j > 0 && depth_bits(sD[(int)((perm >> (4 * (j - 1))) & 15u) * P + t]) > key) --j;
+        const uint64_t lowMask = (j == 0) ? 0ull : ((1ull << (4 * j)) - 1ull);
+        perm = (perm & lowMask) | ((uint64_t)i << (4 * j)) | ((perm & ~lowMask) << 4);
+        ++m;
+      }
+      // appends to either list without a branch
+      const uint64_t bit = (uint64_t)i << (4 * (isInf ? mi : m));
+      infs |= isInf ? bit : 0ull;
+      perm |= app ? bit : 0ull;
+      lastKey = app ? key : lastKey;
+      mi += isInf ? 1 : 0;
+      m += app ? 1 : 0;
+    }
+    // one loop of exactly n steps: the finite list, then the empty ones
+    for (int r = 0; r < n; ++r) {
+      const bool fin = r < m;
+      const uint64_t src = fin ? perm : infs;
+      const int rr = fin ? r : r - m;
+      const int i = (int)((src >> (4 * rr)) & 15u);
+      over(Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]), c0, c1, c2, al);
+    }
+  }
+  return true;
+}
+
+template <int DT>
+__device__ __forceinline__ bool composite_streamed(int mode, int n, const FragRec* list,
+                                                   uint64_t* kbAll, int t, int p,
+                                                   float& c0, float& c1, float& c2, float& al) {
+  if (mode == DFB_BLEND_ORDERED) {
+    for (int ib = 0; ib < n; ib += 8) {
+      float4 c[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (ib + u < n) c[u] = Px<DT>::global(list[ib + u].rgba, p, list[ib + u].scale);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (ib + u < n) over(c[u], c0, c1, c2, al);
+    }
+    return true;
+  }
+  if (mode == DFB_ZCOMPOSITE) {
+    uint64_t best = ~0ull;
+    for (int ib = 0; ib < n; ib += 8) {
+      float z[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) z[u] = (ib + u < n) ? __ldg(list[ib + u].depth + p) : 0.0f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (ib + u < n) {
+          const uint64_t k = ((uint64_t)depth_bits(z[u]) << 32) | (uint32_t)(ib + u);
+          best = k < best ? k : best;
+        }
+    }
+    if ((uint32_t)(best >> 32) == kInfBits) return false;
+    const int i = (int)(uint32_t)best;
+    const float4 f = Px<DT>::global(list[i].rgba, p, list[i].scale);
+    c0 = f.x; c1 = f.y; c2 = f.z; al = f.w;
+    return true;
+  }
+  // rounds: each round keeps the window's nearest keys above the last blended
+  uint64_t* kb = kbAll + t;
+  uint64_t lo = 0;
+  int done = 0;
+  while (done < n) {
+    int m = 0;
+    uint64_t last = 0;
+    for (int ib = 0; ib < n; ib += 8) {
+      float z[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) z[u] = (ib + u < n) ? __ldg(list[ib + u].depth + p) : 0.0f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = ib + u;
+        if (i < n) {
+          const uint64_t k = ((uint64_t)depth_bits(z[u]) << 32) | (uint32_t)i;
+          if (done == 0 || k > lo) {
+            if (m < kSortWindow) {
+              if (m == 0 || k > last) {
+                kb[m * kP] = k;
+                last = k;
+              } else {
+                window_insert(kb, m, k);
+              }
+              ++m;
+            } else if (k < last) {
+              window_insert(kb, kSortWindow - 1, k);  // drops the largest
+              last = kb[(kSortWindow - 1) * kP];
+            }
+          }
+        }
+      }
+    }
+    for (int r = 0; r < m; r += 4) {
+      float4 c[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (r + u < m) {
+          const int i = (int)(uint32_t)kb[(r + u) * kP];
+          c[u] = Px<DT>::global(list[i].rgba, p, list[i].scale);
+        }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (r + u < m) over(c[u], c0, c1, c2, al);
+    }
+    lo = last;
+    done += m;
+  }
+  return true;
+}
+
+// One pixel of one work item.
+struct PixWork {
+  const FrameArgs* A;
+  int tile, chunk, p, P;
+  bool active;
+  size_t pix;   // row-major image index
+  size_t sidx;  // tile-major state index
+};
+
+__device__ __forceinline__ PixWork prepare(const FrameArgs* frames, const int* itemBase,
+                                           int nFrames, int item, int t) {
+  PixWork w;
+  const int f = find_frame(itemBase, nFrames, item);
+  const FrameArgs* A = frames + f;
+  w.A = A;
+  const int local = item - __ldg(itemBase + f);
+  const int T = A->T;
+  w.P = A->P;
+  w.tile = local >> A->logChunks;
+  w.chunk = local & (A->chunks - 1);
+  // tile / tilesX without a division: (tile + 0.5) / tilesX is never within
+  // float rounding of an integer for tile counts below 2^20
+  const int ty = __float2int_rz(((float)w.tile + 0.5f) * A->invTilesX);
+  const int tx = w.tile - ty * A->tilesX;
+  w.p = w.chunk * w.P + t;
+  w.sidx = (size_t)w.tile * T * T + w.p;
+  const int x = tx * T + (w.p & (T - 1));
+  const int y = ty * T + (w.p >> A->logT);
+  w.active = (t < w.P) && (x < A->W) && (y < A->H);
+  w.pix = (size_t)y * A->W + x;
+  return w;
+}
+
+template <int DT>
+__device__ void consumer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
+                         int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
+                         ItemMeta* metas, uint64_t* fullB, uint64_t* emptyB, volatile int* abort,
+                         const float* thr) {
+  const int group = threadIdx.x / kP;
+  const int t = threadIdx.x - group * kP;  // pixel of the item, 0 .. kP-1
+  const int lane = t & 31, warp = t >> 5;
+  for (int k = group; ; k += kGroups) {
+    const int item = blockIdx.x + k * (int)gridDim.x;
+    if (item >= totalItems) break;
+    const int s = k % kSlots;
+    const PixWork w = prepare(frames, itemBase, nFrames, item, t);
+    const FrameArgs* A = w.A;
+    if (!wait_phase(&fullB[s], (uint32_t)(k / kSlots) & 1u, ctl, abort)) {
+      if (lane == 0) give_up(ctl, abort);
+      break;
+    }
+    const ItemMeta* meta = metas + s;
+    const int n = meta->n;
+    const int mode = A->mode;
+    const int P = w.P;
+    unsigned char* base = ring + meta->start;
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f, al = 0.f;
+    bool covered = true;
+    if (w.active) {
+      if (meta->staged)
+        covered = composite_staged<DT>(mode, n, P, base, meta, t, w.p, c0, c1, c2, al);
+      else
+        covered = composite_streamed<DT>(mode, n, A->srecs + meta->off,
+                                         reinterpret_cast<uint64_t*>(base), t, w.p, c0, c1, c2,
+                                         al);
+    }
+    const unsigned flags = A->flags;
+    const bool acc = (flags & DFB_FLAG_ACCUMULATE) != 0;
+    float vsum = 0.0f;
+    if (w.active) {
+      if (mode != DFB_ZCOMPOSITE) {
+        over(make_float4(A->bgR, A->bgG, A->bgB, A->bgA), c0, c1, c2, al);  // generation 0
+      } else if (!covered) {
+        c0 = A->bgR; c1 = A->bgG; c2 = A->bgB; al = A->bgA;
+      }
+      // ---- K4 epilogue ----
+      const float4 col = make_float4(c0, c1, c2, al);
+      if (flags & DFB_FLAG_WRITE_COLOR) A->color[w.pix] = col;
+      float4 out = col;
+      if (acc) {
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        // state rows were streamed into the ring unless this frame starts the
+        // accumulation
+        const float4* sState = reinterpret_cast<const float4*>(base + meta->stateOff);
+        const float4 S = A->frameN != 1 ? sState[t] : zero4;
+        float4 M = A->frameN != 1 ? sState[P + t] : zero4;
+        const float4 CP = (A->kahan && !A->kahanFirst) ? sState[2 * P + t] : zero4;
+        float4 Sn, tot;
+        if (A->kahan) {
+          float4 cn;
+#define DFB_KAHAN(ch)                 \
+  {                                   \
+    const float yk = col.ch - CP.ch;  \
+    const float tk = S.ch + yk;       \
+    cn.ch = (tk - S.ch) - yk;         \
+    Sn.ch = tk;                       \
+    tot.ch = tk - cn.ch;              \
+  }
+          DFB_KAHAN(x) DFB_KAHAN(y) DFB_KAHAN(z) DFB_KAHAN(w)
+#undef DFB_KAHAN
+          A->comp[w.sidx] = cn;
+        } else {
+          Sn = make_float4(S.x + col.x, S.y + col.y, S.z + col.z, S.w + col.w);
+          tot = Sn;
+        }
+        const float iN = A->invN, iN1 = A->invNm1;
+        const float4 mean = make_float4(tot.x * iN, tot.y * iN, tot.z * iN, tot.w * iN);
+        if (A->frameN != 1) {
+          // Welford: M2 += (x - mean_{n-1}) (x - mean_n), mean_{n-1} = S_{n-1}/(n-1)
+          M.x = fmaf(col.x - S.x * iN1, col.x - mean.x, M.x);
+          M.y = fmaf(col.y - S.y * iN1, col.y - mean.y, M.y);
+          M.z = fmaf(col.z - S.z * iN1, col.z - mean.z, M.z);
+          M.w = fmaf(col.w - S.w * iN1, col.w - mean.w, M.w);
+        }
+        A->accum[w.sidx] = Sn;
+        A->m2[w.sidx] = M;
+        vsum = (M.x + M.y + M.z) * iN1;
+        out = mean;
+      }
+      if (flags & DFB_FLAG_PACK_RGBA8) A->rgba8[w.pix] = pack_rgba8(out, thr);
+    }
+    if (acc && warp * 32 < P) {
+      // one partial per warp of 32 pixels, summed per tile by k_tile_variance
+      float v = vsum;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0)
+        A->varPartial[(size_t)w.tile * A->slots + ((w.chunk * P + warp * 32) >> 5)] = v;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&emptyB[s]);  // ring space free for the producer
+  }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads, 1) k_composite(const FrameArgs* __restrict__ frames,
+                                                        const int* __restrict__ itemBase,
+                                                        int nFrames, int totalItems,
+                                                        uint32_t ringBytes, LaunchCtl ctl) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* thr = reinterpret_cast<float*>(smem);
+  uint64_t* fullB = reinterpret_cast<uint64_t*>(smem + kOffBars);
+  uint64_t* emptyB = fullB + kSlots;
+  volatile int* abort = reinterpret_cast<volatile int*>(smem + kOffFlags);
+  ItemMeta* metas = reinterpret_cast<ItemMeta*>(smem + kOffMetas);
+  TileBlock* queue = reinterpret_cast<TileBlock*>(smem + kOffQueue);
+  uint64_t* queueB = emptyB + kSlots;
+  unsigned char* ring = smem + kHeader;
+  for (int i = threadIdx.x; i < 256; i += kThreads) thr[i] = g_srgb_thr[i];
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kSlots; ++q) {
+      mbar_init(&fullB[q], 1);
+      mbar_init(&emptyB[q], kCW);
+    }
+    for (int q = 0; q < kMetaQ; ++q) mbar_init(&queueB[q], 1);
+    *abort = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x >= kGroups * kP)
+    producer<DT>(frames, itemBase, nFrames, totalItems, ctl, ring, ringBytes, metas, queue, fullB,
+                 emptyB, queueB, abort);
+  else
+    consumer<DT>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
+                 thr);
+}
+
+// Per-tile variance: one warp per global tile sums the tile's per-warp
+// partials in slot order.
+__global__ void k_tile_variance(const FrameArgs* __restrict__ frames, int nFrames,
+                                int totalTiles) {
+  const int gt = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (gt >= totalTiles) return;
+  int lo = 0, hi = nFrames - 1;  // frame with the largest tileBase <= gt
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (frames[mid].tileBase <= gt) lo = mid; else hi = mid - 1;
+  }
+  const FrameArgs* A = frames + lo;
+  if (!(A->flags & DFB_FLAG_ACCUMULATE)) return;
+  const int tile = gt - A->tileBase;
+  const int slots = A->slots;
+  float sum = 0.0f;
+  for (int q = lane; q < slots; q += 32) sum += A->varPartial[(size_t)tile * slots + q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) {
+    const int T = A->T;
+    const int tx = tile % A->tilesX, ty = tile / A->tilesX;
+    const int w = min(T, A->W - tx * T), h = min(T, A->H - ty * T);
+    A->tileVar[tile] = sum / (3.0f * (float)(w * h));
+  }
+}
+
+template <int DT>
+cudaError_t launch_dt(const FrameArgs* frames, const int* itemBase, int nFrames, int totalItems,
+                      const TuneParams& tune, const LaunchCtl& ctl, cudaStream_t s) {
+  auto kern = k_composite<DT>;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  static int sms[64] = {0};
+  static int smemMax[64] = {0};
+  if (!sms[dev]) {
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) {
+      sms[dev] = 0;
+      return e;
+    }
+    smemMax[dev] = optin;
+  }
+  const int per = tune.ctasPerSm > 1 ? 2 : 1;
+  uint32_t ring = (uint32_t)tune.ringKB * 1024u;
+  const uint32_t cap = (uint32_t)((smemMax[dev] / per) - kHeader - 1024) & ~127u;
+  if (ring > cap) ring = cap;
+  if (ring < Bytes<DT>::maxItem) return cudaErrorInvalidConfiguration;
+  int grid = sms[dev] * per;
+  if (grid > totalItems) grid = totalItems;
+  if (grid < 1) return cudaSuccess;
+  kern<<<grid, kThreads, kHeader + ring, s>>>(frames, itemBase, nFrames, totalItems, ring, ctl);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+TuneParams default_tune(int dtype) {
+  (void)dtype;
+  return TuneParams{160, 1};
+}
+
+cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int nFrames,
+                             int totalItems, int totalTiles, bool accumulate, int dtype,
+                             const TuneParams& tune, const LaunchCtl& ctl, cudaStream_t s) {
+  cudaError_t e;
+  switch (dtype) {
+    case DFB_F32: e = launch_dt<DFB_F32>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
+    case DFB_F16: e = launch_dt<DFB_F16>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
+    case DFB_BF16: e = launch_dt<DFB_BF16>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
+    default: e = launch_dt<DFB_FP8E4M3>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
+  }
+  if (e != cudaSuccess || !accumulate || totalTiles < 1) return e;
+  k_tile_variance<<<(totalTiles * 32 + 255) / 256, 256, 0, s>>>(frames, nFrames, totalTiles);
+  return cudaGetLastError();
+}
+
+}  // namespace dfb

@@ -1,0 +1,201 @@
+// Device helpers shared by the DFB kernels: order-preserving depth keys,
+// storage-format decoders, the front-to-back "over" step, the sRGB pack and
+// the mbarrier / bulk-copy PTX wrappers used by the pipelined composite.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "dfb_internal.h"
+
+namespace dfb {
+
+// Order-preserving 32-bit image of a depth: NaN reads as +inf, -0 as +0.
+__device__ __forceinline__ uint32_t depth_bits(float z) {
+  uint32_t b = __float_as_uint(z);
+  if ((b & 0x7fffffffu) > 0x7f800000u) b = 0x7f800000u;
+  if (b == 0x80000000u) b = 0u;
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+constexpr uint32_t kInfBits = 0xff800000u;  // depth_bits(+inf)
+
+__device__ __forceinline__ float2 e4m3x2_to_float2(uint32_t two_codes) {
+  uint32_t h2;
+  const unsigned short v = (unsigned short)(two_codes & 0xffffu);
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(v));
+  return make_float2(__half2float(__ushort_as_half((unsigned short)(h2 & 0xffffu))),
+                     __half2float(__ushort_as_half((unsigned short)(h2 >> 16))));
+}
+
+// Bytes of one pixel's RGBA in each storage dtype.
+template <int DT>
+struct PxBytes {
+  static constexpr int value = DT == DFB_F32 ? 16 : (DT == DFB_FP8E4M3 ? 4 : 8);
+};
+
+// Decode pixel p of a fragment's RGBA (global or shared memory) to FP32.
+template <int DT>
+struct Px;
+
+template <>
+struct Px<DFB_F32> {
+  static __device__ __forceinline__ float4 global(const void* base, int p, float) {
+    return __ldg(reinterpret_cast<const float4*>(base) + p);
+  }
+  static __device__ __forceinline__ float4 shared(const unsigned char* base, int p, float) {
+    return reinterpret_cast<const float4*>(base)[p];
+  }
+};
+
+__device__ __forceinline__ float4 decode_f16(uint2 v) {
+  return make_float4(__half2float(__ushort_as_half((unsigned short)(v.x & 0xffffu))),
+                     __half2float(__ushort_as_half((unsigned short)(v.x >> 16))),
+                     __half2float(__ushort_as_half((unsigned short)(v.y & 0xffffu))),
+                     __half2float(__ushort_as_half((unsigned short)(v.y >> 16))));
+}
+
+template <>
+struct Px<DFB_F16> {
+  static __device__ __forceinline__ float4 global(const void* base, int p, float) {
+    return decode_f16(__ldg(reinterpret_cast<const uint2*>(base) + p));
+  }
+  static __device__ __forceinline__ float4 shared(const unsigned char* base, int p, float) {
+    return decode_f16(reinterpret_cast<const uint2*>(base)[p]);
+  }
+};
+
+__device__ __forceinline__ float4 decode_bf16(uint2 v) {
+  return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
+                     __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+}
+
+template <>
+struct Px<DFB_BF16> {
+  static __device__ __forceinline__ float4 global(const void* base, int p, float) {
+    return decode_bf16(__ldg(reinterpret_cast<const uint2*>(base) + p));
+  }
+  static __device__ __forceinline__ float4 shared(const unsigned char* base, int p, float) {
+    return decode_bf16(reinterpret_cast<const uint2*>(base)[p]);
+  }
+};
+
+__device__ __forceinline__ float4 decode_fp8(uint32_t v, float scale) {
+  const float2 rg = e4m3x2_to_float2(v);
+  const float2 ba = e4m3x2_to_float2(v >> 16);
+  return make_float4(rg.x * scale, rg.y * scale, ba.x * scale, ba.y * scale);
+}
+
+template <>
+struct Px<DFB_FP8E4M3> {
+  static __device__ __forceinline__ float4 global(const void* base, int p, float scale) {
+    return decode_fp8(__ldg(reinterpret_cast<const unsigned int*>(base) + p), scale);
+  }
+  static __device__ __forceinline__ float4 shared(const unsigned char* base, int p, float scale) {
+    return decode_fp8(reinterpret_cast<const unsigned int*>(base)[p], scale);
+  }
+};
+
+// Front-to-back "over": the fragment goes behind what is accumulated.
+__device__ __forceinline__ void over(float4 f, float& c0, float& c1, float& c2, float& al) {
+  const float t = 1.0f - al;
+  c0 = fmaf(t, f.x, c0);
+  c1 = fmaf(t, f.y, c1);
+  c2 = fmaf(t, f.z, c2);
+  al = fmaf(t, f.w, al);
+}
+
+// Number of sRGB code boundaries <= x (NaN compares false -> code 0).
+__device__ __forceinline__ uint32_t srgb_code(float x, const float* thr) {
+  uint32_t c = 0;
+#pragma unroll
+  for (uint32_t s = 128; s >= 1; s >>= 1)
+    if (x >= thr[c + s - 1]) c += s;
+  return c;
+}
+
+// Same result as srgb_code: a fast estimate of round(255 * sRGB(x)) from the
+// hardware log2/exp2 approximations is off by at most one code near a code
+// boundary, and one comparison against each neighbouring exact boundary fixes
+// it.  x is clamped to [0, 1] first (NaN -> 0).
+__device__ __forceinline__ uint32_t srgb_code_fast(float x, const float* thr) {
+  x = fminf(fmaxf(x, 0.0f), 1.0f);
+  const float s = x <= 0.0031308f ? 12.92f * x
+                                  : fmaf(1.055f, exp2f(__log2f(x) * (1.0f / 2.4f)), -0.055f);
+  int c = __float2int_rd(fmaf(255.0f, s, 0.5f));
+  c = min(max(c, 0), 255);
+  // x < thr[c-1] and x >= thr[c] exclude each other; thr[255] = +inf
+  const float lo = thr[c > 0 ? c - 1 : 0];
+  c -= (c > 0 && x < lo) ? 1 : 0;
+  c += (x >= thr[c]) ? 1 : 0;
+  return (uint32_t)c;
+}
+
+__device__ __forceinline__ uint32_t pack_rgba8(float4 v, const float* thr) {
+  const float a = fminf(fmaxf(v.w, 0.0f), 1.0f);  // fmaxf(NaN, 0) = 0
+  const uint32_t A = (uint32_t)__float2int_rd(fmaf(255.0f, a, 0.5f));
+  return srgb_code_fast(v.x, thr) | (srgb_code_fast(v.y, thr) << 8) |
+         (srgb_code_fast(v.z, thr) << 16) | (A << 24);
+}
+
+// ---- mbarrier and bulk-copy wrappers (sm_90+ PTX) ----
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses to shared memory before
+// its later async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// One-dimensional bulk copy global -> shared, completing on `bar`.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+}  // namespace dfb

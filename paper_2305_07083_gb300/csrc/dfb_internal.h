@@ -1,5 +1,5 @@
-// Internal definitions shared by the host side (dfb_api.cu) and the kernels
-// (dfb_kernels.cu) of the DFB compositing library.  Not part of the C ABI.
+// Internal definitions shared by the host side (dfb_api.cu, dfb_noalloc.cu)
+// and the kernels (dfb_kernels.cu, dfb_composite.cu).  Not part of the C ABI.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -9,14 +9,16 @@
 
 namespace dfb {
 
-// Pixels (threads) per composite work item.  A work item is one chunk of
-// one tile; a 64x64 tile is 16 work items.
+// Pixels per composite work item (= consumer threads of a CTA).  A work item
+// is 256 consecutive pixels of one tile; a 64x64 tile is 16 items.  Tiles of
+// fewer than 256 pixels are one item each.
 constexpr int kItemPixels = 256;
-// Per-pixel sort window of the depth mode: fragments are taken in rounds of
-// at most kSortWindow, each round the kSortWindow nearest not yet blended.
+// Fragments of an item staged in shared memory by bulk copies; items with
+// more fragments take the slower streaming path.
+constexpr int kStageFragments = 16;
+// Per-pixel sort window of the streaming path: fragments are taken in rounds
+// of at most kSortWindow, each round the window's nearest not yet blended.
 constexpr int kSortWindow = 16;
-// Fragment pointers staged in shared memory per work item.
-constexpr int kRecSmem = 256;
 
 // Device record of one submitted fragment tile (32 bytes).
 struct FragRec {
@@ -29,10 +31,27 @@ struct FragRec {
 };
 static_assert(sizeof(FragRec) == 32, "FragRec layout");
 
+// Fixed-size per-tile block written by the bucketing: the tile's fragment
+// count, its offset in the sorted records, and its first kStageFragments
+// records.  The composite fetches one block per work item with a single bulk
+// copy, so locating an item's fragments needs no dependent loads.
+struct TileBlock {
+  int n;
+  int off;
+  int pad[6];
+  FragRec recs[kStageFragments];
+};
+static_assert(sizeof(TileBlock) == 32 + 32 * kStageFragments, "TileBlock layout");
+
 // Everything a composite work item needs about its frame.
 struct FrameArgs {
   int W, H, T, logT;
-  int tilesX, nTiles, chunks;  // chunks = work items per tile
+  int tilesX, nTiles;
+  int P;                       // pixels per work item: min(kItemPixels, T*T)
+  int chunks;                  // work items per tile: T*T / P (a power of two)
+  int logChunks;
+  float invTilesX;             // 1 / tilesX, for tile -> (tx, ty) without a division
+  int slots;                   // per-tile variance partials: ceil(T*T / 32)
   int tileBase;                // first global tile index of this frame
   int mode, dtype;
   unsigned flags;
@@ -41,42 +60,55 @@ struct FrameArgs {
   int kahanFirst;              // 1: first compensated frame (comp reads as 0)
   float invN, invNm1;          // 1/n and 1/(n-1) (0 when n == 1)
   float bgR, bgG, bgB, bgA;    // premultiplied background colour and coverage
-  const FragRec* recs;
-  const uint32_t* sorted;      // record indices per global tile, (key, index) order
-  const int* counts;           // per global tile
-  const int* offsets;          // per global tile
-  float4* color;
-  float4* accum;
-  float4* comp;
-  float4* m2;
+  const FragRec* srecs;        // records grouped by global tile, (key, index) order
+  const TileBlock* blocks;     // per global tile
+  float4* color;               // row-major image
+  float4* accum;               // tile-major: tile * T*T + pixel of the tile
+  float4* comp;                // tile-major
+  float4* m2;                  // tile-major
   uint32_t* rgba8;
   float* tileVar;
-  float* varPartial;           // [nTiles * chunks] per-item partial sums
-  unsigned* tileDone;          // [nTiles] items finished (self-resetting)
+  float* varPartial;           // [nTiles * slots] per-warp partial sums
 };
 
-// Bucketing (K1): counts -> offsets -> scatter -> per-tile rank sort.
-// `scratch` layouts are owned by the caller.
+// Launch shape of the composite kernel, chosen by the autotuner.
+struct TuneParams {
+  int ringKB;     // shared-memory ring per CTA in KB (its depth: items in flight)
+  int ctasPerSm;  // persistent CTAs per SM (1 or 2)
+};
+
+// Controls of one composite launch.
+struct LaunchCtl {
+  unsigned long long waitNs;  // bound on every barrier wait inside the kernel
+  int stallItem;              // test fault injection: this item is never filled (-1: off)
+  unsigned* err;              // device error word; bit 0 = a wait timed out
+};
+
+// Bucketing (K1): counts -> offsets -> scatter -> per-tile rank sort that
+// writes the records themselves in (key, index) order to `srecs` and fills
+// one TileBlock per tile.
 cudaError_t launch_bucket(const FragRec* recs, int nRec, int nTilesTotal, int* counts,
-                          int* offsets, int* cursor, uint32_t* tmp, uint32_t* sorted,
-                          cudaStream_t s);
+                          int* offsets, int* cursor, uint32_t* tmp, FragRec* srecs,
+                          TileBlock* blocks, cudaStream_t s);
 
-// Composite + accumulate + variance + pack for one frame (K2/K3 + K4).
-cudaError_t launch_composite(const FrameArgs& a, cudaStream_t s);
+// Composite + accumulate + variance + pack (K2/K3 + K4) over the work items of
+// `nFrames` frames (device arrays `frames` and `itemBase`, nFrames + 1 prefix
+// of work items), all of storage dtype `dtype`, one persistent launch; then,
+// if `accumulate`, the per-tile variance of `totalTiles` global tiles.
+cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int nFrames,
+                             int totalItems, int totalTiles, bool accumulate, int dtype,
+                             const TuneParams& tune, const LaunchCtl& ctl, cudaStream_t s);
 
-// Batched persistent form over many frames.  `frames` and `itemBase`
-// (nFrames+1 prefix of work items) are device arrays; `queue` is a device
-// counter that the kernel resets when the last CTA leaves.
-cudaError_t launch_composite_batch(const FrameArgs* frames, const int* itemBase, int nFrames,
-                                   int totalItems, int dtype, unsigned* queue, int ctasPerSm,
-                                   cudaStream_t s);
+// Default launch shape for a dtype.
+TuneParams default_tune(int dtype);
 
-// Normalised mean of the accumulation (sum * invN) into `out` (device).
-cudaError_t launch_normalise(const float4* accum, const float4* comp, int kahan, float invN,
-                             float4* out, int64_t n, cudaStream_t s);
-// Per-pixel variance M2 * invNm1 into `out` (device).
-cudaError_t launch_variance(const float4* m2, float invNm1, float4* out, int64_t n,
-                            cudaStream_t s);
+// Tile-major state -> row-major image `out` (device):
+//   out = (a - b) * scale  when b is given, else a * scale.
+cudaError_t launch_tiles_to_image(const float4* a, const float4* b, float scale, float4* out,
+                                  int W, int H, int T, cudaStream_t s);
+// Row-major image -> tile-major state (pixels outside the frame untouched).
+cudaError_t launch_image_to_tiles(const float4* in, float4* out, int W, int H, int T,
+                                  cudaStream_t s);
 
 // FP32 -> storage dtype conversion of fragment tiles (producer side).
 cudaError_t launch_convert(const float* src, void* dst, float* scales, int nTiles,
@@ -84,6 +116,25 @@ cudaError_t launch_convert(const float* src, void* dst, float* scales, int nTile
 
 // Upload the sRGB threshold table to the current device (idempotent).
 cudaError_t ensure_tables();
+
+// Fill the geometry fields of FrameArgs that follow from W, H, T.
+inline void frame_geometry(FrameArgs& a, int W, int H, int T) {
+  a.W = W;
+  a.H = H;
+  a.T = T;
+  int l = 0;
+  while ((1 << l) < T) ++l;
+  a.logT = l;
+  a.tilesX = (W + T - 1) / T;
+  a.nTiles = a.tilesX * ((H + T - 1) / T);
+  a.P = T * T < kItemPixels ? T * T : kItemPixels;
+  a.chunks = T * T / a.P;
+  int lc = 0;
+  while ((1 << lc) < a.chunks) ++lc;
+  a.logChunks = lc;
+  a.invTilesX = 1.0f / (float)a.tilesX;
+  a.slots = (T * T + 31) / 32;
+}
 
 // Order-preserving 32-bit image of a float (NaN must be handled by caller).
 inline uint32_t ordered_bits_host(float f) {

@@ -25,30 +25,39 @@ using dfb::FragRec;
 using dfb::FrameArgs;
 
 constexpr int kMaxFragments = 65536;  // fragment tiles per call
-constexpr int kMaxTiles = 65536;      // tiles per frame
+constexpr int kMaxTiles = 16384;      // tiles per frame
 
 // Layout of g_scratch (each region 256-byte aligned):
+//   FrameArgs + item prefix + error word
 //   FragRec  recs[kMaxFragments]      32 B each
 //   int      tileIn[kMaxFragments]    raw inputs copied from the caller
 //   float    keyIn[kMaxFragments]
 //   uint64   rgbaIn[kMaxFragments]
 //   uint64   depthIn[kMaxFragments]
 //   float    scaleIn[kMaxFragments]
-//   uint32   tmp[kMaxFragments], sorted[kMaxFragments]
+//   uint32   tmp[kMaxFragments]
+//   FragRec  srecs[kMaxFragments]     records sorted per tile
 //   int      counts[kMaxTiles], offsets[kMaxTiles], cursor[kMaxTiles]
+//   TileBlock blocks[kMaxTiles]       per-tile count/offset/first records
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
-constexpr size_t kOffRecs = 0;
+struct Header {
+  FrameArgs fa;
+  int itemBase[2];
+  unsigned err;
+};
+constexpr size_t kOffRecs = align256(sizeof(Header));
 constexpr size_t kOffTileIn = align256(kOffRecs + sizeof(FragRec) * kMaxFragments);
 constexpr size_t kOffKeyIn = align256(kOffTileIn + sizeof(int) * kMaxFragments);
 constexpr size_t kOffRgbaIn = align256(kOffKeyIn + sizeof(float) * kMaxFragments);
 constexpr size_t kOffDepthIn = align256(kOffRgbaIn + sizeof(uint64_t) * kMaxFragments);
 constexpr size_t kOffScaleIn = align256(kOffDepthIn + sizeof(uint64_t) * kMaxFragments);
 constexpr size_t kOffTmp = align256(kOffScaleIn + sizeof(float) * kMaxFragments);
-constexpr size_t kOffSorted = align256(kOffTmp + sizeof(uint32_t) * kMaxFragments);
-constexpr size_t kOffCounts = align256(kOffSorted + sizeof(uint32_t) * kMaxFragments);
+constexpr size_t kOffSrecs = align256(kOffTmp + sizeof(uint32_t) * kMaxFragments);
+constexpr size_t kOffCounts = align256(kOffSrecs + sizeof(FragRec) * kMaxFragments);
 constexpr size_t kOffOffsets = align256(kOffCounts + sizeof(int) * kMaxTiles);
 constexpr size_t kOffCursor = align256(kOffOffsets + sizeof(int) * kMaxTiles);
-constexpr size_t kScratchBytes = align256(kOffCursor + sizeof(int) * kMaxTiles);  // ~5.3 MB
+constexpr size_t kOffBlocks = align256(kOffCursor + sizeof(int) * kMaxTiles);
+constexpr size_t kScratchBytes = align256(kOffBlocks + sizeof(dfb::TileBlock) * kMaxTiles);  // ~15.2 MB
 
 // The scratch itself.  Every GPU that loads the library holds it until the
 // process exits.  In host code `g_scratch` names a host-side stand-in, not the
@@ -95,10 +104,6 @@ __global__ void k_pack_records(const int* __restrict__ tileIn, const float* __re
   recs[i] = r;
 }
 
-int elt_bytes(int dtype) {
-  return dtype == DFB_F32 ? 4 : (dtype == DFB_FP8E4M3 ? 1 : 2);
-}
-
 bool device_accessible(const void* p) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -126,11 +131,10 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   const int tilesX = (width + T - 1) / T, tilesY = (height + T - 1) / T;
   if ((int64_t)tilesX * tilesY > kMaxTiles || n > kMaxFragments) return DFB_ERR_CAPACITY;
   const int nTiles = tilesX * tilesY;
-  const uintptr_t ralign = (uintptr_t)(4 * elt_bytes(dtype));
   for (int i = 0; i < n; ++i) {
     if (tile_ids[i] < 0 || tile_ids[i] >= nTiles) return DFB_ERR_TILE_RANGE;
     if (isnan(order_keys[i]) || !rgba[i] || !depth[i]) return DFB_ERR_INVALID_ARG;
-    if (((uintptr_t)rgba[i] % ralign) || ((uintptr_t)depth[i] % 4)) return DFB_ERR_INVALID_ARG;
+    if (((uintptr_t)rgba[i] % 16) || ((uintptr_t)depth[i] % 16)) return DFB_ERR_INVALID_ARG;
     if (dtype == DFB_FP8E4M3 && !(scales[i] > 0.0f && isfinite(scales[i])))
       return DFB_ERR_INVALID_ARG;
   }
@@ -154,7 +158,9 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   uint64_t* depthIn = reinterpret_cast<uint64_t*>(base + kOffDepthIn);
   float* scaleIn = reinterpret_cast<float*>(base + kOffScaleIn);
   uint32_t* tmp = reinterpret_cast<uint32_t*>(base + kOffTmp);
-  uint32_t* sorted = reinterpret_cast<uint32_t*>(base + kOffSorted);
+  FragRec* srecs = reinterpret_cast<FragRec*>(base + kOffSrecs);
+  dfb::TileBlock* blocks = reinterpret_cast<dfb::TileBlock*>(base + kOffBlocks);
+  Header* dHdr = reinterpret_cast<Header*>(base);
   int* counts = reinterpret_cast<int*>(base + kOffCounts);
   int* offsets = reinterpret_cast<int*>(base + kOffOffsets);
   int* cursor = reinterpret_cast<int*>(base + kOffCursor);
@@ -184,19 +190,12 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   }
   // ---- bucketing (clears the per-tile counts itself) and compositing ----
   if (e == cudaSuccess)
-    e = dfb::launch_bucket(recs, n, nTiles, counts, offsets, cursor, tmp, sorted, s);
+    e = dfb::launch_bucket(recs, n, nTiles, counts, offsets, cursor, tmp, srecs, blocks, s);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? DFB_ERR_OOM : DFB_ERR_CUDA;
 
-  FrameArgs a{};
-  a.W = width;
-  a.H = height;
-  a.T = T;
-  int logT = 0;
-  while ((1 << logT) < T) ++logT;
-  a.logT = logT;
-  a.tilesX = tilesX;
-  a.nTiles = nTiles;
-  a.chunks = (T * T + dfb::kItemPixels - 1) / dfb::kItemPixels;
+  Header hdr{};
+  FrameArgs& a = hdr.fa;
+  dfb::frame_geometry(a, width, height, T);
   a.tileBase = 0;
   a.mode = mode;
   a.dtype = dtype;
@@ -209,12 +208,19 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   a.bgG = bg[1] * bg[3];
   a.bgB = bg[2] * bg[3];
   a.bgA = bg[3];
-  a.recs = recs;
-  a.sorted = sorted;
-  a.counts = counts;
-  a.offsets = offsets;
+  a.srecs = srecs;
+  a.blocks = blocks;
   a.color = reinterpret_cast<float4*>(color_out);
   a.rgba8 = rgba8_out;
-  e = dfb::launch_composite(a, s);
+  hdr.itemBase[0] = 0;
+  hdr.itemBase[1] = nTiles * a.chunks;
+  hdr.err = 0u;
+  // pageable source: the copy has consumed `hdr` when the call returns
+  e = cudaMemcpyAsync(dHdr, &hdr, sizeof(Header), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return DFB_ERR_CUDA;
+  const dfb::LaunchCtl ctl{2000000000ull, -1, &dHdr->err};
+  e = dfb::launch_composite(&dHdr->fa, dHdr->itemBase, 1, hdr.itemBase[1], nTiles, false, dtype,
+                           dfb::default_tune(dtype), ctl, s);
   return e == cudaSuccess ? DFB_OK : DFB_ERR_CUDA;
 }

@@ -100,6 +100,9 @@ def lib():
         "dfb_read_timing": (C.c_int, [H, C.POINTER(dfb_timing), C.c_int]),
         "dfb_composite_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                             P, P, P, P, P, P, P, P, P]),
+        "dfb_set_tuning": (C.c_int, [H, C.c_int, C.c_int]),
+        "dfb_set_wait_limit": (C.c_int, [H, C.c_double]),
+        "dfb_inject_stall": (C.c_int, [H, C.c_int]),
         "dfb_error_string": (C.c_char_p, [C.c_int]),
         "dfb_version": (C.c_int, []),
     }
@@ -302,3 +305,15 @@ def dfb_composite_noalloc(width, height, tile_size, mode, dtype, tile_ids, order
         rp.ctypes.data, dp.ctypes.data, None if sc is None else sc.ctypes.data,
         None if bg is None else bg.ctypes.data, _ptr(color_out), _ptr(rgba8_out), _stream(stream))
     return _check(st, "dfb_composite_noalloc")
+
+
+def dfb_set_wait_limit(h, seconds):
+    return _check(lib().dfb_set_wait_limit(h, float(seconds)), "dfb_set_wait_limit")
+
+
+def dfb_inject_stall(h, item):
+    return _check(lib().dfb_inject_stall(h, int(item)), "dfb_inject_stall")
+
+
+def dfb_set_tuning(h, ring_kb=0, ctas_per_sm=0):
+    return _check(lib().dfb_set_tuning(h, int(ring_kb), int(ctas_per_sm)), "dfb_set_tuning")

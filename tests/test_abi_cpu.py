@@ -124,8 +124,11 @@ def test_submit_validation():
             assert code_of(submit, h8, [0], None, None, None,
                            np.array([bad], np.float32)) == D.DFB_ERR_INVALID_ARG
         submit(h8, [0], scales=np.array([0.5], np.float32))
-        # FP8 needs only 4-byte aligned RGBA
-        submit(h8, [0], rgba=[FAKE + 4], scales=np.array([0.5], np.float32))
+        # every tile is streamed with bulk copies: 16-byte alignment for all dtypes
+        assert code_of(submit, h8, [0], None, [FAKE + 4], None,
+                       np.array([0.5], np.float32)) == D.DFB_ERR_INVALID_ARG
+        assert code_of(submit, h8, [0], None, None, [FAKE + 8],
+                       np.array([0.5], np.float32)) == D.DFB_ERR_INVALID_ARG
     finally:
         D.dfb_destroy(h8)
 
@@ -200,6 +203,19 @@ def test_complete_frame_without_device_reports_cuda_error():
         assert code_of(D.dfb_end_frame, h) == D.DFB_ERR_CUDA
         # the frame stays open, so it can still be ended once a device is present
         assert code_of(D.dfb_begin_frame, h, 0) == D.DFB_ERR_STATE
+    finally:
+        D.dfb_destroy(h)
+
+
+def test_wait_limit_and_stall_arguments():
+    h = deferred()
+    try:
+        D.dfb_set_wait_limit(h, 0.01)
+        assert code_of(D.dfb_set_wait_limit, h, 0.0) == D.DFB_ERR_INVALID_ARG
+        assert code_of(D.dfb_set_wait_limit, h, 1e9) == D.DFB_ERR_INVALID_ARG
+        D.dfb_inject_stall(h, 3)
+        D.dfb_inject_stall(h, -1)
+        assert code_of(D.dfb_inject_stall, h, -5) == D.DFB_ERR_INVALID_ARG
     finally:
         D.dfb_destroy(h)
 

@@ -328,3 +328,25 @@ def test_full_size_2048_sampled_tiles():
         assert d8.max() <= 1
     st = fb.stats()
     assert st["fragments"] == sc.n and st["fragment_pixels"] == sc.fragment_pixels()
+
+
+# --- failure detection: a bounded wait that runs out -------------------------------------
+def test_stalled_work_item_times_out_and_context_survives():
+    """A work item whose shared-memory stage is never filled (injected on the
+    host) makes the kernel's bounded wait run out: the frame reports
+    DFB_ERR_TIMEOUT, and the next frame on the same context is correct."""
+    sc = scenes.scene_single_frame_256(seed=0)
+    fb = GpuFrameBuffer(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH)
+    D.dfb_set_wait_limit(fb.h, 0.05)
+    D.dfb_inject_stall(fb.h, 0)
+    fb.begin(0)
+    fb.submit_pool(sc.tile_ids, sc.keys, sc.rgba, sc.depth)
+    fb.end()
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_sync(fb.h)
+    assert e.value.code == D.DFB_ERR_TIMEOUT
+    D.dfb_sync(fb.h)                         # the error was reported once
+    fb.begin(0)
+    fb.submit_pool(sc.tile_ids, sc.keys, sc.rgba, sc.depth)
+    fb.end()
+    check_color(fb.color(), oracle_frame(sc, o.BLEND_DEPTH), D.DFB_BLEND_DEPTH)
