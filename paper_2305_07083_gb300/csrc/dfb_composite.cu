@@ -13,10 +13,11 @@
 //
 // The work is bound by HBM bandwidth (~0.4 flop per byte), so the design goal
 // is to keep enough bytes in flight:
-//   * CTA = 2 consumer groups of 8 warps (one pixel per thread, 256 pixels =
-//     one work item; the groups take alternate items) + 1 producer warp.
-//     CTAs are persistent and walk the work items of all frames of the
-//     launch with a static stride.
+//   * CTA = G consumer groups of 8 warps (one pixel per thread, 256 pixels =
+//     one work item; the groups take alternate items) + 1 producer warp;
+//     either 1 CTA per SM with G = 2 or 2 CTAs per SM with G = 1.  CTAs are
+//     persistent and walk the work items of all frames of the launch with a
+//     static stride.
 //   * The producer warp fetches each item's tile block (fragment count,
 //     list offset and sorted records, written by the bucketing) with one bulk
 //     copy kMetaQ items ahead, so locating an item's fragments needs no
@@ -29,8 +30,8 @@
 //   * The accumulation state (sum, M2, Kahan compensation) is stored
 //     tile-major, so an item's state is one contiguous run per buffer that
 //     the producer streams into the same ring space; consumers read every
-//     input from shared memory: they sort and blend, run the epilogue, then
-//     release the ring space.
+//     input from shared memory, sort and blend, take the state into
+//     registers and release the ring space before the epilogue.
 //   * Items with more than kStageFragments fragments are streamed from HBM
 //     by the consumers in rounds of a per-pixel sort window (held in ring
 //     space the item reserves).
@@ -56,8 +57,12 @@ namespace {
 
 constexpr int kP = kItemPixels;          // pixels per item = threads of a consumer group
 constexpr int kCW = kP / 32;             // warps of a consumer group
-constexpr int kGroups = 2;               // consumer groups: items k, k+1 in parallel
-constexpr int kThreads = kGroups * kP + 32;  // + the producer warp
+// Threads of a CTA with G consumer groups (items k, k+1, ... composited in
+// parallel) and one producer warp.
+template <int G>
+struct Shape {
+  static constexpr int threads = G * kP + 32;
+};
 constexpr int kN = kStageFragments;
 constexpr int kSlots = 16;               // items in flight at most
 constexpr int kMetaQ = 8;                // tile blocks fetched ahead
@@ -79,9 +84,11 @@ constexpr int kOffBars = 1024;
 constexpr int kOffFlags = kOffBars + 512;
 constexpr int kOffMetas = kOffFlags + 128;
 constexpr int kOffQueue = kOffMetas + kSlots * 256;
-constexpr int kHeader = kOffQueue + kMetaQ * (int)sizeof(TileBlock);
+constexpr int kOffQLoc = kOffQueue + kMetaQ * (int)sizeof(TileBlock);
+constexpr int kHeader = kOffQLoc + 128;
 static_assert((2 * kSlots + kMetaQ) * 8 <= 512, "barrier space");
 static_assert(kOffQueue % 128 == 0 && kHeader % 128 == 0, "alignment");
+static_assert(kMetaQ * 16 <= 128, "queue locations");
 
 template <int DT>
 struct Bytes {
@@ -158,8 +165,9 @@ __device__ __forceinline__ ItemLoc locate(const FrameArgs* frames, const int* it
 template <int DT>
 __device__ void producer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                          int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
-                         uint32_t ringBytes, ItemMeta* metas, TileBlock* queue, uint64_t* fullB,
-                         uint64_t* emptyB, uint64_t* queueB, volatile int* abort) {
+                         uint32_t ringBytes, ItemMeta* metas, TileBlock* queue, int4* qLoc,
+                         uint64_t* fullB, uint64_t* emptyB, uint64_t* queueB,
+                         volatile int* abort) {
   constexpr int px = Bytes<DT>::px;
   const int lane = threadIdx.x & 31;
   unsigned long long head = 0, tail = 0;  // monotonic ring positions
@@ -172,6 +180,7 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
     if (it >= totalItems || lane != 0) return;
     const ItemLoc L = locate(frames, itemBase, nFrames, it);
     const int q = kk % kMetaQ;
+    qLoc[q] = make_int4(L.f, L.tile, L.chunk, L.gt);
     fence_proxy_async();  // the slot's previous block was read through the generic proxy
     mbar_arrive_expect_tx(&queueB[q], (uint32_t)sizeof(TileBlock));
     bulk_g2s(queue + q, frames[L.f].blocks + L.gt, (uint32_t)sizeof(TileBlock), &queueB[q]);
@@ -191,9 +200,10 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
     const int n = blk->n, off = blk->off;
     FragRec r{};
     if (lane < n && lane < kN) r = blk->recs[lane];
+    const int4 loc = qLoc[q];
+    const ItemLoc cur{loc.x, loc.y, loc.z, loc.w};
     __syncwarp();
     fetch(k + kMetaQ);  // every lane has read the slot
-    const ItemLoc cur = locate(frames, itemBase, nFrames, item);
     const FrameArgs* A = frames + cur.f;
     const int P = A->P, mode = A->mode, T = A->T;
     const bool staged = n <= kN;
@@ -466,7 +476,7 @@ __device__ __forceinline__ PixWork prepare(const FrameArgs* frames, const int* i
   return w;
 }
 
-template <int DT>
+template <int DT, int G>
 __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                          int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
                          ItemMeta* metas, uint64_t* fullB, uint64_t* emptyB, volatile int* abort,
@@ -474,7 +484,7 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
   const int group = threadIdx.x / kP;
   const int t = threadIdx.x - group * kP;  // pixel of the item, 0 .. kP-1
   const int lane = t & 31, warp = t >> 5;
-  for (int k = group; ; k += kGroups) {
+  for (int k = group; ; k += G) {
     const int item = blockIdx.x + k * (int)gridDim.x;
     if (item >= totalItems) break;
     const int s = k % kSlots;
@@ -501,6 +511,19 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
     }
     const unsigned flags = A->flags;
     const bool acc = (flags & DFB_FLAG_ACCUMULATE) != 0;
+    // the item's accumulation state: from the ring into registers, then the
+    // ring space goes back to the producer before the epilogue's math and
+    // stores
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 S = zero4, M = zero4, CP = zero4;
+    if (w.active && acc && A->frameN != 1) {
+      const float4* sState = reinterpret_cast<const float4*>(base + meta->stateOff);
+      S = sState[t];
+      M = sState[P + t];
+      if (A->kahan && !A->kahanFirst) CP = sState[2 * P + t];
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&emptyB[s]);  // ring space free for the producer
     float vsum = 0.0f;
     if (w.active) {
       if (mode != DFB_ZCOMPOSITE) {
@@ -513,13 +536,6 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
       if (flags & DFB_FLAG_WRITE_COLOR) A->color[w.pix] = col;
       float4 out = col;
       if (acc) {
-        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        // state rows were streamed into the ring unless this frame starts the
-        // accumulation
-        const float4* sState = reinterpret_cast<const float4*>(base + meta->stateOff);
-        const float4 S = A->frameN != 1 ? sState[t] : zero4;
-        float4 M = A->frameN != 1 ? sState[P + t] : zero4;
-        const float4 CP = (A->kahan && !A->kahanFirst) ? sState[2 * P + t] : zero4;
         float4 Sn, tot;
         if (A->kahan) {
           float4 cn;
@@ -562,13 +578,12 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
       if (lane == 0)
         A->varPartial[(size_t)w.tile * A->slots + ((w.chunk * P + warp * 32) >> 5)] = v;
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&emptyB[s]);  // ring space free for the producer
   }
 }
 
-template <int DT>
-__global__ void __launch_bounds__(kThreads, 1) k_composite(const FrameArgs* __restrict__ frames,
+template <int DT, int G>
+__global__ void __launch_bounds__(Shape<G>::threads, 3 - G) k_composite(
+    const FrameArgs* __restrict__ frames,
                                                         const int* __restrict__ itemBase,
                                                         int nFrames, int totalItems,
                                                         uint32_t ringBytes, LaunchCtl ctl) {
@@ -579,9 +594,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_composite(const FrameArgs* __re
   volatile int* abort = reinterpret_cast<volatile int*>(smem + kOffFlags);
   ItemMeta* metas = reinterpret_cast<ItemMeta*>(smem + kOffMetas);
   TileBlock* queue = reinterpret_cast<TileBlock*>(smem + kOffQueue);
+  int4* qLoc = reinterpret_cast<int4*>(smem + kOffQLoc);
   uint64_t* queueB = emptyB + kSlots;
   unsigned char* ring = smem + kHeader;
-  for (int i = threadIdx.x; i < 256; i += kThreads) thr[i] = g_srgb_thr[i];
+  for (int i = threadIdx.x; i < 256; i += Shape<G>::threads) thr[i] = g_srgb_thr[i];
   if (threadIdx.x == 0) {
     for (int q = 0; q < kSlots; ++q) {
       mbar_init(&fullB[q], 1);
@@ -592,11 +608,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_composite(const FrameArgs* __re
     fence_barrier_init();
   }
   __syncthreads();
-  if (threadIdx.x >= kGroups * kP)
-    producer<DT>(frames, itemBase, nFrames, totalItems, ctl, ring, ringBytes, metas, queue, fullB,
-                 emptyB, queueB, abort);
+  if (threadIdx.x >= G * kP)
+    producer<DT>(frames, itemBase, nFrames, totalItems, ctl, ring, ringBytes, metas, queue, qLoc,
+                 fullB, emptyB, queueB, abort);
   else
-    consumer<DT>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
+    consumer<DT, G>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
                  thr);
 }
 
@@ -628,10 +644,11 @@ __global__ void k_tile_variance(const FrameArgs* __restrict__ frames, int nFrame
   }
 }
 
-template <int DT>
-cudaError_t launch_dt(const FrameArgs* frames, const int* itemBase, int nFrames, int totalItems,
-                      const TuneParams& tune, const LaunchCtl& ctl, cudaStream_t s) {
-  auto kern = k_composite<DT>;
+template <int DT, int G>
+cudaError_t launch_shape(const FrameArgs* frames, const int* itemBase, int nFrames,
+                         int totalItems, int ringKB, const LaunchCtl& ctl, cudaStream_t s) {
+  auto kern = k_composite<DT, G>;
+  constexpr int per = 3 - G;  // CTAs per SM
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -639,34 +656,46 @@ cudaError_t launch_dt(const FrameArgs* frames, const int* itemBase, int nFrames,
   static int sms[64] = {0};
   static int smemMax[64] = {0};
   if (!sms[dev]) {
-    int optin = 0;
+    int optin = 0, perSm = 0;
     e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
       e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&perSm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) {
       sms[dev] = 0;
       return e;
     }
-    smemMax[dev] = optin;
+    // per CTA: what `per` CTAs can share, less the 1 KB the driver reserves per CTA
+    const int share = perSm / per - 1024;
+    smemMax[dev] = share < optin ? share : optin;
   }
-  const int per = tune.ctasPerSm > 1 ? 2 : 1;
-  uint32_t ring = (uint32_t)tune.ringKB * 1024u;
-  const uint32_t cap = (uint32_t)((smemMax[dev] / per) - kHeader - 1024) & ~127u;
+  uint32_t ring = (uint32_t)ringKB * 1024u;
+  const uint32_t cap = (uint32_t)(smemMax[dev] - kHeader) & ~127u;
   if (ring > cap) ring = cap;
   if (ring < Bytes<DT>::maxItem) return cudaErrorInvalidConfiguration;
   int grid = sms[dev] * per;
   if (grid > totalItems) grid = totalItems;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, kThreads, kHeader + ring, s>>>(frames, itemBase, nFrames, totalItems, ring, ctl);
+  kern<<<grid, Shape<G>::threads, kHeader + ring, s>>>(frames, itemBase, nFrames, totalItems, ring,
+                                                       ctl);
   return cudaGetLastError();
+}
+
+template <int DT>
+cudaError_t launch_dt(const FrameArgs* frames, const int* itemBase, int nFrames, int totalItems,
+                      const TuneParams& tune, const LaunchCtl& ctl, cudaStream_t s) {
+  if (tune.ctasPerSm >= 2)
+    return launch_shape<DT, 1>(frames, itemBase, nFrames, totalItems, tune.ringKB, ctl, s);
+  return launch_shape<DT, 2>(frames, itemBase, nFrames, totalItems, tune.ringKB, ctl, s);
 }
 
 }  // namespace
 
 TuneParams default_tune(int dtype) {
   (void)dtype;
-  return TuneParams{160, 1};
+  return TuneParams{110, 2};
 }
 
 cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int nFrames,
