@@ -230,7 +230,9 @@ def timed(run, steps, warmup, stream, dist=None, sampler=None, read_back=None):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("paper_2305_07083_gb300/csrc/dfb_kernels.cu", "paper_2305_07083_gb300/csrc/dfb_internal.h"):
+    for f in ("paper_2305_07083_gb300/csrc/dfb_composite.cu",
+              "paper_2305_07083_gb300/csrc/dfb_device.cuh",
+              "paper_2305_07083_gb300/csrc/dfb_internal.h"):
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -435,7 +437,8 @@ def main():
     run.close()
     out["gpu_launches"] = launches
     out["gpu_launches_note"] = ("kernels launched by libdfb.so inside the timed FP32 region "
-                                "(per frame: 4 bucketing + 1 composite), counted by the library")
+                                "(per frame: 4 bucketing, the composite, the per-tile variance "
+                                "sum), counted by the library")
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample ----
     if pool is not None:
