@@ -267,6 +267,83 @@ def peaks():
 
 
 # ----------------------------------------------------------------------------
+# batched form: 32 mixed frames, FP16, one persistent launch in a CUDA graph
+# ----------------------------------------------------------------------------
+def run_batched(dev, stream, steps, warmup):
+    import torch
+    from harness import scenes
+    from paper_2305_07083_gb300 import dfb as D
+    frames = scenes.batch_frames_torch(32, seed=0, device=dev)
+    fpx = sum(len(f["tile_ids"]) * f["T"] * f["T"] for f in frames)
+    flags = D.DFB_FLAG_WRITE_COLOR | D.DFB_FLAG_PACK_RGBA8
+    keep, h16, h32 = [], [], []
+    for f in frames:
+        n, P = len(f["tile_ids"]), f["T"] * f["T"]
+        f16 = torch.empty(max(n, 1) * P * 4, dtype=torch.float16, device=dev)
+        if n:
+            D.dfb_convert_tiles(f["rgba"], f16, None, n, P, D.DFB_F16, stream)
+        keep += [f16]
+        for dtype, pool, lst in ((D.DFB_F16, f16, h16), (D.DFB_F32, f["rgba"], h32)):
+            h = D.dfb_create_ex(f["W"], f["H"], f["T"], D.DFB_BLEND_DEPTH, dtype, flags, 0,
+                                max(4096, n))
+            lst.append((h, f, pool, dtype))
+    torch.cuda.synchronize()
+
+    def submit(h, f, pool, dtype):
+        n, P = len(f["tile_ids"]), f["T"] * f["T"]
+        D.dfb_begin_frame(h, 0)
+        D.dfb_submit_tiles(h, f["tile_ids"], f["keys"],
+                           D.pool_pointers(pool, n, P * 4 * D.ELEMENT_BYTES[dtype]),
+                           D.pool_pointers(f["depth"], n, P * 4), None, D.DFB_PTR_DEVICE)
+
+    # the plain FP32 path: every frame through its own dfb_end_frame
+    def plain_step():
+        for h, f, pool, dtype in h32:
+            submit(h, f, pool, dtype)
+            D.dfb_end_frame(h, stream)
+
+    for _ in range(warmup):
+        plain_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plain_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1) / steps
+    # batched FP16: one graph = bucketing + one persistent composite launch
+    for h, f, pool, dtype in h16:
+        submit(h, f, pool, dtype)
+    g = D.dfb_graph_create([h for h, _, _, _ in h16])
+    tune = D.dfb_graph_autotune(g, stream, reps=3)
+    for _ in range(warmup):
+        D.dfb_graph_launch(g, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        D.dfb_graph_launch(g, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / steps
+    counts = np.concatenate([np.bincount(f["tile_ids"], minlength=1) for f in frames])
+    D.dfb_graph_destroy(g)
+    for h, _, _, _ in h16 + h32:
+        D.dfb_destroy(h)
+    del keep, frames
+    torch.cuda.empty_cache()
+    return {"workload": "32 frames of 512x512 / 1024x1024 / 2048x2048 / 4096x1024 (8 each), "
+                        "64x64 tiles, 8 to 512 bricks per frame, BLEND_DEPTH, no accumulation",
+            "fragment_pixels_per_step": fpx, "max_fragments_per_tile": int(counts.max()),
+            "value": fpx / (batch_ms / 1e3), "unit": UNIT, "ms_per_step": batch_ms,
+            "dtype": "f16 storage, f32 math",
+            "launch": "one CUDA graph: bucketing + one persistent composite launch + tile variance",
+            "autotune": tune,
+            "plain_f32_per_frame": {"value": fpx / (plain_ms / 1e3), "ms_per_step": plain_ms},
+            "speedup_vs_plain_f32": plain_ms / batch_ms}
+
+
+# ----------------------------------------------------------------------------
 # reference arm: the oracle on host cores
 # ----------------------------------------------------------------------------
 def run_reference(args):
@@ -315,6 +392,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f16", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--tune", default=None,
                     help="composite launch shape 'ringKB,ctasPerSm' (default: the library's)")
     ap.add_argument("--frames", type=int, default=N_FRAMES,
@@ -435,6 +513,12 @@ def main():
         r16.close()
         del f16
     run.close()
+    frame0 = frames[0].cpu().numpy() if pool is not None else None
+    if not args.no_batched and rank == 0:
+        del frames
+        torch.cuda.empty_cache()
+        out.setdefault("variants", {})["batched_f16_graph"] = run_batched(
+            dev, stream, max(3, min(args.steps, 20)), args.warmup)
     out["gpu_launches"] = launches
     out["gpu_launches_note"] = ("kernels launched by libdfb.so inside the timed FP32 region "
                                 "(per frame: 4 bucketing, the composite, the per-tile variance "
@@ -442,7 +526,7 @@ def main():
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample ----
     if pool is not None:
-        rate, fpx, dt, nt = cpu_oracle_rate(sc, frames[0].cpu().numpy(), sc.n_tiles, pool,
+        rate, fpx, dt, nt = cpu_oracle_rate(sc, frame0, sc.n_tiles, pool,
                                             min_seconds=10.0)
         pool.close()
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",

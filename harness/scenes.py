@@ -367,3 +367,114 @@ def store_rgba(rgba_f32, dtype):
     q = np.clip(q, -448.0, 448.0)
     codes = torch.from_numpy(q).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
     return codes, scales
+
+
+# --- large workloads generated on the GPU -------------------------------------
+def _beta25_torch(torch, shape, gen, device):
+    """Beta(2, 5) as X / (X + Y) with X ~ Gamma(2), Y ~ Gamma(5), each Gamma(k)
+    drawn as the negative log of a product of k uniforms."""
+    u = torch.rand((7,) + tuple(shape), generator=gen, device=device).clamp_min_(1e-12)
+    x = -torch.log(u[0] * u[1])
+    y = -torch.log(u[2] * u[3] * u[4] * u[5] * u[6])
+    return x / (x + y)
+
+
+def brick_scene_torch(W, H, T, boxes, cam: Camera, seed, device):
+    """The recipe of brick_scene (projected brick rectangles refined by ray
+    casting the box, per-pixel depth uniform in the ray interval, alpha
+    Beta(2,5), colour U(0,1) premultiplied) with the random draws made by a
+    seeded torch generator on `device`.  Returns (tile_ids, keys) as numpy
+    arrays in a seeded arrival order and (rgba, depth) as device tensors."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 7919 + 17)
+    tiles_x = -(-W // T)
+    ly, lx = torch.meshgrid(torch.arange(T, device=device), torch.arange(T, device=device),
+                            indexing="ij")
+    lx = lx.reshape(-1).double()
+    ly = ly.reshape(-1).double()
+    tid_l, key_l, rgba_l, z_l = [], [], [], []
+    for bmin, bmax in boxes:
+        corners = np.array([[x, y, z] for x in (bmin[0], bmax[0])
+                            for y in (bmin[1], bmax[1]) for z in (bmin[2], bmax[2])])
+        sx, sy, ok = cam.project(corners)
+        if not ok.all():
+            continue
+        x0 = int(np.floor(max(sx.min(), 0)) // T)
+        x1 = int(min(np.ceil(sx.max()), W) - 1) // T
+        y0 = int(np.floor(max(sy.min(), 0)) // T)
+        y1 = int(min(np.ceil(sy.max()), H) - 1) // T
+        if x1 < x0 or y1 < y0 or sx.max() <= 0 or sy.max() <= 0:
+            continue
+        tys, txs = np.meshgrid(np.arange(y0, y1 + 1), np.arange(x0, x1 + 1), indexing="ij")
+        tys = torch.as_tensor(tys.reshape(-1), device=device)
+        txs = torch.as_tensor(txs.reshape(-1), device=device)
+        px = txs[:, None].double() * T + lx[None, :]
+        py = tys[:, None].double() * T + ly[None, :]
+        pxc, pyc = px + 0.5, py + 0.5
+        th = np.tan(np.radians(cam.vfov_deg) / 2)
+        u = (2.0 * pxc / W - 1.0) * th * (W / H)
+        v = (1.0 - 2.0 * pyc / H) * th
+        f = torch.as_tensor(cam.forward, device=device)
+        r = torch.as_tensor(cam.right, device=device)
+        up = torch.as_tensor(cam.up, device=device)
+        d = f + u[..., None] * r + v[..., None] * up
+        d = d / torch.linalg.norm(d, dim=-1, keepdim=True)
+        o = torch.as_tensor(cam.eye, device=device)
+        lo = torch.as_tensor(bmin, device=device)
+        hi = torch.as_tensor(bmax, device=device)
+        with torch.no_grad():
+            inv = 1.0 / d
+            t0 = (lo - o) * inv
+            t1 = (hi - o) * inv
+            t0 = torch.nan_to_num(t0, nan=-np.inf)
+            t1 = torch.nan_to_num(t1, nan=np.inf)
+            tmin = torch.minimum(t0, t1).amax(dim=-1).clamp_min(0.0)
+            tmax = torch.maximum(t0, t1).amin(dim=-1)
+        hit = (tmax > tmin) & (px < W) & (py < H)
+        keep = hit.any(dim=1)
+        if not bool(keep.any()):
+            continue
+        hit, tmin, tmax = hit[keep], tmin[keep], tmax[keep]
+        n = int(hit.shape[0])
+        tid_l.append((tys[keep] * tiles_x + txs[keep]).cpu().numpy())
+        centre = 0.5 * (np.asarray(bmin) + np.asarray(bmax))
+        key_l.append(np.full(n, np.linalg.norm(centre - cam.eye), np.float32))
+        uu = torch.rand((n, T * T), generator=gen, device=device, dtype=torch.float64)
+        z = torch.where(hit, tmin + uu * (tmax - tmin), torch.full_like(uu, float("inf")))
+        a = _beta25_torch(torch, (n, T * T), gen, device).float() * hit
+        rgb = torch.rand((n, T * T, 3), generator=gen, device=device) * a[..., None]
+        rgba_l.append(torch.cat([rgb, a[..., None]], dim=-1))
+        z_l.append(z.float())
+    tile_ids = np.concatenate(tid_l).astype(np.int32) if tid_l else np.zeros(0, np.int32)
+    keys = np.concatenate(key_l).astype(np.float32) if key_l else np.zeros(0, np.float32)
+    rgba = torch.cat(rgba_l) if rgba_l else torch.zeros((0, T * T, 4), device=device)
+    depth = torch.cat(z_l) if z_l else torch.zeros((0, T * T), device=device)
+    perm = np.random.default_rng(seed).permutation(len(tile_ids))
+    pt = torch.as_tensor(perm, device=device)
+    return tile_ids[perm], keys[perm], rgba[pt].contiguous(), depth[pt].contiguous()
+
+
+BATCH_SIZES = [(512, 512), (1024, 1024), (2048, 2048), (4096, 1024)]
+
+
+def batch_frames_torch(n_frames=32, seed=0, device="cuda", T=64):
+    """Mixed batch: frame i has the size BATCH_SIZES[i % 4], a brick grid of
+    g x g x g (g drawn from 2..8, so 8 to 512 bricks) over a 1 x 1 x 1 cube
+    (2 x 1 x 1 for the 4096x1024 frames) and a seeded orbit camera whose
+    radius leaves the cube covering the frame."""
+    rng = np.random.default_rng([seed, 4])
+    out = []
+    for i in range(n_frames):
+        W, H = BATCH_SIZES[i % len(BATCH_SIZES)]
+        g = int(rng.integers(2, 9))
+        wide = W > H
+        extent = (2.0, 1.0, 1.0) if wide else (1.0, 1.0, 1.0)
+        grid = (2 * g, g, g) if wide and g <= 4 else (g, g, g)
+        hi = tuple(float(e) for e in extent)
+        cam = orbit_camera(W, H, seed * 1000 + i, radius=1.2 if wide else 1.0, hi=hi)
+        tid, key, rgba, depth = brick_scene_torch(W, H, T, brick_grid(grid, hi=hi), cam,
+                                                  seed * 1000 + i, device)
+        out.append({"W": W, "H": H, "T": T, "bricks": int(np.prod(grid)), "tile_ids": tid,
+                    "keys": key, "rgba": rgba, "depth": depth})
+    return out

@@ -287,6 +287,40 @@ DFB_API int dfb_composite_noalloc(int width, int height, int tile_size, int mode
                                   const float* scales, const float* background,
                                   float* color_out, uint32_t* rgba8_out, void* stream);
 
+/* ---- Batched frames replayed from a CUDA graph ------------------------------
+   A dfb_graph holds the device work of compositing the open frames of several
+   handles -- record upload done once, then per launch: the bucketing kernels
+   and ONE persistent composite launch over every work item of every frame
+   (plus the per-tile variance sum) -- captured in a CUDA graph.  Each launch
+   re-reads the fragment tiles through the same device pointers, so producers
+   may rewrite their tiles in place between launches.  Frame arguments are
+   frozen at creation: an accumulating handle keeps the frame count it had
+   (use dfb_end_frame for progressive accumulation).  The handles must stay
+   alive and unused by other calls while the graph exists; results are read
+   with the usual dfb_read_* calls after a launch. */
+typedef struct dfb_graph_t* dfb_graph;
+
+/* Capture the open frames of hs[0..n) (all of one dtype, distinct handles).
+   Their trees are checked as in dfb_end_frames and the frames are ended.
+   Errors: INVALID_ARG, STATE, INCOMPLETE, OOM, CUDA. */
+DFB_API int dfb_graph_create(const dfb_handle* hs, int n, dfb_graph* out);
+
+/* Replay the captured work on `stream`. */
+DFB_API int dfb_graph_launch(dfb_graph g, void* stream);
+
+/* Re-capture with another composite launch shape (see dfb_set_tuning). */
+DFB_API int dfb_graph_set_tuning(dfb_graph g, int ring_kb, int ctas_per_sm);
+
+/* Autotuner: time `reps` replays of each candidate launch shape (ring size =
+   pipeline depth, CTAs per SM) on `stream`, keep the fastest, and report it
+   (either pointer may be NULL).  The graph's handles get the same tuning for
+   their later dfb_end_frame calls.  Errors: INVALID_ARG, CUDA. */
+DFB_API int dfb_graph_autotune(dfb_graph g, void* stream, int reps, int* ring_kb,
+                               int* ctas_per_sm, float* best_ms);
+
+/* Free the graph and its buffers (waits for its last launch). */
+DFB_API int dfb_graph_destroy(dfb_graph g);
+
 /* Launch shape of this handle's composite kernel: shared-memory ring size per
    CTA in KB (how many work items are in flight) and persistent CTAs per SM
    (1 or 2).  0, 0 restores the library default.  Values that do not fit the

@@ -1212,3 +1212,243 @@ int dfb_inject_stall(dfb_handle h, int item) {
 }
 
 }  // extern "C"
+
+// ============================================================================
+// batched frames in a CUDA graph
+// ============================================================================
+struct dfb_graph_t {
+  std::vector<dfb_ctx*> hs;
+  int dtype = 0;
+  bool anyAcc = false;
+  int nRec = 0, nTiles = 0, items = 0;
+  FragRec* dRecs = nullptr;
+  uint32_t* tmp = nullptr;
+  FragRec* srecs = nullptr;
+  dfb::TileBlock* blocks = nullptr;
+  int *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
+  FrameArgs* dFrames = nullptr;
+  int* dItemBase = nullptr;
+  unsigned* err = nullptr;
+  dfb::TuneParams tune{0, 0};
+  cudaStream_t capStream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  bool launched = false;
+};
+
+namespace {
+
+void graph_release_capture(dfb_graph_t* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  g->exec = nullptr;
+  g->graph = nullptr;
+}
+
+// (Re)capture the device work of the graph with its current tuning.
+int graph_capture(dfb_graph_t* g) {
+  graph_release_capture(g);
+  const dfb::TuneParams tune = g->tune.ringKB ? g->tune : dfb::default_tune(g->dtype);
+  // per-device launch set-up happens outside the capture (no work is enqueued)
+  cudaError_t e = dfb::launch_composite(g->dFrames, g->dItemBase, 1, 0, 0, false, g->dtype, tune,
+                                        dfb::LaunchCtl{2000000000ull, -1, g->err}, g->capStream);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaStreamBeginCapture(g->capStream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaError_t le = dfb::launch_bucket(g->dRecs, g->nRec, g->nTiles, g->counts, g->offsets,
+                                      g->cursor, g->tmp, g->srecs, g->blocks, g->capStream);
+  if (le == cudaSuccess)
+    le = dfb::launch_composite(g->dFrames, g->dItemBase, (int)g->hs.size(), g->items, g->nTiles,
+                               g->anyAcc, g->dtype, tune,
+                               dfb::LaunchCtl{2000000000ull, -1, g->err}, g->capStream);
+  e = cudaStreamEndCapture(g->capStream, &g->graph);
+  if (le != cudaSuccess) return cuda_status(le);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  return cuda_status(e);
+}
+
+void graph_free(dfb_graph_t* g) {
+  if (g->launched && g->done) cudaEventSynchronize(g->done);
+  graph_release_capture(g);
+  cudaFree(g->dRecs); cudaFree(g->tmp); cudaFree(g->srecs); cudaFree(g->blocks);
+  cudaFree(g->counts); cudaFree(g->offsets); cudaFree(g->cursor);
+  cudaFree(g->dFrames); cudaFree(g->dItemBase); cudaFree(g->err);
+  if (g->capStream) cudaStreamDestroy(g->capStream);
+  if (g->done) cudaEventDestroy(g->done);
+  delete g;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dfb_graph_create(const dfb_handle* hs, int n, dfb_graph* out) {
+  if (!hs || n < 1 || !out) return DFB_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return DFB_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return DFB_ERR_INVALID_ARG;
+    if (!hs[i]->inFrame) return DFB_ERR_STATE;
+    if (hs[i]->cfg.dtype != hs[0]->cfg.dtype) return DFB_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    const int st = check_trees(hs[i]);
+    if (st != DFB_OK) return st;
+  }
+  for (int i = 0; i < n; ++i) {
+    const int st = allocate(hs[i]);
+    if (st != DFB_OK) return st;
+    if (hs[i]->lastStreamSet) cudaEventSynchronize(hs[i]->frameDone);
+    if (hs[i]->hostCopies) cudaEventSynchronize(hs[i]->copyDone);
+  }
+  dfb_graph_t* g = new (std::nothrow) dfb_graph_t();
+  if (!g) return DFB_ERR_OOM;
+  g->hs.assign(hs, hs + n);
+  g->dtype = hs[0]->cfg.dtype;
+  std::vector<FragRec> recs;
+  std::vector<FrameArgs> fa((size_t)n);
+  std::vector<int> itemBase((size_t)n + 1);
+  int tileBase = 0, items = 0;
+  for (int i = 0; i < n; ++i) {
+    dfb_ctx* h = hs[i];
+    g->anyAcc |= (h->cfg.flags & DFB_FLAG_ACCUMULATE) != 0;
+    for (const FragRec& fr : h->recs) {
+      FragRec r = fr;
+      r.tile += (uint32_t)tileBase;
+      r.frame = (uint32_t)i;
+      recs.push_back(r);
+    }
+    itemBase[i] = items;
+    tileBase += h->nTiles;
+  }
+  g->nRec = (int)recs.size();
+  g->nTiles = tileBase;
+  cudaError_t e = cudaSuccess;
+  const size_t rc = recs.empty() ? 1 : recs.size();
+  e = dalloc(&g->dRecs, rc);
+  if (e == cudaSuccess) e = dalloc(&g->tmp, rc);
+  if (e == cudaSuccess) e = dalloc(&g->srecs, rc);
+  if (e == cudaSuccess) e = dalloc(&g->blocks, (size_t)tileBase);
+  if (e == cudaSuccess) e = dalloc(&g->counts, (size_t)tileBase);
+  if (e == cudaSuccess) e = dalloc(&g->offsets, (size_t)tileBase);
+  if (e == cudaSuccess) e = dalloc(&g->cursor, (size_t)tileBase);
+  if (e == cudaSuccess) e = dalloc(&g->dFrames, (size_t)n);
+  if (e == cudaSuccess) e = dalloc(&g->dItemBase, (size_t)n + 1);
+  if (e == cudaSuccess) e = dalloc(&g->err, 1);
+  if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    graph_free(g);
+    return cuda_status(e);
+  }
+  tileBase = 0;
+  for (int i = 0; i < n; ++i) {
+    fill_frame_args(hs[i], fa[i], tileBase, g->srecs, g->blocks);
+    itemBase[i] = items;
+    items += hs[i]->nTiles * fa[i].chunks;
+    tileBase += hs[i]->nTiles;
+  }
+  itemBase[n] = items;
+  g->items = items;
+  if (!recs.empty())
+    e = cudaMemcpy(g->dRecs, recs.data(), sizeof(FragRec) * recs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(g->dFrames, fa.data(), sizeof(FrameArgs) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(g->dItemBase, itemBase.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->capStream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    graph_free(g);
+    return cuda_status(e);
+  }
+  g->tune = hs[0]->tune;
+  const int st = graph_capture(g);
+  if (st != DFB_OK) {
+    graph_free(g);
+    return st;
+  }
+  for (int i = 0; i < n; ++i) {
+    dfb_ctx* h = hs[i];
+    finish_stats(h);
+    h->stats = h->pendingStats;
+    h->accumN = h->pendingN;
+    h->inFrame = false;
+  }
+  *out = g;
+  return DFB_OK;
+}
+
+int dfb_graph_launch(dfb_graph g, void* stream) {
+  if (!g || !g->exec) return DFB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaGraphLaunch(g->exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(g->done, s);
+  for (size_t i = 0; i < g->hs.size() && e == cudaSuccess; ++i) {
+    dfb_ctx* h = g->hs[i];
+    e = cudaEventRecord(h->frameDone, s);
+    h->lastStream = s;
+    h->lastStreamSet = true;
+    h->haveFrame = true;
+    h->lastErr = g->err;
+    h->launches += (g->nRec ? 4 : 2) + (g->anyAcc ? 2 : 1);
+  }
+  g->launched = true;
+  return cuda_status(e);
+}
+
+int dfb_graph_set_tuning(dfb_graph g, int ring_kb, int ctas_per_sm) {
+  if (!g || ring_kb < 0 || ring_kb > 227 || ctas_per_sm < 0 || ctas_per_sm > 2 ||
+      (ring_kb == 0) != (ctas_per_sm == 0))
+    return DFB_ERR_INVALID_ARG;
+  if (g->launched) cudaEventSynchronize(g->done);
+  g->tune = dfb::TuneParams{ring_kb, ctas_per_sm};
+  return graph_capture(g);
+}
+
+int dfb_graph_autotune(dfb_graph g, void* stream, int reps, int* ring_kb, int* ctas_per_sm,
+                       float* best_ms) {
+  if (!g || reps < 1) return DFB_ERR_INVALID_ARG;
+  static const int cand[][2] = {{110, 2}, {100, 2}, {220, 1}, {160, 1}, {128, 1}};
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  float best = 1e30f;
+  dfb::TuneParams bestT = dfb::default_tune(g->dtype);
+  for (const auto& c : cand) {
+    if (e != cudaSuccess) break;
+    if (dfb_graph_set_tuning(g, c[0], c[1]) != DFB_OK) continue;  // shape does not fit
+    e = cudaGraphLaunch(g->exec, s);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(g->exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && ms / reps < best) {
+      best = ms / reps;
+      bestT = dfb::TuneParams{c[0], c[1]};
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int st = dfb_graph_set_tuning(g, bestT.ringKB, bestT.ctasPerSm);
+  if (st != DFB_OK) return st;
+  for (dfb_ctx* h : g->hs) h->tune = bestT;
+  if (ring_kb) *ring_kb = bestT.ringKB;
+  if (ctas_per_sm) *ctas_per_sm = bestT.ctasPerSm;
+  if (best_ms) *best_ms = best;
+  return DFB_OK;
+}
+
+int dfb_graph_destroy(dfb_graph g) {
+  if (!g) return DFB_OK;
+  graph_free(g);
+  return DFB_OK;
+}
+
+}  // extern "C"

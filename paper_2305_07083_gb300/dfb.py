@@ -103,6 +103,12 @@ def lib():
         "dfb_set_tuning": (C.c_int, [H, C.c_int, C.c_int]),
         "dfb_set_wait_limit": (C.c_int, [H, C.c_double]),
         "dfb_inject_stall": (C.c_int, [H, C.c_int]),
+        "dfb_graph_create": (C.c_int, [P, C.c_int, C.POINTER(H)]),
+        "dfb_graph_launch": (C.c_int, [H, P]),
+        "dfb_graph_set_tuning": (C.c_int, [H, C.c_int, C.c_int]),
+        "dfb_graph_autotune": (C.c_int, [H, P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(C.c_float)]),
+        "dfb_graph_destroy": (C.c_int, [H]),
         "dfb_error_string": (C.c_char_p, [C.c_int]),
         "dfb_version": (C.c_int, []),
     }
@@ -317,3 +323,30 @@ def dfb_inject_stall(h, item):
 
 def dfb_set_tuning(h, ring_kb=0, ctas_per_sm=0):
     return _check(lib().dfb_set_tuning(h, int(ring_kb), int(ctas_per_sm)), "dfb_set_tuning")
+
+
+def dfb_graph_create(handles):
+    arr = (H * len(handles))(*[h.value if isinstance(h, H) else h for h in handles])
+    g = H()
+    _check(lib().dfb_graph_create(C.addressof(arr), len(handles), C.byref(g)), "dfb_graph_create")
+    return g
+
+
+def dfb_graph_launch(g, stream=None):
+    return _check(lib().dfb_graph_launch(g, _stream(stream)), "dfb_graph_launch")
+
+
+def dfb_graph_set_tuning(g, ring_kb, ctas_per_sm):
+    return _check(lib().dfb_graph_set_tuning(g, int(ring_kb), int(ctas_per_sm)),
+                  "dfb_graph_set_tuning")
+
+
+def dfb_graph_autotune(g, stream=None, reps=5):
+    r, c, ms = C.c_int(), C.c_int(), C.c_float()
+    _check(lib().dfb_graph_autotune(g, _stream(stream), int(reps), C.byref(r), C.byref(c),
+                                    C.byref(ms)), "dfb_graph_autotune")
+    return {"ring_kb": r.value, "ctas_per_sm": c.value, "ms": ms.value}
+
+
+def dfb_graph_destroy(g):
+    return _check(lib().dfb_graph_destroy(g), "dfb_graph_destroy")

@@ -1,0 +1,111 @@
+"""Batched compositing: several frames of different sizes in one persistent
+launch (dfb_end_frames), and the same work replayed from a CUDA graph, must
+give exactly the per-frame results (work items are independent and each is
+computed the same way), which match the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+from harness import scenes
+from oracle import dfb_oracle as o
+from paper_2305_07083_gb300 import dfb as D
+
+from tests.gpu_helpers import GpuFrameBuffer
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def mixed_frames(dtype):
+    """(scene, mode) pairs of different sizes, tile sizes and fragment counts,
+    including tiles with more fragments than the kernel stages."""
+    out = []
+    out.append((scenes.scene_data_parallel(256, 192, 64, (3, 3, 3), seed=31, jitter_sigma=0.0),
+                D.DFB_BLEND_DEPTH))
+    counts = np.random.default_rng(32).integers(0, 6, 13 * 9)
+    counts[5] = 40                                   # streamed work items
+    out.append((scenes.random_scene(200, 136, 16, counts, seed=32, special_depths=True),
+                D.DFB_BLEND_DEPTH))
+    out.append((scenes.scene_data_parallel(128, 128, 32, (2, 2, 2), seed=33, jitter_sigma=0.0),
+                D.DFB_BLEND_ORDERED))
+    counts = np.random.default_rng(34).integers(0, 20, 4)
+    out.append((scenes.random_scene(64, 64, 32, counts, seed=34, depth_levels=4),
+                D.DFB_ZCOMPOSITE))
+    return out
+
+
+def make_buffers(frames, dtype):
+    fbs = []
+    for sc, mode in frames:
+        stored, scales = scenes.store_rgba(sc.rgba, dtype)
+        fb = GpuFrameBuffer(sc.W, sc.H, sc.T, mode, dtype)
+        fb.begin(0)
+        fb.submit_pool(sc.tile_ids, sc.keys, stored, sc.depth, scales)
+        fb.stored, fb.scales = stored, scales
+        fbs.append(fb)
+    return fbs
+
+
+def outputs(fb):
+    return fb.color(), fb.rgba8()
+
+
+@pytest.mark.parametrize("dtype", [D.DFB_F32, D.DFB_F16])
+def test_batch_equals_individual_frames_and_oracle(dtype):
+    frames = mixed_frames(dtype)
+    alone = []
+    for fb in make_buffers(frames, dtype):
+        fb.end()
+        alone.append(outputs(fb))
+    fbs = make_buffers(frames, dtype)
+    D.dfb_end_frames([fb.h for fb in fbs])
+    for (sc, mode), fb, (c0, p0) in zip(frames, fbs, alone):
+        c1, p1 = outputs(fb)
+        np.testing.assert_array_equal(c1, c0)
+        np.testing.assert_array_equal(p1, p0)
+        want = o.composite_frame(sc.W, sc.H, sc.T, mode, sc.tile_ids, sc.keys,
+                                 o.dequantize(fb.stored, dtype, fb.scales), sc.depth)
+        if mode == D.DFB_ZCOMPOSITE:
+            np.testing.assert_array_equal(c1.astype(np.float64), want)
+        else:
+            assert np.max(np.abs(c1 - want)) <= TOL
+
+
+def test_graph_replays_equal_individual_frames():
+    dtype = D.DFB_F16
+    frames = mixed_frames(dtype)
+    alone = []
+    for fb in make_buffers(frames, dtype):
+        fb.end()
+        alone.append(outputs(fb))
+    fbs = make_buffers(frames, dtype)
+    g = D.dfb_graph_create([fb.h for fb in fbs])
+    try:
+        for _ in range(2):
+            D.dfb_graph_launch(g)
+            for fb, (c0, p0) in zip(fbs, alone):
+                c1, p1 = outputs(fb)
+                np.testing.assert_array_equal(c1, c0)
+                np.testing.assert_array_equal(p1, p0)
+        best = D.dfb_graph_autotune(g, None, 2)
+        assert best["ring_kb"] > 0 and best["ctas_per_sm"] in (1, 2) and best["ms"] > 0
+        D.dfb_graph_launch(g)
+        for fb, (c0, p0) in zip(fbs, alone):
+            np.testing.assert_array_equal(outputs(fb)[0], c0)
+    finally:
+        D.dfb_graph_destroy(g)
+
+
+def test_graph_rejects_mixed_dtypes_and_closed_frames():
+    a = GpuFrameBuffer(64, 64, 16, D.DFB_BLEND_DEPTH, D.DFB_F32)
+    b = GpuFrameBuffer(64, 64, 16, D.DFB_BLEND_DEPTH, D.DFB_F16)
+    a.begin(0)
+    b.begin(0)
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_graph_create([a.h, b.h])
+    assert e.value.code == D.DFB_ERR_INVALID_ARG
+    c = GpuFrameBuffer(64, 64, 16, D.DFB_BLEND_DEPTH, D.DFB_F32)
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_graph_create([a.h, c.h])
+    assert e.value.code == D.DFB_ERR_STATE
