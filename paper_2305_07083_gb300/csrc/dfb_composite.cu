@@ -316,12 +316,34 @@ __device__ __forceinline__ bool composite_staged(int mode, int n, int P, const u
     const float4 f = Px<DT>::global(meta->rgba[i], p, meta->scale[i]);
     c0 = f.x; c1 = f.y; c2 = f.z; al = f.w;
   } else {
-    // Insertion sort of fragment indices (4-bit slots of `perm`) by depth
-    // key.  The list arrives in key order, so ties stay in (key, submit
-    // index) order, and for bricks whose key order is their depth order
-    // every step is an append.  Fragments empty at this pixel (depth +inf,
-    // which sort after every finite depth) go to a second list kept in list
-    // order and blended last, so they never cause an insertion.
+    // Key pass: depth keys in list order, a mask of fragments empty at this
+    // pixel (depth +inf, which sort after every finite depth) and whether
+    // the finite depths already follow the list's (key, submit index) order.
+    // For bricks whose key order is their depth order that is the common
+    // case: the blend order is then the finite fragments in list order
+    // followed by the empty ones, with no sorting at all.
+    uint32_t infMask = 0, last = 0;
+    bool inOrder = true;
+    for (int i = 0; i < n; ++i) {
+      const uint32_t key = depth_bits(sD[i * P + t]);
+      const bool isInf = key == kInfBits;
+      infMask |= isInf ? (1u << i) : 0u;
+      inOrder = inOrder && (isInf || key >= last);
+      last = isInf ? last : key;
+    }
+    if (inOrder) {
+      for (int i = 0; i < n; ++i)
+        if (!((infMask >> i) & 1u))
+          over(Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]), c0, c1, c2, al);
+      for (int i = 0; i < n; ++i)
+        if ((infMask >> i) & 1u)
+          over(Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]), c0, c1, c2, al);
+      return true;
+    }
+    // General case: insertion sort of fragment indices (4-bit slots of
+    // `perm`) by depth key.  The list arrives in key order, so ties stay in
+    // (key, submit index) order; empty fragments go to a second list kept in
+    // list order and blended last.
     uint64_t perm = 0, infs = 0;
     int m = 0, mi = 0;
     uint32_t lastKey = 0;
@@ -330,7 +352,6 @@ __device__ __forceinline__ bool composite_staged(int mode, int n, int P, const u
       const bool isInf = key == kInfBits;
       const bool app = !isInf && (m == 0 || key >= lastKey);
       if (!isInf && !app) {
-        // rare: depth order differs from key order at this pixel
         int j = m - 1;
         while (j > 0 && depth_bits(sD[(int)((perm >> (4 * (j - 1))) & 15u) * P + t]) > key) --j;
         const uint64_t lowMask = (j == 0) ? 0ull : ((1ull << (4 * j)) - 1ull);
