@@ -316,29 +316,38 @@ __device__ __forceinline__ bool composite_staged(int mode, int n, int P, const u
     const float4 f = Px<DT>::global(meta->rgba[i], p, meta->scale[i]);
     c0 = f.x; c1 = f.y; c2 = f.z; al = f.w;
   } else {
-    // Key pass: depth keys in list order, a mask of fragments empty at this
-    // pixel (depth +inf, which sort after every finite depth) and whether
-    // the finite depths already follow the list's (key, submit index) order.
-    // For bricks whose key order is their depth order that is the common
-    // case: the blend order is then the finite fragments in list order
-    // followed by the empty ones, with no sorting at all.
-    uint32_t infMask = 0, last = 0;
-    bool inOrder = true;
-    for (int i = 0; i < n; ++i) {
-      const uint32_t key = depth_bits(sD[i * P + t]);
-      const bool isInf = key == kInfBits;
-      infMask |= isInf ? (1u << i) : 0u;
-      inOrder = inOrder && (isInf || key >= last);
-      last = isInf ? last : key;
-    }
-    if (inOrder) {
-      for (int i = 0; i < n; ++i)
-        if (!((infMask >> i) & 1u))
-          over(Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]), c0, c1, c2, al);
-      for (int i = 0; i < n; ++i)
-        if ((infMask >> i) & 1u)
-          over(Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]), c0, c1, c2, al);
-      return true;
+    // Speculative pass in list order.  For bricks whose key order is their
+    // depth order (the common case) the finite-depth fragments are already
+    // in blend order, so they are blended as they are read while the order
+    // is checked.  Fragments empty at this pixel (depth +inf, which sort
+    // after every finite depth) are not blended here: blending an all-zero
+    // RGBA is an exact no-op anywhere, so only non-zero empty fragments need
+    // the second pass, in list order, after the finite ones.  If the check
+    // fails the pixel starts over on the sorting path below.
+    {
+      uint32_t last = 0, emptyBits = 0;
+      bool inOrder = true;
+      for (int i = 0; i < n; ++i) {
+        const uint32_t key = depth_bits(sD[i * P + t]);
+        const float4 f = Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]);
+        if (key != kInfBits) {
+          inOrder = inOrder && key >= last;
+          last = key;
+          over(f, c0, c1, c2, al);
+        } else {
+          emptyBits |= __float_as_uint(f.x) | __float_as_uint(f.y) | __float_as_uint(f.z) |
+                       __float_as_uint(f.w);
+        }
+      }
+      if (inOrder) {
+        if (emptyBits) {
+          for (int i = 0; i < n; ++i)
+            if (depth_bits(sD[i * P + t]) == kInfBits)
+              over(Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]), c0, c1, c2, al);
+        }
+        return true;
+      }
+      c0 = c1 = c2 = al = 0.0f;
     }
     // General case: insertion sort of fragment indices (4-bit slots of
     // `perm`) by depth key.  The list arrives in key order, so ties stay in
