@@ -344,6 +344,47 @@ def run_batched(dev, stream, steps, warmup):
 
 
 # ----------------------------------------------------------------------------
+# serving: continuous batching of client jobs
+# ----------------------------------------------------------------------------
+def run_serving(dev, stream, duration_s):
+    import torch
+    from harness import scenes
+    from paper_2305_07083_gb300 import dfb as D
+    from paper_2305_07083_gb300 import serving as S
+
+    def to_f16(rgba, n, P):
+        dst = torch.empty(max(n, 1) * P * 4, dtype=torch.float16, device=dev)
+        if n:
+            D.dfb_convert_tiles(rgba, dst, None, n, P, D.DFB_F16, stream)
+        return dst
+    tpl = scenes.serving_templates(dev, seed=0, convert=to_f16)
+    torch.cuda.synchronize()
+    # 4 clients, each with exponential gaps of mean 8 ms: 2 ms between
+    # arrivals overall
+    arrivals = S.poisson_arrivals(4, 0.008, duration_s, seed=0)
+    jobs = S.make_jobs(tpl, arrivals, seed=0, accumulate_frames=64)
+    srv = S.Server(budget_bytes=24 << 30, max_slots=64, dtype=D.DFB_F16, stream=stream,
+                   keep_results=True)
+    # warm the framebuffer pool and the kernels on a few jobs first
+    warm = S.make_jobs(tpl, [(0.0, c) for c in range(8)], seed=1, accumulate_frames=2)
+    srv.run(warm)
+    st = srv.run(jobs, time_limit_s=duration_s + 60.0)
+    srv.close()
+    out = st.summary()
+    out.update({"clients": 4, "mean_arrival_gap_ms": 2.0, "arrival_window_s": duration_s,
+                "jobs_submitted": len(jobs),
+                "jobs": {"blend": sum(j.kind == "blend" for j in jobs),
+                         "accumulate": sum(j.kind == "accumulate" for j in jobs)},
+                "workload": "blend jobs: 1024x1024 / 2048x2048 / 4096x1024 frames of 64 to "
+                            "1000 bricks; accumulate jobs: 1024x1024 / 2048x1024, one fragment "
+                            "per tile, 64 passes; FP16 storage; HBM budget 24 GiB, 64 slots",
+                "unit": UNIT})
+    del tpl
+    torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------------------
 # reference arm: the oracle on host cores
 # ----------------------------------------------------------------------------
 def run_reference(args):
@@ -393,6 +434,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f16", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=3.0,
+                    help="arrival window of the serving run (0 skips it)")
     ap.add_argument("--tune", default=None,
                     help="composite launch shape 'ringKB,ctasPerSm' (default: the library's)")
     ap.add_argument("--frames", type=int, default=N_FRAMES,
@@ -519,6 +562,8 @@ def main():
         torch.cuda.empty_cache()
         out.setdefault("variants", {})["batched_f16_graph"] = run_batched(
             dev, stream, max(3, min(args.steps, 20)), args.warmup)
+    if args.serving_seconds > 0 and rank == 0:
+        out.setdefault("variants", {})["serving"] = run_serving(dev, stream, args.serving_seconds)
     out["gpu_launches"] = launches
     out["gpu_launches_note"] = ("kernels launched by libdfb.so inside the timed FP32 region "
                                 "(per frame: 4 bucketing, the composite, the per-tile variance "

@@ -478,3 +478,49 @@ def batch_frames_torch(n_frames=32, seed=0, device="cuda", T=64):
         out.append({"W": W, "H": H, "T": T, "bricks": int(np.prod(grid)), "tile_ids": tid,
                     "keys": key, "rgba": rgba, "depth": depth})
     return out
+
+
+# --- serving workload ---------------------------------------------------------
+def serving_templates(device, seed=0, T=64, convert=None):
+    """Job templates resident on the device.
+
+    blend: data-parallel brick frames of 1024x1024, 2048x2048 and 4096x1024
+    with g x g x g bricks, g in 4..10 (64 to 1000 bricks);
+    accumulate: image-parallel frames of 1024x1024 and 2048x1024 with exactly
+    one opaque fragment tile per image tile, 8 distinct passes each (the
+    64-pass jobs cycle through them).
+    ``convert(rgba_f32, n, P)`` turns FP32 tiles into the storage dtype.
+    Returns {"blend": [(W, H, bricks, frame_dict)], "accumulate": [(W, H, [frame_dict])]}.
+    """
+    import torch
+    out = {"blend": [], "accumulate": []}
+    specs = [(1024, 1024, 4), (2048, 2048, 6), (4096, 1024, 8), (1024, 1024, 10),
+             (2048, 2048, 10), (4096, 1024, 5)]
+    for i, (W, H, g) in enumerate(specs):
+        wide = W > H
+        hi = (2.0, 1.0, 1.0) if wide else (1.0, 1.0, 1.0)
+        grid = (g, g, g)
+        cam = orbit_camera(W, H, 7000 + seed * 100 + i, radius=1.2 if wide else 1.0, hi=hi)
+        tid, key, rgba, depth = brick_scene_torch(W, H, T, brick_grid(grid, hi=hi), cam,
+                                                  7000 + seed * 100 + i, device)
+        n = len(tid)
+        stored = convert(rgba, n, T * T) if convert else rgba
+        out["blend"].append((W, H, g ** 3, {"tile_ids": tid, "keys": key, "rgba": stored,
+                                              "depth": depth, "fragment_pixels": n * T * T}))
+        del rgba
+    gen = torch.Generator(device=device)
+    for j, (W, H) in enumerate([(1024, 1024), (2048, 1024)]):
+        nt = (W // T) * (H // T)
+        passes = []
+        for f in range(8):
+            gen.manual_seed(seed * 991 + j * 31 + f)
+            rgb = torch.rand((nt, T * T, 3), generator=gen, device=device)
+            rgba = torch.cat([rgb, torch.ones((nt, T * T, 1), device=device)], dim=-1)
+            depth = torch.ones((nt, T * T), device=device)
+            stored = convert(rgba, nt, T * T) if convert else rgba
+            passes.append({"tile_ids": np.arange(nt, dtype=np.int32),
+                           "keys": np.zeros(nt, np.float32), "rgba": stored, "depth": depth,
+                           "fragment_pixels": nt * T * T})
+            del rgba, rgb
+        out["accumulate"].append((W, H, passes))
+    return out

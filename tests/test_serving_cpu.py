@@ -1,0 +1,34 @@
+"""Host-side logic of the serving loop: arrivals, job mix and footprints
+(no GPU needed)."""
+
+import numpy as np
+
+from paper_2305_07083_gb300 import dfb as D
+from paper_2305_07083_gb300 import serving as S
+
+
+def test_poisson_arrivals_are_seeded_sorted_and_have_the_mean_gap():
+    a = S.poisson_arrivals(4, 0.008, 2.0, seed=1)
+    b = S.poisson_arrivals(4, 0.008, 2.0, seed=1)
+    assert a == b and a == sorted(a) and {c for _, c in a} == {0, 1, 2, 3}
+    gaps = np.diff([t for t, c in a if c == 0])
+    assert abs(gaps.mean() - 0.008) < 0.002           # about 250 arrivals per client
+
+
+def _fake_templates():
+    f = {"tile_ids": np.arange(4, dtype=np.int32), "keys": np.zeros(4, np.float32),
+         "rgba": None, "depth": None, "fragment_pixels": 4 * 64 * 64}
+    return {"blend": [(256, 256, 8, f)], "accumulate": [(128, 128, [f, f])]}
+
+
+def test_job_mix_and_footprint():
+    arrivals = [(0.001 * i, i % 4) for i in range(200)]
+    jobs = S.make_jobs(_fake_templates(), arrivals, seed=0, accumulate_frames=64)
+    kinds = [j.kind for j in jobs]
+    assert 60 < kinds.count("blend") < 140
+    acc = next(j for j in jobs if j.kind == "accumulate")
+    assert acc.n_frames == 64 and len(acc.frames) == 2
+    # framebuffers (68 B per pixel) + the referenced fragment tiles
+    fp16 = acc.footprint(D.DFB_F16)
+    assert fp16 == 128 * 128 * 68 + 2 * 4 * 64 * 64 * (8 + 4)
+    assert acc.footprint(D.DFB_F32) > fp16
