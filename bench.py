@@ -42,6 +42,7 @@ sys.path.insert(0, ROOT)
 METRIC = "composited fragment-pixels/s & HBM GB/s (% of peak) at 2048², FP32 vs FP16"
 UNIT = "fragment-pixels/s"
 N_FRAMES = 16
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e nominal bandwidth
 WORKLOAD = ("2048x2048 frame, 64x64 tiles, 64 bricks (4x4x4 grid), 60-degree perspective orbit "
             "camera (seed 0), 2-14 fragments per tile, FP32 premultiplied RGBA + FP32 depth, "
             "per-pixel depth sort + front-to-back over, 16-frame progressive accumulation with "
@@ -204,26 +205,29 @@ def timed(run, steps, warmup, stream, dist=None, sampler=None, read_back=None):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     if sampler:
         sampler.start()
     run.D.dfb_read_timing(run.h, reset=True)
     run.D.dfb_set_timing(run.h, True)
     l0 = run.D.dfb_get_stats(run.h)["kernel_launches"]
-    e0.record(stream)
-    for _ in range(steps):
+    ev[0].record(stream)
+    for i in range(steps):
         run.step(stream)
         if read_back is not None:
             read_back()
-    e1.record(stream)
+        ev[i + 1].record(stream)
     torch.cuda.synchronize()
     run.D.dfb_set_timing(run.h, False)
     tm = run.D.dfb_read_timing(run.h, reset=True)
     clocks = sampler.stop() if sampler else None
     if dist is not None:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
+    ms = ev[0].elapsed_time(ev[-1])
+    per = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(steps)])
+    med = float(np.median(per))
+    tm["step_ms_median"] = med
+    tm["step_ms_mad"] = float(np.median(np.abs(per - med)))
     launches = run.D.dfb_get_stats(run.h)["kernel_launches"] - l0
     return ms, tm, clocks, launches
 
@@ -506,8 +510,10 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "l2": "inputs larger than L2 (%.0f MB of fragments per frame)" % (frag_b / 1e6)},
         "gb_per_s_step": (algo_bytes * frames_timed) / (ms / 1e3) / 1e9,
+        "step_ms_median": tm["step_ms_median"], "step_ms_mad": tm["step_ms_mad"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "peak_kind": peak_kind + " (copy, burst)",
+                     "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
                      "traffic": ncu_traffic("composite_f32_2048.md"),
                      "kernel": "k_composite<BLEND_DEPTH,F32>",
                      "algorithmic_bytes_per_launch": algo_bytes,

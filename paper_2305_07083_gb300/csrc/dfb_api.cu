@@ -98,6 +98,19 @@ unsigned long long g_table_devices = 0;  // bit d: table uploaded on device d
 
 }  // namespace
 
+// Device buffers of one frame's bucketing (K1) and its launch header.
+struct BucketSet {
+  unsigned char* dStage = nullptr;  // [FrameHeader][FragRec x recCap], uploaded per frame
+  FragRec* dRecs = nullptr;         // = dStage + kHdrBytes
+  uint32_t* tmp = nullptr;
+  FragRec* srecs = nullptr;         // records sorted per tile (bucketing output)
+  dfb::TileBlock* blocks = nullptr; // per-tile count/offset/first records
+  int *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
+  cudaEvent_t ready = nullptr;      // the bucketing that filled this set has finished
+  cudaEvent_t released = nullptr;   // the composite that read this set has finished
+  bool used = false;
+};
+
 struct dfb_ctx {
   dfb_config cfg{};
   int tilesX = 0, tilesY = 0, nTiles = 0, logT = 0, chunks = 0, tilePixels = 0;
@@ -125,13 +138,12 @@ struct dfb_ctx {
   float4 *color = nullptr, *accum = nullptr, *comp = nullptr, *m2 = nullptr;
   uint32_t* rgba8 = nullptr;
   float *tileVar = nullptr, *varPartial = nullptr;
-  int *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
-  unsigned char* dStage = nullptr;  // [FrameHeader][FragRec x recCap], uploaded per frame
-  FragRec* dRecs = nullptr;         // = dStage + sizeof(FrameHeader)
-  uint32_t* tmp = nullptr;
-  FragRec* srecs = nullptr;         // records sorted per tile (bucketing output)
-  dfb::TileBlock* blocks = nullptr; // per-tile count/offset/first records
+  // Two bucketing sets, used by alternate frames: the bucketing of frame f+1
+  // runs on `bucketStream` while frame f composites from the other set.
+  BucketSet sets[2];
+  int setIdx = 0;
   size_t recCap = 0;
+  cudaStream_t bucketStream = nullptr;
   unsigned* errFlag = nullptr;      // device error word of this handle's launches
   unsigned* lastErr = nullptr;      // error word the last launch touching this handle used
   dfb::TuneParams tune{0, 0};       // {0,0}: the library default
@@ -152,9 +164,9 @@ struct dfb_ctx {
   cudaStream_t lastStream = nullptr;
   bool lastStreamSet = false;
 
-  // tracing: ring of (bucket start, composite start, end) events
+  // tracing: ring of (bucket start, bucket end, composite start, composite end) events
   bool timing = false;
-  std::vector<cudaEvent_t> tev;  // 3 per slot
+  std::vector<cudaEvent_t> tev;  // 4 per slot
   size_t tHead = 0, tCount = 0;
   dfb_timing tSum{};
 };
@@ -201,24 +213,30 @@ cudaError_t dalloc(T** p, size_t count) {
 }
 
 int grow_records(dfb_ctx* h, size_t need) {
-  if (need <= h->recCap && h->dStage) return DFB_OK;
+  if (need <= h->recCap && h->sets[0].dStage) return DFB_OK;
   size_t cap = h->recCap ? h->recCap : 4096;
   while (cap < need) cap *= 2;
-  // The previous frame may still read the old arrays.
+  // Earlier frames may still read the old arrays (the last frame's
+  // composite is ordered after every earlier bucketing and composite).
   if (h->lastStreamSet) cudaEventSynchronize(h->frameDone);
-  cudaFree(h->dStage);
-  cudaFree(h->tmp);
-  cudaFree(h->srecs);
-  h->dStage = nullptr;
-  h->dRecs = nullptr;
-  h->tmp = nullptr;
-  h->srecs = nullptr;
   h->recCap = 0;
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&h->dStage), kHdrBytes + sizeof(FragRec) * cap);
-  if (e == cudaSuccess) e = dalloc(&h->tmp, cap);
-  if (e == cudaSuccess) e = dalloc(&h->srecs, cap);
-  if (e != cudaSuccess) return cuda_status(e);
-  h->dRecs = reinterpret_cast<FragRec*>(h->dStage + kHdrBytes);
+  for (BucketSet& b : h->sets) {
+    cudaFree(b.dStage);
+    cudaFree(b.tmp);
+    cudaFree(b.srecs);
+    b.dStage = nullptr;
+    b.dRecs = nullptr;
+    b.tmp = nullptr;
+    b.srecs = nullptr;
+  }
+  for (BucketSet& b : h->sets) {
+    cudaError_t e =
+        cudaMalloc(reinterpret_cast<void**>(&b.dStage), kHdrBytes + sizeof(FragRec) * cap);
+    if (e == cudaSuccess) e = dalloc(&b.tmp, cap);
+    if (e == cudaSuccess) e = dalloc(&b.srecs, cap);
+    if (e != cudaSuccess) return cuda_status(e);
+    b.dRecs = reinterpret_cast<FragRec*>(b.dStage + kHdrBytes);
+  }
   h->recCap = cap;
   return DFB_OK;
 }
@@ -245,10 +263,19 @@ void free_device(dfb_ctx* h) {
   };
   fr(h->color); fr(h->accum); fr(h->comp); fr(h->m2); fr(h->rgba8);
   fr(h->tileVar); fr(h->varPartial);
-  fr(h->counts); fr(h->offsets); fr(h->cursor);
-  fr(h->dStage); fr(h->tmp); fr(h->srecs); fr(h->readTmp); fr(h->errFlag); fr(h->blocks);
-  h->dRecs = nullptr;
+  fr(h->readTmp); fr(h->errFlag);
+  for (BucketSet& b : h->sets) {
+    fr(b.counts); fr(b.offsets); fr(b.cursor);
+    fr(b.dStage); fr(b.tmp); fr(b.srecs); fr(b.blocks);
+    b.dRecs = nullptr;
+    if (b.ready) cudaEventDestroy(b.ready);
+    if (b.released) cudaEventDestroy(b.released);
+    b.ready = b.released = nullptr;
+    b.used = false;
+  }
   h->recCap = 0;
+  if (h->bucketStream) cudaStreamDestroy(h->bucketStream);
+  h->bucketStream = nullptr;
   for (int b = 0; b < 2; ++b) {
     if (h->hRecs[b]) cudaFreeHost(h->hRecs[b]);
     h->hRecs[b] = nullptr;
@@ -291,16 +318,21 @@ int allocate(dfb_ctx* h) {
     if (e == cudaSuccess) e = dalloc(&h->comp, tpx);
     if (e == cudaSuccess) e = dalloc(&h->m2, tpx);
   }
-  if (e == cudaSuccess) e = dalloc(&h->blocks, h->nTiles);
   if (e == cudaSuccess && (f & DFB_FLAG_PACK_RGBA8)) e = dalloc(&h->rgba8, px);
   if (e == cudaSuccess) e = dalloc(&h->tileVar, h->nTiles);
   if (e == cudaSuccess) e = dalloc(&h->varPartial, (size_t)h->nTiles * ((h->tilePixels + 31) / 32));
   if (e == cudaSuccess) e = dalloc(&h->errFlag, 1);
   if (e == cudaSuccess) e = cudaMemset(h->errFlag, 0, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(h->tileVar, 0, sizeof(float) * h->nTiles);
-  if (e == cudaSuccess) e = dalloc(&h->counts, h->nTiles);
-  if (e == cudaSuccess) e = dalloc(&h->offsets, h->nTiles);
-  if (e == cudaSuccess) e = dalloc(&h->cursor, h->nTiles);
+  for (BucketSet& b : h->sets) {
+    if (e == cudaSuccess) e = dalloc(&b.blocks, h->nTiles);
+    if (e == cudaSuccess) e = dalloc(&b.counts, h->nTiles);
+    if (e == cudaSuccess) e = dalloc(&b.offsets, h->nTiles);
+    if (e == cudaSuccess) e = dalloc(&b.cursor, h->nTiles);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.released, cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->bucketStream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->copyStream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->copyDone, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->frameDone, cudaEventDisableTiming);
@@ -821,11 +853,12 @@ constexpr size_t kTimingSlots = 128;
 // Fold the oldest recorded slot into the running sums (waits for it).
 int harvest_one(dfb_ctx* h) {
   const size_t slot = (h->tHead + kTimingSlots - h->tCount) % kTimingSlots;
-  cudaEvent_t* e = &h->tev[3 * slot];
-  cudaError_t r = cudaEventSynchronize(e[2]);
+  cudaEvent_t* e = &h->tev[4 * slot];
+  cudaError_t r = cudaEventSynchronize(e[3]);
   float b = 0.f, c = 0.f;
+  if (r == cudaSuccess) r = cudaEventSynchronize(e[1]);
   if (r == cudaSuccess) r = cudaEventElapsedTime(&b, e[0], e[1]);
-  if (r == cudaSuccess) r = cudaEventElapsedTime(&c, e[1], e[2]);
+  if (r == cudaSuccess) r = cudaEventElapsedTime(&c, e[2], e[3]);
   if (r != cudaSuccess) return cuda_status(r);
   h->tSum.launches += 1;
   h->tSum.bucket_ms += b;
@@ -838,12 +871,12 @@ int harvest_one(dfb_ctx* h) {
 cudaEvent_t* timing_slot(dfb_ctx* h) {
   if (!h->timing) return nullptr;
   if (h->tev.empty()) {
-    h->tev.assign(3 * kTimingSlots, nullptr);
+    h->tev.assign(4 * kTimingSlots, nullptr);
     for (auto& e : h->tev)
       if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
   }
   if (h->tCount == kTimingSlots && harvest_one(h) != DFB_OK) return nullptr;
-  cudaEvent_t* e = &h->tev[3 * h->tHead];
+  cudaEvent_t* e = &h->tev[4 * h->tHead];
   h->tHead = (h->tHead + 1) % kTimingSlots;
   h->tCount += 1;
   return e;
@@ -867,33 +900,51 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
   if (st != DFB_OK) return st;
   const int buf = stage_records(h, &staged);
   if (buf < 0) return buf;
+  BucketSet& b = h->sets[h->setIdx];
+  h->setIdx ^= 1;
   const size_t n = h->recs.size();
   // header: the frame's arguments + the item prefix of a one-frame launch
   FrameHeader* hdr = reinterpret_cast<FrameHeader*>(staged);
-  fill_frame_args(h, hdr->fa, 0, h->srecs, h->blocks);
+  fill_frame_args(h, hdr->fa, 0, b.srecs, b.blocks);
   hdr->itemBase[0] = 0;
   hdr->itemBase[1] = h->nTiles * hdr->fa.chunks;
   const int items = hdr->itemBase[1];
-  FrameArgs* dFa = reinterpret_cast<FrameArgs*>(h->dStage);
-  const int* dItemBase = reinterpret_cast<const int*>(h->dStage + offsetof(FrameHeader, itemBase));
+  FrameArgs* dFa = reinterpret_cast<FrameArgs*>(b.dStage);
+  const int* dItemBase = reinterpret_cast<const int*>(b.dStage + offsetof(FrameHeader, itemBase));
+  // The bucketing reads only library-owned buffers, so it runs on the side
+  // stream, overlapping the previous frame's composite; under stream capture
+  // everything stays on `s`.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool side = cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+                    cap == cudaStreamCaptureStatusNone;
+  if (!side) cudaGetLastError();
   cudaError_t e = cudaSuccess;
-  if (h->lastStreamSet && h->lastStream != s) e = cudaStreamWaitEvent(s, h->frameDone, 0);
-  if (e == cudaSuccess && h->hostCopies) e = cudaStreamWaitEvent(s, h->copyDone, 0);
+  cudaStream_t bs = side ? h->bucketStream : s;
+  if (e == cudaSuccess && h->lastStreamSet && h->lastStream != s)
+    e = cudaStreamWaitEvent(s, h->frameDone, 0);
+  if (e == cudaSuccess && side && b.used) e = cudaStreamWaitEvent(bs, b.released, 0);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->dStage, staged, kHdrBytes + sizeof(FragRec) * n, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaEventRecord(h->hRecDone[buf], s);
+    e = cudaMemcpyAsync(b.dStage, staged, kHdrBytes + sizeof(FragRec) * n, cudaMemcpyHostToDevice,
+                        bs);
+  if (e == cudaSuccess) e = cudaEventRecord(h->hRecDone[buf], bs);
   cudaEvent_t* ev = timing_slot(h);
-  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], bs);
   if (e == cudaSuccess)
-    e = dfb::launch_bucket(h->dRecs, (int)n, h->nTiles, h->counts, h->offsets, h->cursor, h->tmp,
-                           h->srecs, h->blocks, s);
-  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+    e = dfb::launch_bucket(b.dRecs, (int)n, h->nTiles, b.counts, b.offsets, b.cursor, b.tmp,
+                           b.srecs, b.blocks, bs);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], bs);
+  if (e == cudaSuccess && side) e = cudaEventRecord(b.ready, bs);
+  if (e == cudaSuccess && side) e = cudaStreamWaitEvent(s, b.ready, 0);
+  if (e == cudaSuccess && h->hostCopies) e = cudaStreamWaitEvent(s, h->copyDone, 0);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
   if (e == cudaSuccess)
     e = dfb::launch_composite(dFa, dItemBase, 1, items, h->nTiles,
                               (h->cfg.flags & DFB_FLAG_ACCUMULATE) != 0, h->cfg.dtype, tune_of(h),
                               ctl_of(h), s);
-  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
+  if (e == cudaSuccess) e = cudaEventRecord(b.released, s);
   if (e == cudaSuccess) e = cudaEventRecord(h->frameDone, s);
+  b.used = true;
   h->launches += (n ? 4 : 2) + ((h->cfg.flags & DFB_FLAG_ACCUMULATE) ? 2 : 1);
   h->lastErr = h->errFlag;
   h->stallItem = -1;
@@ -947,10 +998,11 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
     e = dfb::launch_bucket(b.dRecs, (int)nRec, (int)nTiles, b.counts, b.offsets, b.cursor, b.tmp,
                            b.srecs, b.blocks, s);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
   if (e == cudaSuccess)
     e = dfb::launch_composite(b.dFrames, b.dItemBase, n, items, tileBase, anyAcc, dtype,
                               tune_of(hs[0]), ctl_of(hs[0]), s);
-  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
   if (e == cudaSuccess) e = cudaEventRecord(b.done, s);
   b.used = true;
   hs[0]->launches += (nRec ? 4 : 2) + (anyAcc ? 2 : 1);

@@ -148,6 +148,35 @@ def test_accumulation_variance_and_pack():
     assert fb.stats()["accumulated"] == nf
 
 
+def test_back_to_back_frames_on_alternating_streams():
+    """Frames queued without a read in between (the bucketing of each frame
+    overlaps the previous composite on the library's side stream), with
+    different fragment sets per frame and the user stream switching every
+    frame: every frame's colour and the accumulation match the oracle."""
+    torch = pytest.importorskip("torch")
+    W, H, T = 160, 96, 16
+    n_tiles = (W // T) * (H // T)
+    fb = GpuFrameBuffer(W, H, T, D.DFB_BLEND_DEPTH, flags=D.DFB_FLAGS_DEFAULT)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    imgs, colors = [], []
+    for f in range(7):
+        counts = np.random.default_rng(70 + f).integers(0, 7, n_tiles)
+        sc = scenes.random_scene(W, H, T, counts, seed=70 + f)
+        fb.begin(accumulate=f > 0)
+        fb.submit_pool(sc.tile_ids, sc.keys, sc.rgba, sc.depth)
+        streams[f % 2].wait_stream(torch.cuda.current_stream())  # uploads done
+        fb.end(streams[f % 2])
+        imgs.append(o.composite_frame(W, H, T, o.BLEND_DEPTH, sc.tile_ids, sc.keys,
+                                      sc.rgba.astype(np.float64), sc.depth))
+        if f in (2, 6):
+            colors.append((f, fb.color()))
+    for f, c in colors:
+        check_color(c, imgs[f], D.DFB_BLEND_DEPTH)
+    assert np.max(np.abs(fb.accum() - o.accumulate(imgs))) <= TOL
+    px, _ = fb.variance()
+    assert np.max(np.abs(px - o.variance(imgs))) <= 1e-6
+
+
 def test_accumulate_reset_and_single_frame_variance():
     sc = scenes.scene_single_frame_256(seed=1)
     fb = GpuFrameBuffer(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH)
