@@ -79,6 +79,26 @@ def cpu_oracle_rate(sc, rgba, n_tiles_sample, pool, min_seconds=0.0, max_passes=
     return fpx * passes / dt, fpx * passes, dt, len(tiles) * passes
 
 
+# ----------------------------------------------------------------------------
+# ranks: one independent replica per GPU; the only collective is the max of
+# the timed interval
+# ----------------------------------------------------------------------------
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's ``x`` (all ranks get it)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, world, ms_max):
+    """Units all ranks processed (each rank the same fixed amount: weak
+    scaling) per second of the slowest rank's timed interval."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def make_pool():
     import multiprocessing as mp
     cores = len(os.sched_getaffinity(0))
@@ -480,12 +500,9 @@ def main():
     sampler = ClockSampler(local) if rank == 0 else None
     ms, tm, clocks, launches = timed(run, args.steps, args.warmup, stream, dist, sampler)
     st = D.dfb_get_stats(run.h)
-    ms_t = torch.tensor([ms], device=dev)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
-    value = world * fpx_frame * N_FRAMES * args.steps / (ms / 1e3)
+    value = whole_job_value(fpx_frame * N_FRAMES * args.steps, world, ms)
     frames_timed = args.steps * N_FRAMES
     comp_ms = tm["composite_ms"] / max(tm["launches"], 1)
     # algorithmic bytes of one composite launch: fragment bytes + framebuffer
