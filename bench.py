@@ -392,7 +392,7 @@ def run_serving(dev, stream, duration_s):
     # warm the framebuffer pool and the kernels on a few jobs first
     warm = S.make_jobs(tpl, [(0.0, c) for c in range(8)], seed=1, accumulate_frames=2)
     srv.run(warm)
-    st = srv.run(jobs, time_limit_s=duration_s + 60.0)
+    st = srv.run(jobs, time_limit_s=duration_s + 60.0, trace=True)
     srv.close()
     out = st.summary()
     out.update({"clients": 4, "mean_arrival_gap_ms": 2.0, "arrival_window_s": duration_s,
@@ -461,7 +461,7 @@ def main():
     ap.add_argument("--serving-seconds", type=float, default=3.0,
                     help="arrival window of the serving run (0 skips it)")
     ap.add_argument("--tune", default=None,
-                    help="composite launch shape 'ringKB,ctasPerSm' (default: the library's)")
+                    help="composite launch shape 'ringKB,ctasPerSm,groups' (default: the library's)")
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="distinct resident frames (the 16-frame step cycles through them); "
                          "fewer frames only to keep profiler captures small")

@@ -191,6 +191,41 @@ DFB_API int dfb_submit_tiles_ex(dfb_handle h, int n, const dfb_tile_desc* tiles,
    without waiting.  Errors: STATE, INCOMPLETE, OOM, CUDA. */
 DFB_API int dfb_end_frame(dfb_handle h, void* stream);
 
+/* ---- Prepared submissions ------------------------------------------------------
+   A producer that renders into the same tile buffers every frame (the
+   progressive-refinement passes of Sec. 4.1, the per-rank brick buffers of
+   Sec. 4.2) submits the same list each frame.  A dfb_tileset is that list --
+   the arguments of one dfb_submit_tiles call with device pointers --
+   validated once and kept as ready records, so submitting it again costs one
+   copy of 32 bytes per tile.  The set borrows the device pointers: they must
+   stay valid (their contents may change) while any frame that used the set
+   can still run. */
+typedef struct dfb_tileset_t* dfb_tileset;
+
+/* Validate n generation-1 tiles against the geometry and dtype of `h` (as
+   dfb_submit_tiles with DFB_PTR_DEVICE does) and keep them as a set usable
+   with every handle of the same width, height, tile size and dtype.  Arrays
+   are host arrays of length n (n >= 0); scales may be NULL unless the dtype
+   is FP8.  Errors: INVALID_ARG, TILE_RANGE, OOM. */
+DFB_API int dfb_tileset_create(dfb_handle h, int n, const int* tile_ids, const float* order_keys,
+                               const void* const* rgba, const float* const* depth,
+                               const float* scales, dfb_tileset* out);
+DFB_API int dfb_tileset_destroy(dfb_tileset s);
+
+/* Submit a prepared set into the open frame of `h`: the same records, in the
+   same order, as the dfb_submit_tiles call it was made from.  Errors:
+   INVALID_ARG (null, or a set made for another geometry or dtype), STATE. */
+DFB_API int dfb_submit_tileset(dfb_handle h, dfb_tileset s);
+
+/* One step of a compositing server: for every i, begin a frame on hs[i]
+   (accumulating onto its previous frames if accumulate[i] != 0; accumulate
+   may be NULL = no accumulation), submit sets[i], then end all frames with
+   one batched launch on `stream` (dfb_end_frames).  Everything is validated
+   before any frame is begun: handles distinct and not inside a frame, sets
+   matching their handles, one dtype.  Errors: INVALID_ARG, STATE, OOM, CUDA. */
+DFB_API int dfb_run_frames(const dfb_handle* hs, const dfb_tileset* sets, const int* accumulate,
+                           int n, void* stream);
+
 /* Composite the open frames of several handles with one persistent launch on
    `stream`: the batched form of dfb_end_frame.  Every handle is validated
    first; on any error nothing is launched and the first error is returned.
@@ -309,23 +344,28 @@ DFB_API int dfb_graph_create(const dfb_handle* hs, int n, dfb_graph* out);
 DFB_API int dfb_graph_launch(dfb_graph g, void* stream);
 
 /* Re-capture with another composite launch shape (see dfb_set_tuning). */
-DFB_API int dfb_graph_set_tuning(dfb_graph g, int ring_kb, int ctas_per_sm);
+DFB_API int dfb_graph_set_tuning(dfb_graph g, int ring_kb, int ctas_per_sm, int groups);
 
 /* Autotuner: time `reps` replays of each candidate launch shape (ring size =
-   pipeline depth, CTAs per SM) on `stream`, keep the fastest, and report it
-   (either pointer may be NULL).  The graph's handles get the same tuning for
-   their later dfb_end_frame calls.  Errors: INVALID_ARG, CUDA. */
+   pipeline depth, CTAs per SM, consumer groups per CTA) on `stream`, keep the
+   fastest, and report it (any pointer may be NULL).  The graph's handles get
+   the same tuning for their later dfb_end_frame calls.  Errors: INVALID_ARG,
+   CUDA. */
 DFB_API int dfb_graph_autotune(dfb_graph g, void* stream, int reps, int* ring_kb,
-                               int* ctas_per_sm, float* best_ms);
+                               int* ctas_per_sm, int* groups, float* best_ms);
 
 /* Free the graph and its buffers (waits for its last launch). */
 DFB_API int dfb_graph_destroy(dfb_graph g);
 
 /* Launch shape of this handle's composite kernel: shared-memory ring size per
-   CTA in KB (how many work items are in flight) and persistent CTAs per SM
-   (1 or 2).  0, 0 restores the library default.  Values that do not fit the
-   device are clamped at launch.  Errors: INVALID_ARG. */
-DFB_API int dfb_set_tuning(dfb_handle h, int ring_kb, int ctas_per_sm);
+   CTA in KB (how many work items are in flight), persistent CTAs per SM, and
+   consumer groups per CTA (work items composited at once by one CTA).  The
+   shapes built are (groups, CTAs per SM) = (1, 2), (2, 2), (1, 3), (2, 1)
+   and (3, 1).  0, 0, 0 restores the library default.  A ring larger
+   than the CTAs can share is clamped at launch; one too small for the
+   largest work item of the dtype makes the launch fail with DFB_ERR_CUDA.
+   Errors: INVALID_ARG (a shape not in the list). */
+DFB_API int dfb_set_tuning(dfb_handle h, int ring_kb, int ctas_per_sm, int groups);
 
 /* Bound on every wait inside the composite kernel (default 2 s).  A wait
    that runs out makes the kernel give up, and the next dfb_sync (or host

@@ -129,6 +129,8 @@ struct dfb_ctx {
   std::vector<int> recvGen1, childGen1;  // generation-1 arrivals per tile
   std::vector<std::vector<GenCount>> deeper;  // generations >= 2, per tile (lazy)
   std::vector<int> touchedDeeper;
+  std::vector<int> fragCount;  // records per tile in the open frame (all generations)
+  std::vector<int> longTiles;  // tiles with more than kStageFragments records
   bool hostCopies = false;
   int64_t launches = 0;  // kernels launched by this handle
   dfb_frame_stats stats{};
@@ -146,7 +148,7 @@ struct dfb_ctx {
   cudaStream_t bucketStream = nullptr;
   unsigned* errFlag = nullptr;      // device error word of this handle's launches
   unsigned* lastErr = nullptr;      // error word the last launch touching this handle used
-  dfb::TuneParams tune{0, 0};       // {0,0}: the library default
+  dfb::TuneParams tune{0, 0, 0};    // {0,0,0}: the library default
   unsigned long long waitNs = 2000000000ull;  // bound on every device-side wait
   int stallItem = -1;               // fault injection for tests (next launch only)
   float4* readTmp = nullptr;  // normalise / variance output for host reads
@@ -212,6 +214,12 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (count ? count : 1));
 }
 
+// Upload buffer of one frame:
+//   [FrameHeader][FragRec x records][long tiles x L][their item prefix x L+1]
+size_t stage_bytes(const dfb_ctx* h, size_t records) {
+  return kHdrBytes + sizeof(FragRec) * records + sizeof(int) * (2 * (size_t)h->nTiles + 1);
+}
+
 int grow_records(dfb_ctx* h, size_t need) {
   if (need <= h->recCap && h->sets[0].dStage) return DFB_OK;
   size_t cap = h->recCap ? h->recCap : 4096;
@@ -231,7 +239,7 @@ int grow_records(dfb_ctx* h, size_t need) {
   }
   for (BucketSet& b : h->sets) {
     cudaError_t e =
-        cudaMalloc(reinterpret_cast<void**>(&b.dStage), kHdrBytes + sizeof(FragRec) * cap);
+        cudaMalloc(reinterpret_cast<void**>(&b.dStage), stage_bytes(h, cap));
     if (e == cudaSuccess) e = dalloc(&b.tmp, cap);
     if (e == cudaSuccess) e = dalloc(&b.srecs, cap);
     if (e != cudaSuccess) return cuda_status(e);
@@ -249,7 +257,7 @@ int grow_staging(dfb_ctx* h, int buf, size_t need) {
   h->hRecs[buf] = nullptr;
   h->hRecCap[buf] = 0;
   cudaError_t e =
-      cudaMallocHost(reinterpret_cast<void**>(&h->hRecs[buf]), kHdrBytes + sizeof(FragRec) * cap);
+      cudaMallocHost(reinterpret_cast<void**>(&h->hRecs[buf]), stage_bytes(h, cap));
   if (e != cudaSuccess) return DFB_ERR_OOM;
   h->hRecCap[buf] = cap;
   return DFB_OK;
@@ -382,6 +390,14 @@ int64_t in_frame_pixels(const dfb_ctx* h, int tile) {
   return (w < T ? w : T) * (hh < T ? hh : T);
 }
 
+// Count `c` more records of `tile`; list the tile once it has more than the
+// composite kernel stages.
+inline void count_frags(dfb_ctx* h, int tile, int c) {
+  int& v = h->fragCount[tile];
+  if (v <= dfb::kStageFragments && v + c > dfb::kStageFragments) h->longTiles.push_back(tile);
+  v += c;
+}
+
 void note_tree(dfb_ctx* h, int tile, int gen, int children) {
   if (gen == 1) {
     h->recvGen1[tile] += 1;
@@ -462,6 +478,7 @@ int append_records(dfb_ctx* h, int n, const dfb_tile_desc* tiles, int where) {
     r.frame = 0;
     h->recs.push_back(r);
     note_tree(h, t.tile_id, t.generation, t.children);
+    count_frags(h, t.tile_id, 1);
     const int64_t fpx = in_frame_pixels(h, t.tile_id);
     h->pendingStats.fragments += 1;
     h->pendingStats.fragment_pixels += fpx;
@@ -523,6 +540,16 @@ void fill_frame_args(const dfb_ctx* h, FrameArgs& a, int tileBase, const FragRec
   a.varPartial = h->varPartial;
 }
 
+// Launch shapes the composite is built for (groups per CTA, CTAs per SM).
+bool valid_tuning(int ring_kb, int ctas_per_sm, int groups) {
+  if (ring_kb == 0 && ctas_per_sm == 0 && groups == 0) return true;
+  if (ring_kb < 1 || ring_kb > 227) return false;
+  static const int shapes[][2] = {{1, 2}, {2, 2}, {1, 3}, {2, 1}, {3, 1}};
+  for (const auto& sh : shapes)
+    if (sh[0] == groups && sh[1] == ctas_per_sm) return true;
+  return false;
+}
+
 dfb::TuneParams tune_of(const dfb_ctx* h) {
   return h->tune.ringKB ? h->tune : dfb::default_tune(h->cfg.dtype);
 }
@@ -555,6 +582,45 @@ void finish_stats(dfb_ctx* h) {
   s.kernel_launches = h->launches;
 }
 
+// Argument checks of a bulk setTile with device or host pointers.
+int validate_arrays(const dfb_ctx* h, int n, const int* tile_ids, const float* order_keys,
+                    const void* const* rgba, const float* const* depth, const float* scales) {
+  if (n > 0 && (!tile_ids || !order_keys || !rgba || !depth)) return DFB_ERR_INVALID_ARG;
+  const bool fp8 = h->cfg.dtype == DFB_FP8E4M3;
+  if (n > 0 && fp8 && !scales) return DFB_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (tile_ids[i] < 0 || tile_ids[i] >= h->nTiles) return DFB_ERR_TILE_RANGE;
+    if (isnan(order_keys[i]) || !rgba[i] || !depth[i]) return DFB_ERR_INVALID_ARG;
+    if (((uintptr_t)rgba[i] % 16) || ((uintptr_t)depth[i] % 16)) return DFB_ERR_INVALID_ARG;
+    if (fp8 && !(scales[i] > 0.0f && isfinite(scales[i]))) return DFB_ERR_INVALID_ARG;
+  }
+  return DFB_OK;
+}
+
+// Records of n validated generation-1 tiles with device pointers; counts the
+// arrivals per tile into `gen1` (if given).  Returns their in-frame pixels.
+int64_t build_records(const dfb_ctx* h, int n, const int* tile_ids, const float* order_keys,
+                      const void* const* rgba, const float* const* depth, const float* scales,
+                      FragRec* out, int* gen1) {
+  const bool fp8 = h->cfg.dtype == DFB_FP8E4M3;
+  int64_t fpx = 0;
+  const int T = h->cfg.tile_size;
+  const int fullX = h->cfg.width / T, fullY = h->cfg.height / T;
+  for (int i = 0; i < n; ++i) {
+    const int t = tile_ids[i];
+    out[i].rgba = rgba[i];
+    out[i].depth = depth[i];
+    out[i].tile = (uint32_t)t;
+    out[i].key = dfb::ordered_bits_host(order_keys[i]);
+    out[i].scale = fp8 ? scales[i] : 1.0f;
+    out[i].frame = 0;
+    if (gen1) gen1[t] += 1;
+    const int tx = t % h->tilesX, ty = t / h->tilesX;
+    fpx += (tx < fullX && ty < fullY) ? (int64_t)T * T : in_frame_pixels(h, t);
+  }
+  return fpx;
+}
+
 // Copy the open frame's records behind the header slot of a pinned staging
 // buffer; returns the slot index and the buffer start.
 int stage_records(dfb_ctx* h, FragRec** out) {
@@ -565,6 +631,10 @@ int stage_records(dfb_ctx* h, FragRec** out) {
   if (st != DFB_OK) return st;
   if (!h->recs.empty())
     memcpy(h->hRecs[buf] + kHdrBytes, h->recs.data(), sizeof(FragRec) * h->recs.size());
+  const size_t nl = h->longTiles.size();
+  int* lt = reinterpret_cast<int*>(h->hRecs[buf] + kHdrBytes + sizeof(FragRec) * h->recs.size());
+  if (nl) memcpy(lt, h->longTiles.data(), sizeof(int) * nl);
+  for (size_t i = 0; i <= nl; ++i) lt[nl + i] = (int)i * h->chunks;
   *out = reinterpret_cast<FragRec*>(h->hRecs[buf]);
   return buf;
 }
@@ -620,6 +690,7 @@ int dfb_create_ex(const dfb_config* cfg, dfb_handle* out) {
   h->declared.assign(h->nTiles, -1);
   h->recvGen1.assign(h->nTiles, 0);
   h->childGen1.assign(h->nTiles, 0);
+  h->fragCount.assign(h->nTiles, 0);
   if (!(cfg->flags & DFB_FLAG_DEFER_ALLOC)) {
     const int st = allocate(h);
     if (st != DFB_OK) {
@@ -668,6 +739,8 @@ int dfb_begin_frame(dfb_handle h, int accumulate) {
   std::fill(h->childGen1.begin(), h->childGen1.end(), 0);
   for (int t : h->touchedDeeper) h->deeper[t].clear();
   h->touchedDeeper.clear();
+  std::fill(h->fragCount.begin(), h->fragCount.end(), 0);
+  h->longTiles.clear();
   h->hostCopies = false;
   h->arenaIdx ^= 1;
   h->arenas[h->arenaIdx].reset();
@@ -715,17 +788,10 @@ int dfb_submit_tiles(dfb_handle h, int n, const int* tile_ids, const float* orde
   if (!h || n < 0) return DFB_ERR_INVALID_ARG;
   if (!h->inFrame) return DFB_ERR_STATE;
   if (n == 0) return DFB_OK;
-  if (!tile_ids || !order_keys || !rgba || !depth) return DFB_ERR_INVALID_ARG;
   if (where < DFB_PTR_AUTO || where > DFB_PTR_HOST) return DFB_ERR_INVALID_ARG;
-  const bool fp8 = h->cfg.dtype == DFB_FP8E4M3;
-  if (fp8 && !scales) return DFB_ERR_INVALID_ARG;
   // validate everything first: nothing is submitted if an entry is bad
-  for (int i = 0; i < n; ++i) {
-    if (tile_ids[i] < 0 || tile_ids[i] >= h->nTiles) return DFB_ERR_TILE_RANGE;
-    if (isnan(order_keys[i]) || !rgba[i] || !depth[i]) return DFB_ERR_INVALID_ARG;
-    if (((uintptr_t)rgba[i] % 16) || ((uintptr_t)depth[i] % 16)) return DFB_ERR_INVALID_ARG;
-    if (fp8 && !(scales[i] > 0.0f && isfinite(scales[i]))) return DFB_ERR_INVALID_ARG;
-  }
+  const int st = validate_arrays(h, n, tile_ids, order_keys, rgba, depth, scales);
+  if (st != DFB_OK) return st;
   if (where != DFB_PTR_DEVICE) {
     std::vector<dfb_tile_desc> ts((size_t)n);
     for (int i = 0; i < n; ++i)
@@ -736,22 +802,9 @@ int dfb_submit_tiles(dfb_handle h, int n, const int* tile_ids, const float* orde
   // device pointers: append directly
   const size_t base = h->recs.size();
   h->recs.resize(base + (size_t)n);
-  FragRec* out = h->recs.data() + base;
-  int64_t fpx = 0;
-  const int T = h->cfg.tile_size;
-  const int fullX = h->cfg.width / T, fullY = h->cfg.height / T;
-  for (int i = 0; i < n; ++i) {
-    const int t = tile_ids[i];
-    out[i].rgba = rgba[i];
-    out[i].depth = depth[i];
-    out[i].tile = (uint32_t)t;
-    out[i].key = dfb::ordered_bits_host(order_keys[i]);
-    out[i].scale = fp8 ? scales[i] : 1.0f;
-    out[i].frame = 0;
-    h->recvGen1[t] += 1;
-    const int tx = t % h->tilesX, ty = t / h->tilesX;
-    fpx += (tx < fullX && ty < fullY) ? (int64_t)T * T : in_frame_pixels(h, t);
-  }
+  const int64_t fpx = build_records(h, n, tile_ids, order_keys, rgba, depth, scales,
+                                    h->recs.data() + base, h->recvGen1.data());
+  for (int i = 0; i < n; ++i) count_frags(h, tile_ids[i], 1);
   h->pendingStats.fragments += n;
   h->pendingStats.fragment_pixels += fpx;
   return DFB_OK;
@@ -780,13 +833,17 @@ int dfb_end_frame(dfb_handle h, void* stream) {
 namespace {
 
 struct BatchRes {
-  // Resources of multi-frame launches (one per process and device).
+  // Resources of one multi-frame launch; each device has two, used by
+  // alternate launches, so the bucketing of the next batch (on a side
+  // stream) overlaps the composite of the current one.
   FragRec* dRecs = nullptr;
   uint32_t* tmp = nullptr;
   FragRec* srecs = nullptr;
   size_t recCap = 0;
   int *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
   dfb::TileBlock* blocks = nullptr;
+  int* dLong = nullptr;  // long tiles of the launch (global ids), then their item prefix
+  int* hLong = nullptr;
   size_t tileCap = 0;
   FrameArgs* dFrames = nullptr;
   int* dItemBase = nullptr;
@@ -794,20 +851,30 @@ struct BatchRes {
   FragRec* hRecs = nullptr;
   FrameArgs* hFrames = nullptr;
   int* hItemBase = nullptr;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t ready = nullptr;     // the bucketing into this set has finished
+  cudaEvent_t released = nullptr;  // the composite that read this set has finished
   bool used = false;
 };
 
+struct BatchDev {
+  BatchRes sets[2];
+  int idx = 0;
+  cudaStream_t side = nullptr;
+};
+
 std::mutex g_batch_mu;
-BatchRes g_batch[64];
+BatchDev g_batch[64];
 
 int batch_reserve(BatchRes& b, size_t nRec, size_t nTiles, size_t nFrames) {
   cudaError_t e = cudaSuccess;
-  if (!b.done) {
-    e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+  if (!b.ready) {
+    e = cudaEventCreateWithFlags(&b.ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.released, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_status(e);
   }
-  if (b.used) cudaEventSynchronize(b.done);  // last batch finished with the arrays
+  // The launch that last used this set has finished with its host and device
+  // arrays (its uploads and bucketing precede its composite).
+  if (b.used) cudaEventSynchronize(b.released);
   if (nRec > b.recCap) {
     size_t cap = b.recCap ? b.recCap : 4096;
     while (cap < nRec) cap *= 2;
@@ -824,11 +891,16 @@ int batch_reserve(BatchRes& b, size_t nRec, size_t nTiles, size_t nFrames) {
     size_t cap = b.tileCap ? b.tileCap : 4096;
     while (cap < nTiles) cap *= 2;
     cudaFree(b.counts); cudaFree(b.offsets); cudaFree(b.cursor); cudaFree(b.blocks);
+    cudaFree(b.dLong); cudaFreeHost(b.hLong);
     b.counts = b.offsets = b.cursor = nullptr; b.blocks = nullptr; b.tileCap = 0;
+    b.dLong = b.hLong = nullptr;
     e = dalloc(&b.counts, cap);
     if (e == cudaSuccess) e = dalloc(&b.offsets, cap);
     if (e == cudaSuccess) e = dalloc(&b.cursor, cap);
     if (e == cudaSuccess) e = dalloc(&b.blocks, cap);
+    if (e == cudaSuccess) e = dalloc(&b.dLong, 2 * cap + 1);
+    if (e == cudaSuccess)
+      e = cudaMallocHost(reinterpret_cast<void**>(&b.hLong), sizeof(int) * (2 * cap + 1));
     if (e != cudaSuccess) return cuda_status(e);
     b.tileCap = cap;
   }
@@ -911,6 +983,12 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
   const int items = hdr->itemBase[1];
   FrameArgs* dFa = reinterpret_cast<FrameArgs*>(b.dStage);
   const int* dItemBase = reinterpret_cast<const int*>(b.dStage + offsetof(FrameHeader, itemBase));
+  const int nLong = (int)h->longTiles.size();
+  dfb::LongList lng;
+  lng.tiles = reinterpret_cast<const int*>(b.dStage + kHdrBytes + sizeof(FragRec) * n);
+  lng.base = lng.tiles + nLong;
+  lng.n = nLong;
+  lng.items = nLong * h->chunks;
   // The bucketing reads only library-owned buffers, so it runs on the side
   // stream, overlapping the previous frame's composite; under stream capture
   // everything stays on `s`.
@@ -924,8 +1002,9 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
     e = cudaStreamWaitEvent(s, h->frameDone, 0);
   if (e == cudaSuccess && side && b.used) e = cudaStreamWaitEvent(bs, b.released, 0);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b.dStage, staged, kHdrBytes + sizeof(FragRec) * n, cudaMemcpyHostToDevice,
-                        bs);
+    e = cudaMemcpyAsync(b.dStage, staged,
+                        kHdrBytes + sizeof(FragRec) * n + sizeof(int) * (2 * nLong + 1),
+                        cudaMemcpyHostToDevice, bs);
   if (e == cudaSuccess) e = cudaEventRecord(h->hRecDone[buf], bs);
   cudaEvent_t* ev = timing_slot(h);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], bs);
@@ -940,12 +1019,12 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
   if (e == cudaSuccess)
     e = dfb::launch_composite(dFa, dItemBase, 1, items, h->nTiles,
                               (h->cfg.flags & DFB_FLAG_ACCUMULATE) != 0, h->cfg.dtype, tune_of(h),
-                              ctl_of(h), s);
+                              ctl_of(h), lng, s);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
   if (e == cudaSuccess) e = cudaEventRecord(b.released, s);
   if (e == cudaSuccess) e = cudaEventRecord(h->frameDone, s);
   b.used = true;
-  h->launches += (n ? 4 : 2) + ((h->cfg.flags & DFB_FLAG_ACCUMULATE) ? 2 : 1);
+  h->launches += (n ? 4 : 2) + ((h->cfg.flags & DFB_FLAG_ACCUMULATE) ? 2 : 1) + (nLong ? 1 : 0);
   h->lastErr = h->errFlag;
   h->stallItem = -1;
   return cuda_status(e);
@@ -955,7 +1034,13 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return DFB_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_batch_mu);
-  BatchRes& b = g_batch[dev];
+  BatchDev& bd = g_batch[dev];
+  if (!bd.side && cudaStreamCreateWithFlags(&bd.side, cudaStreamNonBlocking) != cudaSuccess) {
+    bd.side = nullptr;
+    return DFB_ERR_CUDA;
+  }
+  BatchRes& b = bd.sets[bd.idx];
+  bd.idx ^= 1;
   size_t nRec = 0, nTiles = 0;
   for (int i = 0; i < n; ++i) {
     nRec += hs[i]->recs.size();
@@ -965,7 +1050,8 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
   if (st != DFB_OK) return st;
   cudaError_t e = cudaSuccess;
   size_t r = 0;
-  int tileBase = 0, items = 0;
+  int tileBase = 0, items = 0, nLong = 0;
+  std::vector<int> longChunks;
   const int dtype = hs[0]->cfg.dtype;
   bool anyAcc = false;
   for (int i = 0; i < n; ++i) {
@@ -977,6 +1063,10 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
       g.frame = (uint32_t)i;
       b.hRecs[r++] = g;
     }
+    for (int t : h->longTiles) {
+      b.hLong[nLong++] = tileBase + t;
+      longChunks.push_back(h->chunks);
+    }
     fill_frame_args(h, b.hFrames[i], tileBase, b.srecs, b.blocks);
     b.hItemBase[i] = items;
     items += h->nTiles * b.hFrames[i].chunks;
@@ -986,26 +1076,49 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
     if (h->hostCopies && e == cudaSuccess) e = cudaStreamWaitEvent(s, h->copyDone, 0);
   }
   b.hItemBase[n] = items;
+  // Uploads and bucketing touch only this set, so they run on the device's
+  // side stream (not under stream capture), overlapping earlier work on `s`.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool side = cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+                    cap == cudaStreamCaptureStatusNone;
+  if (!side) cudaGetLastError();
+  cudaStream_t bs = side ? bd.side : s;
+  if (e == cudaSuccess && side && b.used) e = cudaStreamWaitEvent(bs, b.released, 0);
   if (e == cudaSuccess && nRec)
-    e = cudaMemcpyAsync(b.dRecs, b.hRecs, sizeof(FragRec) * nRec, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(b.dRecs, b.hRecs, sizeof(FragRec) * nRec, cudaMemcpyHostToDevice, bs);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b.dFrames, b.hFrames, sizeof(FrameArgs) * n, cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(b.dFrames, b.hFrames, sizeof(FrameArgs) * n, cudaMemcpyHostToDevice, bs);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b.dItemBase, b.hItemBase, sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(b.dItemBase, b.hItemBase, sizeof(int) * (n + 1), cudaMemcpyHostToDevice,
+                        bs);
+  dfb::LongList lng;
+  lng.n = nLong;
+  lng.tiles = b.dLong;
+  lng.base = b.dLong + nLong;
+  for (int i = 0; i < nLong; ++i) {
+    b.hLong[nLong + i] = lng.items;
+    lng.items += longChunks[i];
+  }
+  b.hLong[2 * nLong] = lng.items;
+  if (e == cudaSuccess && nLong)
+    e = cudaMemcpyAsync(b.dLong, b.hLong, sizeof(int) * (2 * nLong + 1), cudaMemcpyHostToDevice,
+                        bs);
   cudaEvent_t* ev = timing_slot(hs[0]);
-  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], bs);
   if (e == cudaSuccess)
     e = dfb::launch_bucket(b.dRecs, (int)nRec, (int)nTiles, b.counts, b.offsets, b.cursor, b.tmp,
-                           b.srecs, b.blocks, s);
-  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+                           b.srecs, b.blocks, bs);
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], bs);
+  if (e == cudaSuccess && side) e = cudaEventRecord(b.ready, bs);
+  if (e == cudaSuccess && side) e = cudaStreamWaitEvent(s, b.ready, 0);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
   if (e == cudaSuccess)
     e = dfb::launch_composite(b.dFrames, b.dItemBase, n, items, tileBase, anyAcc, dtype,
-                              tune_of(hs[0]), ctl_of(hs[0]), s);
+                              tune_of(hs[0]), ctl_of(hs[0]), lng, s);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
-  if (e == cudaSuccess) e = cudaEventRecord(b.done, s);
+  if (e == cudaSuccess) e = cudaEventRecord(b.released, s);
   b.used = true;
-  hs[0]->launches += (nRec ? 4 : 2) + (anyAcc ? 2 : 1);
+  hs[0]->launches += (nRec ? 4 : 2) + (anyAcc ? 2 : 1) + (nLong ? 1 : 0);
   hs[0]->stallItem = -1;
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     e = cudaEventRecord(hs[i]->frameDone, s);
@@ -1243,11 +1356,9 @@ int dfb_read_timing(dfb_handle h, dfb_timing* out, int reset) {
   return DFB_OK;
 }
 
-int dfb_set_tuning(dfb_handle h, int ring_kb, int ctas_per_sm) {
-  if (!h || ring_kb < 0 || ring_kb > 227 || ctas_per_sm < 0 || ctas_per_sm > 2)
-    return DFB_ERR_INVALID_ARG;
-  if ((ring_kb == 0) != (ctas_per_sm == 0)) return DFB_ERR_INVALID_ARG;
-  h->tune = dfb::TuneParams{ring_kb, ctas_per_sm};
+int dfb_set_tuning(dfb_handle h, int ring_kb, int ctas_per_sm, int groups) {
+  if (!h || !valid_tuning(ring_kb, ctas_per_sm, groups)) return DFB_ERR_INVALID_ARG;
+  h->tune = dfb::TuneParams{ring_kb, ctas_per_sm, groups};
   return DFB_OK;
 }
 
@@ -1280,8 +1391,10 @@ struct dfb_graph_t {
   int *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
   FrameArgs* dFrames = nullptr;
   int* dItemBase = nullptr;
+  int* dLong = nullptr;  // long tiles (global ids), then their item prefix
+  dfb::LongList lng;
   unsigned* err = nullptr;
-  dfb::TuneParams tune{0, 0};
+  dfb::TuneParams tune{0, 0, 0};
   cudaStream_t capStream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -1304,7 +1417,8 @@ int graph_capture(dfb_graph_t* g) {
   const dfb::TuneParams tune = g->tune.ringKB ? g->tune : dfb::default_tune(g->dtype);
   // per-device launch set-up happens outside the capture (no work is enqueued)
   cudaError_t e = dfb::launch_composite(g->dFrames, g->dItemBase, 1, 0, 0, false, g->dtype, tune,
-                                        dfb::LaunchCtl{2000000000ull, -1, g->err}, g->capStream);
+                                        dfb::LaunchCtl{2000000000ull, -1, g->err},
+                                        dfb::LongList{}, g->capStream);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaStreamBeginCapture(g->capStream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_status(e);
@@ -1313,7 +1427,8 @@ int graph_capture(dfb_graph_t* g) {
   if (le == cudaSuccess)
     le = dfb::launch_composite(g->dFrames, g->dItemBase, (int)g->hs.size(), g->items, g->nTiles,
                                g->anyAcc, g->dtype, tune,
-                               dfb::LaunchCtl{2000000000ull, -1, g->err}, g->capStream);
+                               dfb::LaunchCtl{2000000000ull, -1, g->err}, g->lng,
+                               g->capStream);
   e = cudaStreamEndCapture(g->capStream, &g->graph);
   if (le != cudaSuccess) return cuda_status(le);
   if (e != cudaSuccess) return cuda_status(e);
@@ -1326,7 +1441,7 @@ void graph_free(dfb_graph_t* g) {
   graph_release_capture(g);
   cudaFree(g->dRecs); cudaFree(g->tmp); cudaFree(g->srecs); cudaFree(g->blocks);
   cudaFree(g->counts); cudaFree(g->offsets); cudaFree(g->cursor);
-  cudaFree(g->dFrames); cudaFree(g->dItemBase); cudaFree(g->err);
+  cudaFree(g->dFrames); cudaFree(g->dItemBase); cudaFree(g->dLong); cudaFree(g->err);
   if (g->capStream) cudaStreamDestroy(g->capStream);
   if (g->done) cudaEventDestroy(g->done);
   delete g;
@@ -1363,10 +1478,15 @@ int dfb_graph_create(const dfb_handle* hs, int n, dfb_graph* out) {
   std::vector<FragRec> recs;
   std::vector<FrameArgs> fa((size_t)n);
   std::vector<int> itemBase((size_t)n + 1);
+  std::vector<int> longs, longChunks;
   int tileBase = 0, items = 0;
   for (int i = 0; i < n; ++i) {
     dfb_ctx* h = hs[i];
     g->anyAcc |= (h->cfg.flags & DFB_FLAG_ACCUMULATE) != 0;
+    for (int t : h->longTiles) {
+      longs.push_back(tileBase + t);
+      longChunks.push_back(h->chunks);
+    }
     for (const FragRec& fr : h->recs) {
       FragRec r = fr;
       r.tile += (uint32_t)tileBase;
@@ -1389,6 +1509,18 @@ int dfb_graph_create(const dfb_handle* hs, int n, dfb_graph* out) {
   if (e == cudaSuccess) e = dalloc(&g->cursor, (size_t)tileBase);
   if (e == cudaSuccess) e = dalloc(&g->dFrames, (size_t)n);
   if (e == cudaSuccess) e = dalloc(&g->dItemBase, (size_t)n + 1);
+  const size_t nl = longs.size();
+  {
+    int acc = 0;
+    for (size_t i = 0; i < nl; ++i) {
+      longs.push_back(acc);  // item prefix after the tile ids
+      acc += longChunks[i];
+    }
+    longs.push_back(acc);
+    g->lng.n = (int)nl;
+    g->lng.items = acc;
+  }
+  if (e == cudaSuccess) e = dalloc(&g->dLong, longs.size());
   if (e == cudaSuccess) e = dalloc(&g->err, 1);
   if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
@@ -1410,6 +1542,10 @@ int dfb_graph_create(const dfb_handle* hs, int n, dfb_graph* out) {
     e = cudaMemcpy(g->dFrames, fa.data(), sizeof(FrameArgs) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(g->dItemBase, itemBase.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+  g->lng.tiles = g->dLong;
+  g->lng.base = g->dLong + nl;
+  if (e == cudaSuccess)
+    e = cudaMemcpy(g->dLong, longs.data(), sizeof(int) * longs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->capStream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -1445,25 +1581,26 @@ int dfb_graph_launch(dfb_graph g, void* stream) {
     h->lastStreamSet = true;
     h->haveFrame = true;
     h->lastErr = g->err;
-    h->launches += (g->nRec ? 4 : 2) + (g->anyAcc ? 2 : 1);
+    h->launches += (g->nRec ? 4 : 2) + (g->anyAcc ? 2 : 1) + (g->lng.n ? 1 : 0);
   }
   g->launched = true;
   return cuda_status(e);
 }
 
-int dfb_graph_set_tuning(dfb_graph g, int ring_kb, int ctas_per_sm) {
-  if (!g || ring_kb < 0 || ring_kb > 227 || ctas_per_sm < 0 || ctas_per_sm > 2 ||
-      (ring_kb == 0) != (ctas_per_sm == 0))
-    return DFB_ERR_INVALID_ARG;
+int dfb_graph_set_tuning(dfb_graph g, int ring_kb, int ctas_per_sm, int groups) {
+  if (!g || !valid_tuning(ring_kb, ctas_per_sm, groups)) return DFB_ERR_INVALID_ARG;
   if (g->launched) cudaEventSynchronize(g->done);
-  g->tune = dfb::TuneParams{ring_kb, ctas_per_sm};
+  g->tune = dfb::TuneParams{ring_kb, ctas_per_sm, groups};
   return graph_capture(g);
 }
 
 int dfb_graph_autotune(dfb_graph g, void* stream, int reps, int* ring_kb, int* ctas_per_sm,
-                       float* best_ms) {
+                       int* groups, float* best_ms) {
   if (!g || reps < 1) return DFB_ERR_INVALID_ARG;
-  static const int cand[][2] = {{110, 2}, {100, 2}, {220, 1}, {160, 1}, {128, 1}};
+  // {ring KB, CTAs per SM, groups}; shapes whose ring is too small for the
+  // dtype's largest item fail to launch and are skipped
+  static const int cand[][3] = {{110, 2, 2}, {100, 2, 2}, {110, 2, 1}, {72, 3, 1},
+                                {64, 3, 1}, {220, 1, 2}};
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e = cudaEventCreate(&a);
@@ -1472,27 +1609,34 @@ int dfb_graph_autotune(dfb_graph g, void* stream, int reps, int* ring_kb, int* c
   dfb::TuneParams bestT = dfb::default_tune(g->dtype);
   for (const auto& c : cand) {
     if (e != cudaSuccess) break;
-    if (dfb_graph_set_tuning(g, c[0], c[1]) != DFB_OK) continue;  // shape does not fit
-    e = cudaGraphLaunch(g->exec, s);  // warm-up
-    if (e == cudaSuccess) e = cudaEventRecord(a, s);
-    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(g->exec, s);
-    if (e == cudaSuccess) e = cudaEventRecord(b, s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    if (dfb_graph_set_tuning(g, c[0], c[1], c[2]) != DFB_OK) continue;  // does not fit
+    cudaError_t le = cudaGraphLaunch(g->exec, s);  // warm-up
+    if (le == cudaSuccess) le = cudaEventRecord(a, s);
+    for (int r = 0; r < reps && le == cudaSuccess; ++r) le = cudaGraphLaunch(g->exec, s);
+    if (le == cudaSuccess) le = cudaEventRecord(b, s);
+    if (le == cudaSuccess) le = cudaEventSynchronize(b);
     float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-    if (e == cudaSuccess && ms / reps < best) {
+    if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, a, b);
+    if (le != cudaSuccess) {
+      // a shape the device rejects is skipped; an error that persists is not
+      cudaGetLastError();
+      e = cudaDeviceSynchronize();
+      continue;
+    }
+    if (ms / reps < best) {
       best = ms / reps;
-      bestT = dfb::TuneParams{c[0], c[1]};
+      bestT = dfb::TuneParams{c[0], c[1], c[2]};
     }
   }
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
   if (e != cudaSuccess) return cuda_status(e);
-  const int st = dfb_graph_set_tuning(g, bestT.ringKB, bestT.ctasPerSm);
+  const int st = dfb_graph_set_tuning(g, bestT.ringKB, bestT.ctasPerSm, bestT.groups);
   if (st != DFB_OK) return st;
   for (dfb_ctx* h : g->hs) h->tune = bestT;
   if (ring_kb) *ring_kb = bestT.ringKB;
   if (ctas_per_sm) *ctas_per_sm = bestT.ctasPerSm;
+  if (groups) *groups = bestT.groups;
   if (best_ms) *best_ms = best;
   return DFB_OK;
 }
@@ -1501,6 +1645,116 @@ int dfb_graph_destroy(dfb_graph g) {
   if (!g) return DFB_OK;
   graph_free(g);
   return DFB_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// prepared submissions and the one-call server step
+// ============================================================================
+struct dfb_tileset_t {
+  int width = 0, height = 0, tileSize = 0, dtype = 0;
+  std::vector<FragRec> recs;
+  std::vector<int> tiles, counts;  // generation-1 arrivals per touched tile
+  int64_t fragmentPixels = 0;
+};
+
+namespace {
+
+bool same_geometry(const dfb_ctx* h, const dfb_tileset_t* s) {
+  return s->width == h->cfg.width && s->height == h->cfg.height &&
+         s->tileSize == h->cfg.tile_size && s->dtype == h->cfg.dtype;
+}
+
+void submit_set(dfb_ctx* h, const dfb_tileset_t* s) {
+  h->recs.insert(h->recs.end(), s->recs.begin(), s->recs.end());
+  for (size_t i = 0; i < s->tiles.size(); ++i) {
+    h->recvGen1[s->tiles[i]] += s->counts[i];
+    count_frags(h, s->tiles[i], s->counts[i]);
+  }
+  h->pendingStats.fragments += (int64_t)s->recs.size();
+  h->pendingStats.fragment_pixels += s->fragmentPixels;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dfb_tileset_create(dfb_handle h, int n, const int* tile_ids, const float* order_keys,
+                       const void* const* rgba, const float* const* depth, const float* scales,
+                       dfb_tileset* out) {
+  if (!h || n < 0 || !out) return DFB_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int st = validate_arrays(h, n, tile_ids, order_keys, rgba, depth, scales);
+  if (st != DFB_OK) return st;
+  dfb_tileset_t* s = new (std::nothrow) dfb_tileset_t();
+  if (!s) return DFB_ERR_OOM;
+  try {
+    s->width = h->cfg.width;
+    s->height = h->cfg.height;
+    s->tileSize = h->cfg.tile_size;
+    s->dtype = h->cfg.dtype;
+    s->recs.resize((size_t)n);
+    std::vector<int> perTile((size_t)h->nTiles, 0);
+    s->fragmentPixels = build_records(h, n, tile_ids, order_keys, rgba, depth, scales,
+                                      s->recs.data(), perTile.data());
+    for (int t = 0; t < h->nTiles; ++t)
+      if (perTile[t]) {
+        s->tiles.push_back(t);
+        s->counts.push_back(perTile[t]);
+      }
+  } catch (const std::bad_alloc&) {
+    delete s;
+    return DFB_ERR_OOM;
+  }
+  *out = s;
+  return DFB_OK;
+}
+
+int dfb_tileset_destroy(dfb_tileset s) {
+  delete s;
+  return DFB_OK;
+}
+
+int dfb_submit_tileset(dfb_handle h, dfb_tileset s) {
+  if (!h || !s) return DFB_ERR_INVALID_ARG;
+  if (!h->inFrame) return DFB_ERR_STATE;
+  if (!same_geometry(h, s)) return DFB_ERR_INVALID_ARG;
+  try {
+    submit_set(h, s);
+  } catch (const std::bad_alloc&) {
+    return DFB_ERR_OOM;
+  }
+  return DFB_OK;
+}
+
+int dfb_run_frames(const dfb_handle* hs, const dfb_tileset* sets, const int* accumulate, int n,
+                   void* stream) {
+  if (!hs || !sets || n < 1) return DFB_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i] || !sets[i]) return DFB_ERR_INVALID_ARG;
+    if (hs[i]->inFrame) return DFB_ERR_STATE;
+    if (!same_geometry(hs[i], sets[i])) return DFB_ERR_INVALID_ARG;
+    if (hs[i]->cfg.dtype != hs[0]->cfg.dtype) return DFB_ERR_INVALID_ARG;
+  }
+  {
+    std::vector<const dfb_ctx*> sorted(hs, hs + n);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+      return DFB_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    int st = dfb_begin_frame(hs[i], accumulate ? accumulate[i] : 0);
+    if (st == DFB_OK) {
+      try {
+        submit_set(hs[i], sets[i]);
+      } catch (const std::bad_alloc&) {
+        st = DFB_ERR_OOM;
+      }
+    }
+    if (st != DFB_OK) return st;
+  }
+  return dfb_end_frames(hs, n, stream);
 }
 
 }  // extern "C"

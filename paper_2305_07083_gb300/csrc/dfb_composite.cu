@@ -62,7 +62,10 @@ constexpr int kCW = kP / 32;             // warps of a consumer group
 template <int G>
 struct Shape {
   static constexpr int threads = G * kP + 32;
+  static_assert(threads <= 1024, "threads per CTA");
 };
+// Launch shapes: G consumer groups per CTA, PER resident CTAs per SM.
+//   (G, PER) = (1, 2), (2, 2), (1, 3), (2, 1), (3, 1)
 constexpr int kN = kStageFragments;
 constexpr int kSlots = 16;               // items in flight at most
 constexpr int kMetaQ = 8;                // tile blocks fetched ahead
@@ -93,11 +96,9 @@ static_assert(kMetaQ * 16 <= 128, "queue locations");
 template <int DT>
 struct Bytes {
   static constexpr int px = PxBytes<DT>::value;
-  // largest item the ring must hold: a staged item or a sort window, plus
-  // three rows of framebuffer state (sum, M2, Kahan compensation)
-  static constexpr uint32_t frag =
-      (uint32_t)kN * kP * (4 + px) > kWindowBytes ? (uint32_t)kN * kP * (4 + px) : kWindowBytes;
-  static constexpr uint32_t maxItem = frag + 3u * kP * 16u;
+  // largest item the ring must hold: kN fragments plus three rows of
+  // framebuffer state (sum, M2, Kahan compensation)
+  static constexpr uint32_t maxItem = (uint32_t)kN * kP * (4 + px) + 3u * kP * 16u;
 };
 
 __device__ __forceinline__ int find_frame(const int* itemBase, int nFrames, int item) {
@@ -206,17 +207,18 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
     fetch(k + kMetaQ);  // every lane has read the slot
     const FrameArgs* A = frames + cur.f;
     const int P = A->P, mode = A->mode, T = A->T;
+    // Items of tiles with more than kN fragments belong to the long-tile
+    // kernel: they get an empty slot that the consumers skip.
     const bool staged = n <= kN;
     const uint32_t dBytes = mode != DFB_BLEND_ORDERED ? (uint32_t)P * 4u : 0u;
     const uint32_t cBytes = mode != DFB_ZCOMPOSITE ? (uint32_t)P * px : 0u;
-    const uint32_t fragBytes = staged ? (uint32_t)n * (dBytes + cBytes)
-                                      : (mode == DFB_BLEND_DEPTH ? kWindowBytes : 0u);
+    const uint32_t fragBytes = staged ? (uint32_t)n * (dBytes + cBytes) : 0u;
     // accumulation state of the item's pixels: one contiguous run per buffer
-    const bool loadState = (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1;
+    const bool loadState = staged && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1;
     const int nState = loadState ? (A->kahan && !A->kahanFirst ? 3 : 2) : 0;
     const uint32_t stateBytes = (uint32_t)P * 16u;
-    const uint32_t data = (staged ? (uint32_t)n * (dBytes + cBytes) : 0u) + nState * stateBytes;
-    const uint32_t need = fragBytes + (uint32_t)nState * stateBytes;  // multiple of 16
+    const uint32_t data = fragBytes + nState * stateBytes;
+    const uint32_t need = data;  // multiple of 16
     // ring space: no item straddles the end of the ring
     if ((uint32_t)(head % ringBytes) + need > ringBytes) head += ringBytes - head % ringBytes;
     const int s = k % kSlots;
@@ -234,7 +236,7 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
     const uint32_t start = (uint32_t)(head % ringBytes);
     head += need;
     ItemMeta* meta = metas + s;
-    if (lane < n && lane < kN) {
+    if (staged && lane < n) {
       meta->rgba[lane] = r.rgba;
       meta->scale[lane] = r.scale;
     }
@@ -506,6 +508,72 @@ __device__ __forceinline__ PixWork prepare(const FrameArgs* frames, const int* i
   return w;
 }
 
+// Background (generation 0), then the K4 epilogue of one pixel: colour,
+// running sum (Kahan-compensated past the threshold), Welford M2, mean, RGBA8,
+// and one variance partial per warp of 32 pixels.  S, M, CP are the pixel's
+// previous sum, M2 and compensation.  Every lane of the warp calls it (the
+// partial is a warp reduction); inactive lanes contribute zero.
+__device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& w, int lane,
+                                             int warp, float c0, float c1, float c2, float al,
+                                             bool covered, float4 S, float4 M, float4 CP,
+                                             const float* thr) {
+  const unsigned flags = A->flags;
+  const bool acc = (flags & DFB_FLAG_ACCUMULATE) != 0;
+  float vsum = 0.0f;
+  if (w.active) {
+    if (A->mode != DFB_ZCOMPOSITE) {
+      over(make_float4(A->bgR, A->bgG, A->bgB, A->bgA), c0, c1, c2, al);  // generation 0
+    } else if (!covered) {
+      c0 = A->bgR; c1 = A->bgG; c2 = A->bgB; al = A->bgA;
+    }
+    const float4 col = make_float4(c0, c1, c2, al);
+    if (flags & DFB_FLAG_WRITE_COLOR) A->color[w.pix] = col;
+    float4 out = col;
+    if (acc) {
+      float4 Sn, tot;
+      if (A->kahan) {
+        float4 cn;
+#define DFB_KAHAN(ch)                 \
+  {                                   \
+    const float yk = col.ch - CP.ch;  \
+    const float tk = S.ch + yk;       \
+    cn.ch = (tk - S.ch) - yk;         \
+    Sn.ch = tk;                       \
+    tot.ch = tk - cn.ch;              \
+  }
+        DFB_KAHAN(x) DFB_KAHAN(y) DFB_KAHAN(z) DFB_KAHAN(w)
+#undef DFB_KAHAN
+        A->comp[w.sidx] = cn;
+      } else {
+        Sn = make_float4(S.x + col.x, S.y + col.y, S.z + col.z, S.w + col.w);
+        tot = Sn;
+      }
+      const float iN = A->invN, iN1 = A->invNm1;
+      const float4 mean = make_float4(tot.x * iN, tot.y * iN, tot.z * iN, tot.w * iN);
+      if (A->frameN != 1) {
+        // Welford: M2 += (x - mean_{n-1}) (x - mean_n), mean_{n-1} = S_{n-1}/(n-1)
+        M.x = fmaf(col.x - S.x * iN1, col.x - mean.x, M.x);
+        M.y = fmaf(col.y - S.y * iN1, col.y - mean.y, M.y);
+        M.z = fmaf(col.z - S.z * iN1, col.z - mean.z, M.z);
+        M.w = fmaf(col.w - S.w * iN1, col.w - mean.w, M.w);
+      }
+      A->accum[w.sidx] = Sn;
+      A->m2[w.sidx] = M;
+      vsum = (M.x + M.y + M.z) * iN1;
+      out = mean;
+    }
+    if (flags & DFB_FLAG_PACK_RGBA8) A->rgba8[w.pix] = pack_rgba8(out, thr);
+  }
+  if (acc && warp * 32 < w.P) {
+    // one partial per warp of 32 pixels, summed per tile by k_tile_variance
+    float v = vsum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0)
+      A->varPartial[(size_t)w.tile * A->slots + ((w.chunk * w.P + warp * 32) >> 5)] = v;
+  }
+}
+
 template <int DT, int G>
 __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                          int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
@@ -525,28 +593,23 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
       break;
     }
     const ItemMeta* meta = metas + s;
+    if (!meta->staged) {  // a long tile's item: done by k_composite_long
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&emptyB[s]);
+      continue;
+    }
     const int n = meta->n;
-    const int mode = A->mode;
     const int P = w.P;
-    unsigned char* base = ring + meta->start;
+    const unsigned char* base = ring + meta->start;
     float c0 = 0.f, c1 = 0.f, c2 = 0.f, al = 0.f;
     bool covered = true;
-    if (w.active) {
-      if (meta->staged)
-        covered = composite_staged<DT>(mode, n, P, base, meta, t, w.p, c0, c1, c2, al);
-      else
-        covered = composite_streamed<DT>(mode, n, A->srecs + meta->off,
-                                         reinterpret_cast<uint64_t*>(base), t, w.p, c0, c1, c2,
-                                         al);
-    }
-    const unsigned flags = A->flags;
-    const bool acc = (flags & DFB_FLAG_ACCUMULATE) != 0;
+    if (w.active) covered = composite_staged<DT>(A->mode, n, P, base, meta, t, w.p, c0, c1, c2, al);
     // the item's accumulation state: from the ring into registers, then the
     // ring space goes back to the producer before the epilogue's math and
     // stores
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 S = zero4, M = zero4, CP = zero4;
-    if (w.active && acc && A->frameN != 1) {
+    if (w.active && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1) {
       const float4* sState = reinterpret_cast<const float4*>(base + meta->stateOff);
       S = sState[t];
       M = sState[P + t];
@@ -554,65 +617,12 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&emptyB[s]);  // ring space free for the producer
-    float vsum = 0.0f;
-    if (w.active) {
-      if (mode != DFB_ZCOMPOSITE) {
-        over(make_float4(A->bgR, A->bgG, A->bgB, A->bgA), c0, c1, c2, al);  // generation 0
-      } else if (!covered) {
-        c0 = A->bgR; c1 = A->bgG; c2 = A->bgB; al = A->bgA;
-      }
-      // ---- K4 epilogue ----
-      const float4 col = make_float4(c0, c1, c2, al);
-      if (flags & DFB_FLAG_WRITE_COLOR) A->color[w.pix] = col;
-      float4 out = col;
-      if (acc) {
-        float4 Sn, tot;
-        if (A->kahan) {
-          float4 cn;
-#define DFB_KAHAN(ch)                 \
-  {                                   \
-    const float yk = col.ch - CP.ch;  \
-    const float tk = S.ch + yk;       \
-    cn.ch = (tk - S.ch) - yk;         \
-    Sn.ch = tk;                       \
-    tot.ch = tk - cn.ch;              \
-  }
-          DFB_KAHAN(x) DFB_KAHAN(y) DFB_KAHAN(z) DFB_KAHAN(w)
-#undef DFB_KAHAN
-          A->comp[w.sidx] = cn;
-        } else {
-          Sn = make_float4(S.x + col.x, S.y + col.y, S.z + col.z, S.w + col.w);
-          tot = Sn;
-        }
-        const float iN = A->invN, iN1 = A->invNm1;
-        const float4 mean = make_float4(tot.x * iN, tot.y * iN, tot.z * iN, tot.w * iN);
-        if (A->frameN != 1) {
-          // Welford: M2 += (x - mean_{n-1}) (x - mean_n), mean_{n-1} = S_{n-1}/(n-1)
-          M.x = fmaf(col.x - S.x * iN1, col.x - mean.x, M.x);
-          M.y = fmaf(col.y - S.y * iN1, col.y - mean.y, M.y);
-          M.z = fmaf(col.z - S.z * iN1, col.z - mean.z, M.z);
-          M.w = fmaf(col.w - S.w * iN1, col.w - mean.w, M.w);
-        }
-        A->accum[w.sidx] = Sn;
-        A->m2[w.sidx] = M;
-        vsum = (M.x + M.y + M.z) * iN1;
-        out = mean;
-      }
-      if (flags & DFB_FLAG_PACK_RGBA8) A->rgba8[w.pix] = pack_rgba8(out, thr);
-    }
-    if (acc && warp * 32 < P) {
-      // one partial per warp of 32 pixels, summed per tile by k_tile_variance
-      float v = vsum;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0)
-        A->varPartial[(size_t)w.tile * A->slots + ((w.chunk * P + warp * 32) >> 5)] = v;
-    }
+    finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, thr);
   }
 }
 
-template <int DT, int G>
-__global__ void __launch_bounds__(Shape<G>::threads, 3 - G) k_composite(
+template <int DT, int G, int PER>
+__global__ void __launch_bounds__(Shape<G>::threads, PER) k_composite(
     const FrameArgs* __restrict__ frames,
                                                         const int* __restrict__ itemBase,
                                                         int nFrames, int totalItems,
@@ -646,6 +656,59 @@ __global__ void __launch_bounds__(Shape<G>::threads, 3 - G) k_composite(
                  thr);
 }
 
+// Tiles with more than kN fragments, after the main kernel: the work items of
+// all long tiles are spread over the CTAs (kP threads, one pixel per thread).
+// The fragments are streamed from HBM in rounds of a per-pixel sort window
+// held in shared memory (composite_streamed), then the pixel goes through the
+// same epilogue as in the main kernel.  Long lists are rare, and keeping this
+// path out of k_composite keeps that kernel's register count low enough for
+// more resident warps.
+template <int DT>
+__global__ void __launch_bounds__(kP) k_composite_long(const FrameArgs* __restrict__ frames,
+                                                       const int* __restrict__ itemBase,
+                                                       int nFrames, LongList lng) {
+  extern __shared__ __align__(16) unsigned char lsmem[];
+  float* thr = reinterpret_cast<float*>(lsmem);
+  uint64_t* window = reinterpret_cast<uint64_t*>(lsmem + 1024);
+  for (int i = threadIdx.x; i < 256; i += kP) thr[i] = g_srgb_thr[i];
+  __syncthreads();
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int u = blockIdx.x; u < lng.items; u += gridDim.x) {
+    int j = 0, hj = lng.n - 1;  // long tile with the largest item base <= u
+    while (j < hj) {
+      const int mid = (j + hj + 1) >> 1;
+      if (__ldg(lng.base + mid) <= u) j = mid; else hj = mid - 1;
+    }
+    const int gt = __ldg(lng.tiles + j);
+    const int c = u - __ldg(lng.base + j);
+    int lo = 0, hi = nFrames - 1;  // frame with the largest tileBase <= gt
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (frames[mid].tileBase <= gt) lo = mid; else hi = mid - 1;
+    }
+    const FrameArgs* A = frames + lo;
+    const TileBlock* blk = A->blocks + gt;
+    const int n = blk->n, off = blk->off;
+    {
+      const int item = __ldg(itemBase + lo) + (gt - A->tileBase) * A->chunks + c;
+      const PixWork w = prepare(frames, itemBase, nFrames, item, t);
+      float c0 = 0.f, c1 = 0.f, c2 = 0.f, al = 0.f;
+      bool covered = true;
+      if (w.active)
+        covered = composite_streamed<DT>(A->mode, n, A->srecs + off, window, t, w.p, c0, c1, c2,
+                                         al);
+      const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 S = zero4, M = zero4, CP = zero4;
+      if (w.active && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1) {
+        S = A->accum[w.sidx];
+        M = A->m2[w.sidx];
+        if (A->kahan && !A->kahanFirst) CP = A->comp[w.sidx];
+      }
+      finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, thr);
+    }
+  }
+}
+
 // Per-tile variance: one warp per global tile sums the tile's per-warp
 // partials in slot order.
 __global__ void k_tile_variance(const FrameArgs* __restrict__ frames, int nFrames,
@@ -674,11 +737,11 @@ __global__ void k_tile_variance(const FrameArgs* __restrict__ frames, int nFrame
   }
 }
 
-template <int DT, int G>
+template <int DT, int G, int PER>
 cudaError_t launch_shape(const FrameArgs* frames, const int* itemBase, int nFrames,
                          int totalItems, int ringKB, const LaunchCtl& ctl, cudaStream_t s) {
-  auto kern = k_composite<DT, G>;
-  constexpr int per = 3 - G;  // CTAs per SM
+  auto kern = k_composite<DT, G, PER>;
+  constexpr int per = PER;  // CTAs per SM
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -716,27 +779,65 @@ cudaError_t launch_shape(const FrameArgs* frames, const int* itemBase, int nFram
 template <int DT>
 cudaError_t launch_dt(const FrameArgs* frames, const int* itemBase, int nFrames, int totalItems,
                       const TuneParams& tune, const LaunchCtl& ctl, cudaStream_t s) {
-  if (tune.ctasPerSm >= 2)
-    return launch_shape<DT, 1>(frames, itemBase, nFrames, totalItems, tune.ringKB, ctl, s);
-  return launch_shape<DT, 2>(frames, itemBase, nFrames, totalItems, tune.ringKB, ctl, s);
+  const int per = tune.ctasPerSm, g = tune.groups;
+#define DFB_SHAPE(G_, PER_)                                                                   \
+  if (g == G_ && per == PER_)                                                                 \
+    return launch_shape<DT, G_, PER_>(frames, itemBase, nFrames, totalItems, tune.ringKB, ctl, s);
+  DFB_SHAPE(1, 2)
+  DFB_SHAPE(2, 2)
+  DFB_SHAPE(1, 3)
+  DFB_SHAPE(2, 1)
+  DFB_SHAPE(3, 1)
+#undef DFB_SHAPE
+  return cudaErrorInvalidConfiguration;
 }
 
 }  // namespace
 
+// Measured on the 2048x2048 brick workload: FP32 items need the larger ring
+// of 2 CTAs per SM (two consumer groups each); the narrower formats fit a
+// full item into the ring of 3 CTAs per SM.
 TuneParams default_tune(int dtype) {
-  (void)dtype;
-  return TuneParams{110, 2};
+  if (dtype == DFB_F32) return TuneParams{110, 2, 2};
+  return TuneParams{72, 3, 1};
 }
 
 cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int nFrames,
                              int totalItems, int totalTiles, bool accumulate, int dtype,
-                             const TuneParams& tune, const LaunchCtl& ctl, cudaStream_t s) {
+                             const TuneParams& tune, const LaunchCtl& ctl, const LongList& lng,
+                             cudaStream_t s) {
   cudaError_t e;
   switch (dtype) {
     case DFB_F32: e = launch_dt<DFB_F32>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
     case DFB_F16: e = launch_dt<DFB_F16>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
     case DFB_BF16: e = launch_dt<DFB_BF16>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
     default: e = launch_dt<DFB_FP8E4M3>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
+  }
+  if (e == cudaSuccess && lng.n > 0 && lng.items > 0) {
+    static int sms[64] = {0};
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && (dev < 0 || dev >= 64)) e = cudaErrorInvalidDevice;
+    if (e == cudaSuccess && !sms[dev])
+      e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int grid = lng.items < 8 * sms[dev] ? lng.items : 8 * sms[dev];
+    const size_t smem = 1024 + kWindowBytes;
+    switch (dtype) {
+      case DFB_F32:
+        k_composite_long<DFB_F32><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng);
+        break;
+      case DFB_F16:
+        k_composite_long<DFB_F16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng);
+        break;
+      case DFB_BF16:
+        k_composite_long<DFB_BF16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng);
+        break;
+      default:
+        k_composite_long<DFB_FP8E4M3><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng);
+        break;
+    }
+    e = cudaGetLastError();
   }
   if (e != cudaSuccess || !accumulate || totalTiles < 1) return e;
   k_tile_variance<<<(totalTiles * 32 + 255) / 256, 256, 0, s>>>(frames, nFrames, totalTiles);

@@ -13,8 +13,8 @@ namespace dfb {
 // is 256 consecutive pixels of one tile; a 64x64 tile is 16 items.  Tiles of
 // fewer than 256 pixels are one item each.
 constexpr int kItemPixels = 256;
-// Fragments of an item staged in shared memory by bulk copies; items with
-// more fragments take the slower streaming path.
+// Fragments of an item staged in shared memory by bulk copies; tiles with
+// more fragments are composited by a separate, streaming kernel.
 constexpr int kStageFragments = 16;
 // Per-pixel sort window of the streaming path: fragments are taken in rounds
 // of at most kSortWindow, each round the window's nearest not yet blended.
@@ -74,7 +74,18 @@ struct FrameArgs {
 // Launch shape of the composite kernel, chosen by the autotuner.
 struct TuneParams {
   int ringKB;     // shared-memory ring per CTA in KB (its depth: items in flight)
-  int ctasPerSm;  // persistent CTAs per SM (1 or 2)
+  int ctasPerSm;  // persistent CTAs per SM
+  int groups;     // consumer groups per CTA (items composited at once)
+};
+
+// Tiles of a launch with more than kStageFragments fragments: global tile
+// ids and the prefix of their work items (base[i] = items of tiles 0..i-1;
+// base[n] = items), device arrays.
+struct LongList {
+  const int* tiles = nullptr;
+  const int* base = nullptr;
+  int n = 0;
+  int items = 0;
 };
 
 // Controls of one composite launch.
@@ -93,11 +104,13 @@ cudaError_t launch_bucket(const FragRec* recs, int nRec, int nTilesTotal, int* c
 
 // Composite + accumulate + variance + pack (K2/K3 + K4) over the work items of
 // `nFrames` frames (device arrays `frames` and `itemBase`, nFrames + 1 prefix
-// of work items), all of storage dtype `dtype`, one persistent launch; then,
-// if `accumulate`, the per-tile variance of `totalTiles` global tiles.
+// of work items), all of storage dtype `dtype`, one persistent launch; then
+// the work items of the long tiles (which the first launch skips); then, if
+// `accumulate`, the per-tile variance of `totalTiles` global tiles.
 cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int nFrames,
                              int totalItems, int totalTiles, bool accumulate, int dtype,
-                             const TuneParams& tune, const LaunchCtl& ctl, cudaStream_t s);
+                             const TuneParams& tune, const LaunchCtl& ctl, const LongList& lng,
+                             cudaStream_t s);
 
 // Default launch shape for a dtype.
 TuneParams default_tune(int dtype);

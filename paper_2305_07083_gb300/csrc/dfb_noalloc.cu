@@ -16,6 +16,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <vector>
 
 #include "dfb_internal.h"
 
@@ -39,6 +40,8 @@ constexpr int kMaxTiles = 16384;      // tiles per frame
 //   FragRec  srecs[kMaxFragments]     records sorted per tile
 //   int      counts[kMaxTiles], offsets[kMaxTiles], cursor[kMaxTiles]
 //   TileBlock blocks[kMaxTiles]       per-tile count/offset/first records
+//   int      longIn[2 * kMaxTiles + 1] tiles with more fragments than the composite
+//                                      stages, then the prefix of their work items
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 struct Header {
   FrameArgs fa;
@@ -57,7 +60,8 @@ constexpr size_t kOffCounts = align256(kOffSrecs + sizeof(FragRec) * kMaxFragmen
 constexpr size_t kOffOffsets = align256(kOffCounts + sizeof(int) * kMaxTiles);
 constexpr size_t kOffCursor = align256(kOffOffsets + sizeof(int) * kMaxTiles);
 constexpr size_t kOffBlocks = align256(kOffCursor + sizeof(int) * kMaxTiles);
-constexpr size_t kScratchBytes = align256(kOffBlocks + sizeof(dfb::TileBlock) * kMaxTiles);  // ~15.2 MB
+constexpr size_t kOffLong = align256(kOffBlocks + sizeof(dfb::TileBlock) * kMaxTiles);
+constexpr size_t kScratchBytes = align256(kOffLong + sizeof(int) * (2 * kMaxTiles + 1));  // ~15.3 MB
 
 // The scratch itself.  Every GPU that loads the library holds it until the
 // process exits.  In host code `g_scratch` names a host-side stand-in, not the
@@ -131,8 +135,10 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   const int tilesX = (width + T - 1) / T, tilesY = (height + T - 1) / T;
   if ((int64_t)tilesX * tilesY > kMaxTiles || n > kMaxFragments) return DFB_ERR_CAPACITY;
   const int nTiles = tilesX * tilesY;
+  std::vector<int> perTile((size_t)nTiles, 0), longTiles;  // host memory only
   for (int i = 0; i < n; ++i) {
     if (tile_ids[i] < 0 || tile_ids[i] >= nTiles) return DFB_ERR_TILE_RANGE;
+    if (++perTile[tile_ids[i]] == dfb::kStageFragments + 1) longTiles.push_back(tile_ids[i]);
     if (isnan(order_keys[i]) || !rgba[i] || !depth[i]) return DFB_ERR_INVALID_ARG;
     if (((uintptr_t)rgba[i] % 16) || ((uintptr_t)depth[i] % 16)) return DFB_ERR_INVALID_ARG;
     if (dtype == DFB_FP8E4M3 && !(scales[i] > 0.0f && isfinite(scales[i])))
@@ -164,6 +170,15 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   int* counts = reinterpret_cast<int*>(base + kOffCounts);
   int* offsets = reinterpret_cast<int*>(base + kOffOffsets);
   int* cursor = reinterpret_cast<int*>(base + kOffCursor);
+  int* longIn = reinterpret_cast<int*>(base + kOffLong);
+  const int nLong = (int)longTiles.size();
+  const int chunksPerTile = T * T < dfb::kItemPixels ? 1 : T * T / dfb::kItemPixels;
+  for (int i = 0; i <= nLong; ++i) longTiles.push_back(i * chunksPerTile);  // item prefix
+  dfb::LongList lng;
+  lng.tiles = longIn;
+  lng.base = longIn + nLong;
+  lng.n = nLong;
+  lng.items = nLong * chunksPerTile;
   static_assert(sizeof(void*) == sizeof(uint64_t), "64-bit pointers");
 
   // ---- inputs into the scratch (plain copies; the host arrays may be pageable) ----
@@ -180,6 +195,9 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
       e = cudaMemcpyAsync(depthIn, depth, sizeof(void*) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && fp8)
       e = cudaMemcpyAsync(scaleIn, scales, sizeof(float) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nLong)
+      e = cudaMemcpyAsync(longIn, longTiles.data(), sizeof(int) * (2 * nLong + 1),
+                          cudaMemcpyHostToDevice, s);
     // the caller may reuse its host arrays once this call returns
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) {
@@ -221,6 +239,6 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   if (e != cudaSuccess) return DFB_ERR_CUDA;
   const dfb::LaunchCtl ctl{2000000000ull, -1, &dHdr->err};
   e = dfb::launch_composite(&dHdr->fa, dHdr->itemBase, 1, hdr.itemBase[1], nTiles, false, dtype,
-                           dfb::default_tune(dtype), ctl, s);
+                           dfb::default_tune(dtype), ctl, lng, s);
   return e == cudaSuccess ? DFB_OK : DFB_ERR_CUDA;
 }

@@ -86,6 +86,10 @@ def lib():
         "dfb_submit_tiles_ex": (C.c_int, [H, C.c_int, P, C.c_int]),
         "dfb_end_frame": (C.c_int, [H, P]),
         "dfb_end_frames": (C.c_int, [P, C.c_int, P]),
+        "dfb_tileset_create": (C.c_int, [H, C.c_int, P, P, P, P, P, C.POINTER(H)]),
+        "dfb_tileset_destroy": (C.c_int, [H]),
+        "dfb_submit_tileset": (C.c_int, [H, H]),
+        "dfb_run_frames": (C.c_int, [P, P, P, C.c_int, P]),
         "dfb_sync": (C.c_int, [H]),
         "dfb_read_color": (C.c_int, [H, P]),
         "dfb_read_accum": (C.c_int, [H, P]),
@@ -100,13 +104,14 @@ def lib():
         "dfb_read_timing": (C.c_int, [H, C.POINTER(dfb_timing), C.c_int]),
         "dfb_composite_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                             P, P, P, P, P, P, P, P, P]),
-        "dfb_set_tuning": (C.c_int, [H, C.c_int, C.c_int]),
+        "dfb_set_tuning": (C.c_int, [H, C.c_int, C.c_int, C.c_int]),
         "dfb_set_wait_limit": (C.c_int, [H, C.c_double]),
         "dfb_inject_stall": (C.c_int, [H, C.c_int]),
         "dfb_graph_create": (C.c_int, [P, C.c_int, C.POINTER(H)]),
         "dfb_graph_launch": (C.c_int, [H, P]),
-        "dfb_graph_set_tuning": (C.c_int, [H, C.c_int, C.c_int]),
+        "dfb_graph_set_tuning": (C.c_int, [H, C.c_int, C.c_int, C.c_int]),
         "dfb_graph_autotune": (C.c_int, [H, P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                         C.POINTER(C.c_int),
                                          C.POINTER(C.c_float)]),
         "dfb_graph_destroy": (C.c_int, [H]),
         "dfb_error_string": (C.c_char_p, [C.c_int]),
@@ -234,6 +239,50 @@ def dfb_end_frames(handles, stream=None):
                   "dfb_end_frames")
 
 
+def dfb_tileset_create(h, tile_ids, order_keys, rgba_ptrs, depth_ptrs, scales=None):
+    """Prepared bulk setTile (device pointers) for handles shaped like ``h``."""
+    tid = np.ascontiguousarray(tile_ids, dtype=np.int32)
+    key = np.ascontiguousarray(order_keys, dtype=np.float32)
+    rp = np.ascontiguousarray(rgba_ptrs, dtype=np.uint64)
+    dp = np.ascontiguousarray(depth_ptrs, dtype=np.uint64)
+    sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float32)
+    n = len(tid)
+    if not (len(key) == len(rp) == len(dp) == n) or (sc is not None and len(sc) != n):
+        raise ValueError("array lengths differ")
+    s = H()
+    _check(lib().dfb_tileset_create(h, n, tid.ctypes.data, key.ctypes.data, rp.ctypes.data,
+                                    dp.ctypes.data, None if sc is None else sc.ctypes.data,
+                                    C.byref(s)), "dfb_tileset_create")
+    return s
+
+
+def dfb_tileset_destroy(s):
+    return _check(lib().dfb_tileset_destroy(s), "dfb_tileset_destroy")
+
+
+def dfb_submit_tileset(h, s):
+    return _check(lib().dfb_submit_tileset(h, s), "dfb_submit_tileset")
+
+
+def _addresses(objs):
+    return np.array([o.value if isinstance(o, H) else (o or 0) for o in objs], dtype=np.uint64)
+
+
+def dfb_run_frames(handles, sets, accumulate=None, stream=None):
+    """Begin, submit a prepared set and end the frames of several handles in
+    one call (one batched launch)."""
+    hs = _addresses(handles)
+    ss = _addresses(sets)
+    if len(hs) != len(ss):
+        raise ValueError("one set per handle")
+    acc = None if accumulate is None else np.ascontiguousarray(accumulate, dtype=np.int32)
+    if acc is not None and len(acc) != len(hs):
+        raise ValueError("one accumulate flag per handle")
+    return _check(lib().dfb_run_frames(hs.ctypes.data, ss.ctypes.data,
+                                       None if acc is None else acc.ctypes.data, len(hs),
+                                       _stream(stream)), "dfb_run_frames")
+
+
 def dfb_sync(h):
     return _check(lib().dfb_sync(h), "dfb_sync")
 
@@ -321,8 +370,9 @@ def dfb_inject_stall(h, item):
     return _check(lib().dfb_inject_stall(h, int(item)), "dfb_inject_stall")
 
 
-def dfb_set_tuning(h, ring_kb=0, ctas_per_sm=0):
-    return _check(lib().dfb_set_tuning(h, int(ring_kb), int(ctas_per_sm)), "dfb_set_tuning")
+def dfb_set_tuning(h, ring_kb=0, ctas_per_sm=0, groups=0):
+    return _check(lib().dfb_set_tuning(h, int(ring_kb), int(ctas_per_sm), int(groups)),
+                  "dfb_set_tuning")
 
 
 def dfb_graph_create(handles):
@@ -336,16 +386,16 @@ def dfb_graph_launch(g, stream=None):
     return _check(lib().dfb_graph_launch(g, _stream(stream)), "dfb_graph_launch")
 
 
-def dfb_graph_set_tuning(g, ring_kb, ctas_per_sm):
-    return _check(lib().dfb_graph_set_tuning(g, int(ring_kb), int(ctas_per_sm)),
+def dfb_graph_set_tuning(g, ring_kb, ctas_per_sm, groups):
+    return _check(lib().dfb_graph_set_tuning(g, int(ring_kb), int(ctas_per_sm), int(groups)),
                   "dfb_graph_set_tuning")
 
 
 def dfb_graph_autotune(g, stream=None, reps=5):
-    r, c, ms = C.c_int(), C.c_int(), C.c_float()
+    r, c, gr, ms = C.c_int(), C.c_int(), C.c_int(), C.c_float()
     _check(lib().dfb_graph_autotune(g, _stream(stream), int(reps), C.byref(r), C.byref(c),
-                                    C.byref(ms)), "dfb_graph_autotune")
-    return {"ring_kb": r.value, "ctas_per_sm": c.value, "ms": ms.value}
+                                    C.byref(gr), C.byref(ms)), "dfb_graph_autotune")
+    return {"ring_kb": r.value, "ctas_per_sm": c.value, "groups": gr.value, "ms": ms.value}
 
 
 def dfb_graph_destroy(g):

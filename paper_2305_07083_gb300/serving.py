@@ -9,9 +9,10 @@ image tile over many passes (Sec. 4.1, progressive refinement).  The server
   budget and a slot is free, giving each job its own resident framebuffer
   (a handle of libdfb.so);
 * on every step composites the next frame of *every* active job in one
-  batched launch (dfb_end_frames: one bucketing pass and one persistent
-  composite launch over all their work items), so jobs that arrive while
-  others are on the GPU join the next launch;
+  batched launch (dfb_run_frames: each job's frame is a prepared tile set,
+  validated once; one bucketing pass and one persistent composite launch
+  over all their work items), so jobs that arrive while others are on the
+  GPU join the next launch;
 * retires jobs whose last frame has been composited: their RGBA8 frame is
   read back, the latency (arrival to result on the host) is recorded and
   the footprint is released for the next queued job.
@@ -24,6 +25,7 @@ compositing runs in the library's kernels.
 from __future__ import annotations
 
 import time
+import weakref
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -42,6 +44,7 @@ class FrameData:
     fragment_pixels: int
     rgba_ptrs: np.ndarray = None
     depth_ptrs: np.ndarray = None
+    tileset: object = None
 
     def pointers(self, T, dtype):
         if self.rgba_ptrs is None:
@@ -49,6 +52,15 @@ class FrameData:
             self.rgba_ptrs = D.pool_pointers(self.rgba, n, P * 4 * D.ELEMENT_BYTES[dtype])
             self.depth_ptrs = D.pool_pointers(self.depth, n, P * 4)
         return self.rgba_ptrs, self.depth_ptrs
+
+    def prepared(self, handle, T, dtype):
+        """The frame as a prepared tile set for handles shaped like
+        `handle` (made once; every job on this frame shares it)."""
+        if self.tileset is None:
+            rp, dp = self.pointers(T, dtype)
+            self.tileset = D.dfb_tileset_create(handle, self.tile_ids, self.keys, rp, dp)
+            weakref.finalize(self, D.dfb_tileset_destroy, self.tileset)
+        return self.tileset
 
 
 @dataclass
@@ -93,6 +105,8 @@ class ServerStats:
     batch_sizes: list = field(default_factory=list)
     peak_active: int = 0
     peak_footprint: int = 0
+    host_ms: dict = field(default_factory=dict)   # host time per phase of the loop
+    gpu_ms: float = 0.0                          # device time of the batched launches
 
     def summary(self) -> dict:
         lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
@@ -106,7 +120,9 @@ class ServerStats:
                 "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
                 "max_batch": int(max(self.batch_sizes)) if self.batch_sizes else 0,
                 "peak_active_jobs": self.peak_active,
-                "peak_footprint_bytes": self.peak_footprint}
+                "peak_footprint_bytes": self.peak_footprint,
+                "host_ms": {k: round(v, 3) for k, v in self.host_ms.items()},
+                "gpu_busy_ms": round(self.gpu_ms, 3)}
 
 
 class Server:
@@ -147,7 +163,7 @@ class Server:
         self.out_pool = {}
 
     # -- the loop -------------------------------------------------------------
-    def run(self, jobs, time_limit_s: float = 1e9) -> ServerStats:
+    def run(self, jobs, time_limit_s: float = 1e9, trace: bool = False) -> ServerStats:
         """Serve `jobs` (any order; admitted by arrival time) until all have
         finished or the time limit has passed.
 
@@ -158,6 +174,10 @@ class Server:
         completion is observed by polling an event.  The library bounds how
         far the host runs ahead (a batch waits for the previous batch before
         reusing its staging buffers).
+
+        With `trace`, the stats also split the host time by phase (admit,
+        prepare, launch, retire) and sum the device time of every batched
+        launch (CUDA events around each step on the stream).
         """
         import torch
         stream = self.stream if self.stream is not None else torch.cuda.current_stream()
@@ -165,6 +185,8 @@ class Server:
         queue, active, inflight = [], [], []
         used = 0
         st = ServerStats()
+        phase = {"admit": 0.0, "prepare": 0.0, "launch": 0.0, "retire": 0.0}
+        step_events = []
         t0 = time.perf_counter()
 
         def observe(block):
@@ -185,7 +207,8 @@ class Server:
             inflight = keep
 
         while pending or queue or active or inflight:
-            now = time.perf_counter() - t0
+            ta = time.perf_counter()
+            now = ta - t0
             if now > time_limit_s:
                 break
             while pending and pending[0].arrival <= now:
@@ -209,11 +232,28 @@ class Server:
                 elif pending:
                     time.sleep(max(0.0, min(pending[0].arrival - now, 0.001)))
                 continue
+            tb = time.perf_counter()
+            phase["admit"] += tb - ta
             # one step: the next frame of every active job in one launch
             fpx = 0
+            sets, acc = [], []
             for job in active:
-                fpx += self._submit(job)
-            D.dfb_end_frames([j.handle for j in active], stream)
+                fr = job.frames[job.done_frames % len(job.frames)]
+                sets.append(fr.prepared(job.handle, job.T, self.dtype))
+                acc.append(1 if job.done_frames > 0 else 0)
+                fpx += fr.fragment_pixels
+            tc = time.perf_counter()
+            if trace:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            D.dfb_run_frames([j.handle for j in active], sets, acc, stream)
+            if trace:
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record(stream)
+                step_events.append((e0, e1))
+            td = time.perf_counter()
+            phase["prepare"] += tc - tb
+            phase["launch"] += td - tc
             st.steps += 1
             st.batch_sizes.append(len(active))
             st.launches_frames += len(active)
@@ -235,10 +275,13 @@ class Server:
                 else:
                     still.append(job)
             active = still
+            phase["retire"] += time.perf_counter() - td
         while inflight and time.perf_counter() - t0 <= time_limit_s:
             observe(True)
         st.wall_s = time.perf_counter() - t0
         torch.cuda.synchronize()
+        st.host_ms = {k: 1e3 * v for k, v in phase.items()}
+        st.gpu_ms = sum(a.elapsed_time(b) for a, b in step_events)
         for job in active:       # time limit: release what is still open
             self.pool.setdefault((job.W, job.H, job.T, job.mode), []).append(job.handle)
             job.handle = None
@@ -260,19 +303,28 @@ class Server:
 
 def make_jobs(templates, arrivals, seed=0, accumulate_frames=64, T=64):
     """Jobs for (time, client) arrivals: half blend jobs on a random blend
-    template, half accumulate jobs of `accumulate_frames` passes."""
+    template, half accumulate jobs of `accumulate_frames` passes.  Jobs on
+    the same template share its FrameData (and so its prepared tile sets)."""
     rng = np.random.default_rng([seed, 6])
+    shared = {}
+
+    def frame(kind, i, j, d):
+        key = (kind, i, j)
+        if key not in shared:
+            shared[key] = FrameData(d["tile_ids"], d["keys"], d["rgba"], d["depth"],
+                                    d["fragment_pixels"])
+        return shared[key]
+
     jobs = []
     for i, (t, c) in enumerate(arrivals):
         if rng.random() < 0.5:
-            W, H, _, fd = templates["blend"][int(rng.integers(len(templates["blend"])))]
-            frames = [FrameData(fd["tile_ids"], fd["keys"], fd["rgba"], fd["depth"],
-                                fd["fragment_pixels"])]
-            jobs.append(Job(i, c, t, "blend", W, H, T, frames, 1))
+            k = int(rng.integers(len(templates["blend"])))
+            W, H, _, fd = templates["blend"][k]
+            jobs.append(Job(i, c, t, "blend", W, H, T, [frame("blend", k, 0, fd)], 1))
         else:
-            W, H, passes = templates["accumulate"][int(rng.integers(len(templates["accumulate"])))]
-            frames = [FrameData(p["tile_ids"], p["keys"], p["rgba"], p["depth"],
-                                p["fragment_pixels"]) for p in passes]
+            k = int(rng.integers(len(templates["accumulate"])))
+            W, H, passes = templates["accumulate"][k]
+            frames = [frame("accumulate", k, j, p) for j, p in enumerate(passes)]
             jobs.append(Job(i, c, t, "accumulate", W, H, T, frames, accumulate_frames))
     return jobs
 

@@ -227,3 +227,120 @@ def test_null_handle_and_pointers():
     assert L.dfb_create_ex(None, None) == D.DFB_ERR_INVALID_ARG
     assert L.dfb_end_frames(None, 1, None) == D.DFB_ERR_INVALID_ARG
     assert L.dfb_convert_tiles(None, None, None, 1, 16, 1, None) == D.DFB_ERR_INVALID_ARG
+
+
+# --- prepared submissions (validated on the host; nothing is launched) -------
+def _deferred(W=128, H=64, T=32, dtype=D.DFB_F32):
+    return D.dfb_create_ex(W, H, T, D.DFB_BLEND_DEPTH, dtype,
+                           D.DFB_FLAGS_DEFAULT | D.DFB_FLAG_DEFER_ALLOC)
+
+
+def _fake_pointers(n, tile_bytes, base):
+    # addresses are only validated here (alignment), never dereferenced
+    return np.uint64(base) + np.arange(n, dtype=np.uint64) * np.uint64(tile_bytes)
+
+
+def test_tileset_validation():
+    h = _deferred()
+    tid = np.array([0, 3, 7, 3], np.int32)
+    key = np.array([0.5, 1.0, 2.0, 0.25], np.float32)
+    rp = _fake_pointers(4, 32 * 32 * 16, 1 << 40)
+    dp = _fake_pointers(4, 32 * 32 * 4, 1 << 41)
+    s = D.dfb_tileset_create(h, tid, key, rp, dp)
+    bad = dict(tid=np.array([0, 8, 1, 2], np.int32))          # 8 tiles: ids 0..7
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_tileset_create(h, bad["tid"], key, rp, dp)
+    assert e.value.code == D.DFB_ERR_TILE_RANGE
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_tileset_create(h, tid, key, rp + np.uint64(4), dp)   # misaligned
+    assert e.value.code == D.DFB_ERR_INVALID_ARG
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_tileset_create(h, tid, np.array([0, math.nan, 1, 2], np.float32), rp, dp)
+    assert e.value.code == D.DFB_ERR_INVALID_ARG
+    # FP8 sets need positive finite scales
+    h8 = _deferred(dtype=D.DFB_FP8E4M3)
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_tileset_create(h8, tid, key, rp, dp)
+    assert e.value.code == D.DFB_ERR_INVALID_ARG
+    s8 = D.dfb_tileset_create(h8, tid, key, rp, dp, np.ones(4, np.float32))
+    # submitting: only inside a frame, only into handles of the same shape
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_submit_tileset(h, s)
+    assert e.value.code == D.DFB_ERR_STATE
+    D.dfb_begin_frame(h, 0)
+    D.dfb_submit_tileset(h, s)
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_submit_tileset(h, s8)          # other dtype
+    assert e.value.code == D.DFB_ERR_INVALID_ARG
+    other = _deferred(W=96)
+    D.dfb_begin_frame(other, 0)
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_submit_tileset(other, s)       # other geometry
+    assert e.value.code == D.DFB_ERR_INVALID_ARG
+    empty = D.dfb_tileset_create(h, [], [], [], [])
+    D.dfb_submit_tileset(h, empty)
+    for x in (s, s8, empty):
+        D.dfb_tileset_destroy(x)
+    for x in (h, h8, other):
+        D.dfb_destroy(x)
+
+
+def test_tileset_counts_toward_declared_trees():
+    """A set's tiles are generation-1 arrivals: a tile that declared more
+    children than the set delivers keeps the frame open (INCOMPLETE is
+    returned before any device work)."""
+    h = _deferred()
+    tid = np.array([2, 2, 5], np.int32)
+    s = D.dfb_tileset_create(h, tid, np.zeros(3, np.float32),
+                             _fake_pointers(3, 32 * 32 * 16, 1 << 40),
+                             _fake_pointers(3, 32 * 32 * 4, 1 << 41))
+    D.dfb_begin_frame(h, 0)
+    D.dfb_set_tile_children(h, 2, 3)
+    D.dfb_submit_tileset(h, s)
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_end_frame(h)
+    assert e.value.code == D.DFB_ERR_INCOMPLETE
+    D.dfb_tileset_destroy(s)
+    D.dfb_destroy(h)
+
+
+def test_run_frames_validates_before_beginning():
+    a, b = _deferred(), _deferred()
+    c = _deferred(dtype=D.DFB_F16)
+    mk = lambda h, dt=16: D.dfb_tileset_create(h, [1], [0.0],
+                                               _fake_pointers(1, 32 * 32 * dt, 1 << 40),
+                                               _fake_pointers(1, 32 * 32 * 4, 1 << 41))
+    sa, sc = mk(a), mk(c, 8)
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_run_frames([a, a], [sa, sa])                   # not distinct
+    assert e.value.code == D.DFB_ERR_INVALID_ARG
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_run_frames([a, c], [sa, sc])                   # mixed dtypes
+    assert e.value.code == D.DFB_ERR_INVALID_ARG
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_run_frames([a, b], [sa, sc])                   # set of another dtype
+    assert e.value.code == D.DFB_ERR_INVALID_ARG
+    D.dfb_begin_frame(b, 0)
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_run_frames([a, b], [sa, sa])                   # b is inside a frame
+    assert e.value.code == D.DFB_ERR_STATE
+    # nothing was begun on `a` by the failed calls
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_submit_tileset(a, sa)
+    assert e.value.code == D.DFB_ERR_STATE
+    for x in (sa, sc):
+        D.dfb_tileset_destroy(x)
+    for x in (a, b, c):
+        D.dfb_destroy(x)
+
+
+def test_tuning_shapes():
+    h = _deferred()
+    for shape in ((110, 2, 1), (110, 2, 2), (72, 3, 1), (220, 1, 2), (220, 1, 3), (0, 0, 0)):
+        D.dfb_set_tuning(h, *shape)
+    for shape in ((110, 2, 3), (110, 4, 1), (220, 1, 4), (0, 2, 1), (300, 2, 1), (110, 0, 0),
+                  (-1, 2, 1)):
+        with pytest.raises(D.DfbError) as e:
+            D.dfb_set_tuning(h, *shape)
+        assert e.value.code == D.DFB_ERR_INVALID_ARG
+    D.dfb_destroy(h)

@@ -84,6 +84,27 @@ def test_long_fragment_lists(mode, n):
     check_color(fb.color(), oracle_frame(sc, mode), mode, tol=2e-5 if n > 100 else TOL)
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_long_tiles_of_many_items_with_accumulation(mode):
+    """Long tiles (more than 16 fragments) of 64x64 pixels are 16 work items
+    each, composited by the long-tile kernel next to ordinary tiles; two
+    accumulated frames exercise its reads of the running state."""
+    counts = np.array([20, 3, 33, 0, 17, 16, 1, 25])
+    fb = GpuFrameBuffer(256, 128, 64, mode)
+    imgs = []
+    for f in range(2):
+        sc = scenes.random_scene(256, 128, 64, counts, seed=80 + f, alpha_max=0.3)
+        fb.begin(accumulate=f > 0)
+        fb.submit_pool(sc.tile_ids, sc.keys, sc.rgba, sc.depth)
+        fb.end()
+        imgs.append(oracle_frame(sc, mode))
+        check_color(fb.color(), imgs[-1], mode)
+    assert np.max(np.abs(fb.accum() - o.accumulate(imgs))) <= TOL
+    px, tv = fb.variance()
+    assert np.max(np.abs(px - o.variance(imgs))) <= 1e-6
+    np.testing.assert_allclose(tv, o.tile_variance(o.variance(imgs), 64), rtol=1e-4, atol=1e-9)
+
+
 def test_empty_frame_shows_background():
     sc = scenes.random_scene(64, 64, 16, np.zeros(16, int), seed=1)
     for mode in MODES:
