@@ -17,7 +17,7 @@
 #include "dfb_internal.h"
 
 namespace dfb {
-cudaError_t upload_srgb_table(const float* host256);
+cudaError_t upload_srgb_tables(const SrgbTables& host);
 }
 
 using dfb::FragRec;
@@ -184,7 +184,8 @@ int cuda_status(cudaError_t e) {
 int ensure_table(int dev) {
   std::lock_guard<std::mutex> lk(g_table_mu);
   if (dev < 64 && (g_table_devices >> dev) & 1ull) return DFB_OK;
-  float thr[256];
+  dfb::SrgbTables tb{};
+  float* thr = tb.thr;
   for (int c = 1; c <= 255; ++c) {
     // linear value where code c begins: the inverse sRGB curve at (c-0.5)/255
     const double v = (c - 0.5) / 255.0;
@@ -192,7 +193,23 @@ int ensure_table(int dev) {
     thr[c - 1] = (float)lin;
   }
   thr[255] = INFINITY;
-  const int st = cuda_status(dfb::upload_srgb_table(thr));
+  // bucket table: boundaries <= the first value of each bucket, and a check
+  // that no bucket holds a second boundary
+  for (int i = 0; i < dfb::kSrgbLutEntries; ++i) {
+    auto bucket_start = [](int j) {
+      const uint32_t bits = (uint32_t)(j + dfb::kSrgbLutBias) << 16;
+      float f;
+      memcpy(&f, &bits, sizeof f);
+      return f;
+    };
+    const float x0 = bucket_start(i);
+    int c = 0;
+    while (c < 255 && thr[c] <= x0) ++c;
+    tb.lut[i] = (unsigned char)c;
+    if (i + 1 < dfb::kSrgbLutEntries && c + 1 < 255 && thr[c + 1] < bucket_start(i + 1))
+      return DFB_ERR_CUDA;  // cannot happen for this curve and bucket width
+  }
+  const int st = cuda_status(dfb::upload_srgb_tables(tb));
   if (st == DFB_OK && dev < 64) g_table_devices |= (1ull << dev);
   return st;
 }

@@ -44,13 +44,18 @@
 
 namespace dfb {
 
-// sRGB code boundaries: code c (1..255) starts at linear value g_srgb_thr[c-1];
-// g_srgb_thr[255] = +inf.  Uploaded by the host from the inverse of the
-// IEC 61966-2-1 curve evaluated in double.
-__device__ float g_srgb_thr[256];
+// sRGB encode tables (SrgbTables), uploaded by the host.
+__device__ SrgbTables g_srgb;
 
-cudaError_t upload_srgb_table(const float* host256) {
-  return cudaMemcpyToSymbol(g_srgb_thr, host256, sizeof(float) * 256);
+cudaError_t upload_srgb_tables(const SrgbTables& host) {
+  return cudaMemcpyToSymbol(g_srgb, &host, sizeof(SrgbTables));
+}
+
+// Copy the sRGB tables into shared memory (every thread of the CTA calls it).
+__device__ __forceinline__ void load_srgb(SrgbTables* dst, int nThreads) {
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&g_srgb);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(SrgbTables) / 4); i += nThreads) d[i] = src[i];
 }
 
 namespace {
@@ -81,9 +86,9 @@ struct ItemMeta {
 };
 static_assert(sizeof(ItemMeta) <= 256, "item meta");
 
-// Shared memory: [sRGB table 1 KB][barriers 512 B][flags 128 B][metas 4 KB]
+// Shared memory: [sRGB tables 2.75 KB][barriers 512 B][flags 128 B][metas 4 KB]
 //                [tile-block queue][ring]
-constexpr int kOffBars = 1024;
+constexpr int kOffBars = (int)sizeof(SrgbTables);
 constexpr int kOffFlags = kOffBars + 512;
 constexpr int kOffMetas = kOffFlags + 128;
 constexpr int kOffQueue = kOffMetas + kSlots * 256;
@@ -516,7 +521,7 @@ __device__ __forceinline__ PixWork prepare(const FrameArgs* frames, const int* i
 __device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& w, int lane,
                                              int warp, float c0, float c1, float c2, float al,
                                              bool covered, float4 S, float4 M, float4 CP,
-                                             const float* thr) {
+                                             const SrgbTables* tb) {
   const unsigned flags = A->flags;
   const bool acc = (flags & DFB_FLAG_ACCUMULATE) != 0;
   float vsum = 0.0f;
@@ -562,7 +567,7 @@ __device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& 
       vsum = (M.x + M.y + M.z) * iN1;
       out = mean;
     }
-    if (flags & DFB_FLAG_PACK_RGBA8) A->rgba8[w.pix] = pack_rgba8(out, thr);
+    if (flags & DFB_FLAG_PACK_RGBA8) A->rgba8[w.pix] = pack_rgba8(out, tb);
   }
   if (acc && warp * 32 < w.P) {
     // one partial per warp of 32 pixels, summed per tile by k_tile_variance
@@ -578,7 +583,7 @@ template <int DT, int G>
 __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                          int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
                          ItemMeta* metas, uint64_t* fullB, uint64_t* emptyB, volatile int* abort,
-                         const float* thr) {
+                         const SrgbTables* tb) {
   const int group = threadIdx.x / kP;
   const int t = threadIdx.x - group * kP;  // pixel of the item, 0 .. kP-1
   const int lane = t & 31, warp = t >> 5;
@@ -617,7 +622,7 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&emptyB[s]);  // ring space free for the producer
-    finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, thr);
+    finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, tb);
   }
 }
 
@@ -628,7 +633,7 @@ __global__ void __launch_bounds__(Shape<G>::threads, PER) k_composite(
                                                         int nFrames, int totalItems,
                                                         uint32_t ringBytes, LaunchCtl ctl) {
   extern __shared__ __align__(128) unsigned char smem[];
-  float* thr = reinterpret_cast<float*>(smem);
+  SrgbTables* tb = reinterpret_cast<SrgbTables*>(smem);
   uint64_t* fullB = reinterpret_cast<uint64_t*>(smem + kOffBars);
   uint64_t* emptyB = fullB + kSlots;
   volatile int* abort = reinterpret_cast<volatile int*>(smem + kOffFlags);
@@ -637,7 +642,7 @@ __global__ void __launch_bounds__(Shape<G>::threads, PER) k_composite(
   int4* qLoc = reinterpret_cast<int4*>(smem + kOffQLoc);
   uint64_t* queueB = emptyB + kSlots;
   unsigned char* ring = smem + kHeader;
-  for (int i = threadIdx.x; i < 256; i += Shape<G>::threads) thr[i] = g_srgb_thr[i];
+  load_srgb(tb, Shape<G>::threads);
   if (threadIdx.x == 0) {
     for (int q = 0; q < kSlots; ++q) {
       mbar_init(&fullB[q], 1);
@@ -653,7 +658,7 @@ __global__ void __launch_bounds__(Shape<G>::threads, PER) k_composite(
                  fullB, emptyB, queueB, abort);
   else
     consumer<DT, G>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
-                 thr);
+                    tb);
 }
 
 // Tiles with more than kN fragments, after the main kernel: the work items of
@@ -668,9 +673,9 @@ __global__ void __launch_bounds__(kP) k_composite_long(const FrameArgs* __restri
                                                        const int* __restrict__ itemBase,
                                                        int nFrames, LongList lng) {
   extern __shared__ __align__(16) unsigned char lsmem[];
-  float* thr = reinterpret_cast<float*>(lsmem);
-  uint64_t* window = reinterpret_cast<uint64_t*>(lsmem + 1024);
-  for (int i = threadIdx.x; i < 256; i += kP) thr[i] = g_srgb_thr[i];
+  SrgbTables* tb = reinterpret_cast<SrgbTables*>(lsmem);
+  uint64_t* window = reinterpret_cast<uint64_t*>(lsmem + sizeof(SrgbTables));
+  load_srgb(tb, kP);
   __syncthreads();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int u = blockIdx.x; u < lng.items; u += gridDim.x) {
@@ -704,7 +709,7 @@ __global__ void __launch_bounds__(kP) k_composite_long(const FrameArgs* __restri
         M = A->m2[w.sidx];
         if (A->kahan && !A->kahanFirst) CP = A->comp[w.sidx];
       }
-      finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, thr);
+      finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, tb);
     }
   }
 }
@@ -822,7 +827,7 @@ cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int n
       e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const int grid = lng.items < 8 * sms[dev] ? lng.items : 8 * sms[dev];
-    const size_t smem = 1024 + kWindowBytes;
+    const size_t smem = sizeof(SrgbTables) + kWindowBytes;
     switch (dtype) {
       case DFB_F32:
         k_composite_long<DFB_F32><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng);

@@ -105,37 +105,20 @@ __device__ __forceinline__ void over(float4 f, float& c0, float& c1, float& c2, 
   al = fmaf(t, f.w, al);
 }
 
-// Number of sRGB code boundaries <= x (NaN compares false -> code 0).
-__device__ __forceinline__ uint32_t srgb_code(float x, const float* thr) {
-  uint32_t c = 0;
-#pragma unroll
-  for (uint32_t s = 128; s >= 1; s >>= 1)
-    if (x >= thr[c + s - 1]) c += s;
-  return c;
+// sRGB code of a linear value: the number of code boundaries <= x, after
+// clamping x to [0, 1] (NaN -> 0), read from the bucket table (SrgbTables).
+__device__ __forceinline__ uint32_t srgb_code(float x, const SrgbTables* tb) {
+  x = fminf(fmaxf(x, 0.0f), 1.0f);  // fmaxf(NaN, 0) = 0
+  int i = (int)(__float_as_uint(x) >> 16) - kSrgbLutBias;
+  i = min(max(i, 0), kSrgbLutEntries - 1);
+  const uint32_t c = tb->lut[i];
+  return c + (x >= tb->thr[c] ? 1u : 0u);
 }
 
-// Same result as srgb_code: a fast estimate of round(255 * sRGB(x)) from the
-// hardware log2/exp2 approximations is off by at most one code near a code
-// boundary, and one comparison against each neighbouring exact boundary fixes
-// it.  x is clamped to [0, 1] first (NaN -> 0).
-__device__ __forceinline__ uint32_t srgb_code_fast(float x, const float* thr) {
-  x = fminf(fmaxf(x, 0.0f), 1.0f);
-  const float s = x <= 0.0031308f ? 12.92f * x
-                                  : fmaf(1.055f, exp2f(__log2f(x) * (1.0f / 2.4f)), -0.055f);
-  int c = __float2int_rd(fmaf(255.0f, s, 0.5f));
-  c = min(max(c, 0), 255);
-  // x < thr[c-1] and x >= thr[c] exclude each other; thr[255] = +inf
-  const float lo = thr[c > 0 ? c - 1 : 0];
-  c -= (c > 0 && x < lo) ? 1 : 0;
-  c += (x >= thr[c]) ? 1 : 0;
-  return (uint32_t)c;
-}
-
-__device__ __forceinline__ uint32_t pack_rgba8(float4 v, const float* thr) {
+__device__ __forceinline__ uint32_t pack_rgba8(float4 v, const SrgbTables* tb) {
   const float a = fminf(fmaxf(v.w, 0.0f), 1.0f);  // fmaxf(NaN, 0) = 0
   const uint32_t A = (uint32_t)__float2int_rd(fmaf(255.0f, a, 0.5f));
-  return srgb_code_fast(v.x, thr) | (srgb_code_fast(v.y, thr) << 8) |
-         (srgb_code_fast(v.z, thr) << 16) | (A << 24);
+  return srgb_code(v.x, tb) | (srgb_code(v.y, tb) << 8) | (srgb_code(v.z, tb) << 16) | (A << 24);
 }
 
 // ---- mbarrier and bulk-copy wrappers (sm_90+ PTX) ----

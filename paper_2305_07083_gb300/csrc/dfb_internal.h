@@ -43,6 +43,22 @@ struct TileBlock {
 };
 static_assert(sizeof(TileBlock) == 32 + 32 * kStageFragments, "TileBlock layout");
 
+// Tables of the sRGB encode (IEC 61966-2-1) used by the RGBA8 pack.  thr[c-1]
+// is the linear value where code c begins (the inverse curve at (c-0.5)/255,
+// evaluated in double and rounded to FP32), thr[255] = +inf, so the code of x
+// is the number of entries <= x.  lut[i] is that number at the start of
+// bucket i, the FP32 values whose top 16 bits are kSrgbLutBias + i (exponent
+// and 7 mantissa bits; bucket 0 starts at 2^-13, below the first boundary,
+// and bucket kSrgbLutEntries-1 is 1.0).  No bucket holds more than one
+// boundary, so code(x) = lut[i] + (x >= thr[lut[i]]).
+constexpr int kSrgbLutEntries = 13 * 128 + 1;
+constexpr int kSrgbLutBias = (127 - 13) << 7;
+struct SrgbTables {
+  float thr[256];
+  unsigned char lut[1792];
+};
+static_assert(sizeof(SrgbTables) % 128 == 0 && kSrgbLutEntries <= 1792, "sRGB tables");
+
 // Everything a composite work item needs about its frame.
 struct FrameArgs {
   int W, H, T, logT;
