@@ -33,6 +33,17 @@ to the code; the list of readings is:
   curve and A linearly, rounding half up; a NaN channel packs to 0.
 * FP16 / BF16 storage upcasts exactly; FP8 e4m3 storage decodes the code and
   multiplies by the fragment's FP32 scale.
+* The image-parallel tile operation with redundantly assigned tiles
+  (Sec. 4.1.1: the tiles rendered with different seeds are averaged into one
+  tile equivalent to a higher sampling rate) weighs every tile of an image
+  tile equally: the per-pixel mean of the k tiles' RGBA, ignoring depth.  The
+  mean then goes over the background like the other tile operations; a tile
+  that received nothing shows the background.
+* Pixel operations (Sec. 3.1.2) run on the finished value just before the
+  display conversion; the paper leaves their formula to the user.  Two
+  standard operators are provided, on premultiplied RGB with alpha
+  unchanged: an exposure scale ``e * rgb`` and Reinhard's global operator
+  per channel, ``e*rgb / (1 + e*rgb)``.
 """
 
 from __future__ import annotations
@@ -46,6 +57,9 @@ import numpy as np
 BLEND_DEPTH = 0      # per-pixel depth sort, then blend (Sec. 4.2, Listing 4)
 BLEND_ORDERED = 1    # blend in order-key order: the "list" tree of Sec. 4.2
 ZCOMPOSITE = 2       # nearest fragment wins (Sec. 2.1, depth compositing)
+AVERAGE = 3          # mean of redundantly rendered tiles (Sec. 4.1.1)
+
+PIXELOP_NONE, PIXELOP_EXPOSURE, PIXELOP_REINHARD = 0, 1, 2
 
 F32, F16, BF16, FP8E4M3 = 0, 1, 2, 3
 
@@ -187,6 +201,13 @@ def over_front_to_back(C, A, c, a):
     return C + t[..., None] * c, A + t * a
 
 
+def average_tiles(rgba):
+    """Per-pixel mean of n redundantly rendered tiles, equal weights
+    (Sec. 4.1.1): (n, P, 4) -> (P, 4)."""
+    rgba = np.asarray(rgba, dtype=np.float64)
+    return rgba.sum(axis=0) / rgba.shape[0]
+
+
 def composite_tile(rgba, depth, keys, sidx, mode: int, bg=(0.0, 0.0, 0.0, 0.0)):
     """Composite one tile's fragments.
 
@@ -198,7 +219,8 @@ def composite_tile(rgba, depth, keys, sidx, mode: int, bg=(0.0, 0.0, 0.0, 0.0)):
     them"), then the background.  BLEND_ORDERED: blend in (key, submit index)
     order for every pixel (Sec. 4.2, tree built as a list).  ZCOMPOSITE: the
     RGBA of the per-pixel minimum of (depth, key, submit index), or the
-    premultiplied background where that depth is +inf.
+    premultiplied background where that depth is +inf.  AVERAGE: the mean of
+    the n fragments' RGBA, then the background (Sec. 4.1.1).
     """
     rgba = np.asarray(rgba, dtype=np.float64)
     n = rgba.shape[0]
@@ -209,6 +231,13 @@ def composite_tile(rgba, depth, keys, sidx, mode: int, bg=(0.0, 0.0, 0.0, 0.0)):
     if n == 0:
         out[:, :3] = bg_c
         out[:, 3] = bg[3]
+        return out
+    if mode == AVERAGE:
+        mean = average_tiles(rgba)
+        C, A = over_front_to_back(mean[:, :3], mean[:, 3], np.broadcast_to(bg_c, (P, 3)),
+                                  np.full(P, bg[3]))
+        out[:, :3] = C
+        out[:, 3] = A
         return out
     keys = np.array([canonical_key(k) for k in keys], dtype=np.float64)
     sidx = np.asarray(sidx, dtype=np.int64)
@@ -322,6 +351,22 @@ def pack_rgba8(img):
     a = np.floor(255.0 * v[..., 3] + 0.5)
     b = np.concatenate([rgb, a[..., None]], axis=-1).astype(np.uint32)
     return b[..., 0] | (b[..., 1] << 8) | (b[..., 2] << 16) | (b[..., 3] << 24)
+
+
+def pixel_op(img, op: int, exposure: float = 1.0):
+    """A pixel operation on finished pixels (Sec. 3.1.2), before the display
+    conversion: RGB transformed, alpha unchanged."""
+    img = np.array(img, dtype=np.float64)
+    if op == PIXELOP_NONE:
+        return img
+    x = exposure * img[..., :3]
+    if op == PIXELOP_EXPOSURE:
+        img[..., :3] = x
+    elif op == PIXELOP_REINHARD:
+        img[..., :3] = x / (1.0 + x)
+    else:
+        raise ValueError("unknown pixel operation")
+    return img
 
 
 def unpack_rgba8(u32):

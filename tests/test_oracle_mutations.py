@@ -36,6 +36,33 @@ def _srgb_no_offset(x):
     return np.where(x <= 0.0031308, 12.92 * x, 1.055 * np.power(np.maximum(x, 0.0), 1.0 / 2.4))
 
 
+def _average_wrong_divisor(rgba):
+    rgba = np.asarray(rgba, dtype=np.float64)
+    return rgba.sum(axis=0) / max(rgba.shape[0] - 1, 1)
+
+
+def _average_first_tile_only(rgba):
+    return np.asarray(rgba, dtype=np.float64)[0]
+
+
+_real_pixel_op = o.pixel_op
+
+
+def _reinhard_without_exposure(img, op, exposure=1.0):
+    if op == o.PIXELOP_REINHARD:
+        img = np.array(img, dtype=np.float64)
+        img[..., :3] = img[..., :3] / (1.0 + img[..., :3])
+        return img
+    return _real_pixel_op(img, op, exposure)
+
+
+def _exposure_on_alpha(img, op, exposure=1.0):
+    img = np.array(img, dtype=np.float64)
+    if op == o.PIXELOP_EXPOSURE:
+        return img * exposure
+    return _real_pixel_op(img, op, exposure)
+
+
 MUTANTS = [
     ("over_front_to_back", _wrong_sign, [pins.test_equal_layers_closed_form]),
     ("over_front_to_back", _back_to_front_formula, [pins.test_golden_hand_derived_pixels]),
@@ -43,6 +70,11 @@ MUTANTS = [
     ("accumulate", _unsorted_accumulate, [pins.test_accumulate_fsum_and_constant]),
     ("variance", _population_variance, [pins.test_variance_library_and_closed_forms]),
     ("srgb_encode", _srgb_no_offset, [pins.test_srgb_pack_fixed_points]),
+    ("average_tiles", _average_wrong_divisor, [pins.test_average_of_identical_tiles_is_the_tile,
+                                               pins.test_average_closed_form]),
+    ("average_tiles", _average_first_tile_only, [pins.test_average_closed_form]),
+    ("pixel_op", _reinhard_without_exposure, [pins.test_reinhard_closed_forms]),
+    ("pixel_op", _exposure_on_alpha, [pins.test_pixel_op_identities]),
 ]
 
 

@@ -374,3 +374,82 @@ def test_half_and_bf16_upcast_exact():
     tb = torch.from_numpy(x).to(torch.bfloat16)
     bits = tb.view(torch.int16).numpy().view(np.uint16)
     np.testing.assert_array_equal(o.dequantize(bits, o.BF16), tb.double().numpy())
+
+
+# --- redundant tiles averaged by the image-parallel tile operation (Sec. 4.1.1) --
+def test_average_of_identical_tiles_is_the_tile():
+    rng = np.random.default_rng(41)
+    tile = rng.integers(0, 64, (16, 4)) / 64.0          # dyadic: every step is exact
+    for k in (1, 2, 3, 7):
+        rgba = np.broadcast_to(tile, (k, 16, 4))
+        out = o.composite_tile(*_frags(rgba, np.zeros((k, 16))), o.AVERAGE)
+        np.testing.assert_array_equal(out, tile)
+
+
+def test_average_closed_form():
+    """Constant tiles v_1..v_k average to (v_1 + ... + v_k) / k (dyadic, exact)."""
+    vals = [0.125, 0.5, 0.75, 0.25]
+    rgba = np.stack([np.full((8, 4), v) for v in vals])
+    out = o.composite_tile(*_frags(rgba, np.zeros((4, 8))), o.AVERAGE)
+    np.testing.assert_array_equal(out, np.full((8, 4), sum(vals) / 4))
+    two = o.composite_tile(*_frags(rgba[:3], np.zeros((3, 8))), o.AVERAGE)
+    np.testing.assert_array_equal(two, np.full((8, 4), (0.125 + 0.5 + 0.75) / 3))
+
+
+def test_average_goes_over_background_and_empty_tile_shows_it():
+    rgba = np.stack([np.full((4, 4), 0.25), np.full((4, 4), 0.75)])   # mean: c = 0.5, a = 0.5
+    bg = (1.0, 0.5, 0.25, 0.5)                                        # premultiplied 0.5, 0.25, 0.125
+    out = o.composite_tile(*_frags(rgba, np.zeros((2, 4))), o.AVERAGE, bg)
+    want = np.array([0.5 + 0.5 * 0.5, 0.5 + 0.5 * 0.25, 0.5 + 0.5 * 0.125, 0.5 + 0.5 * 0.5])
+    np.testing.assert_array_equal(out, np.broadcast_to(want, (4, 4)))
+    empty = o.composite_tile(np.zeros((0, 4, 4)), np.zeros((0, 4)), [], [], o.AVERAGE, bg)
+    np.testing.assert_array_equal(empty, np.broadcast_to([0.5, 0.25, 0.125, 0.5], (4, 4)))
+
+
+def test_average_ignores_depth_and_order():
+    rng = np.random.default_rng(42)
+    rgba = rng.random((5, 32, 4))
+    a = o.composite_tile(rgba, rng.random((5, 32)).astype(np.float32), np.zeros(5), np.arange(5),
+                         o.AVERAGE)
+    perm = rng.permutation(5)
+    b = o.composite_tile(rgba[perm], rng.random((5, 32)).astype(np.float32), rng.random(5),
+                         np.arange(5), o.AVERAGE)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(a, np.array([[math.fsum(rgba[:, p, c]) / 5 for c in range(4)]
+                                            for p in range(32)]), rtol=0, atol=1e-15)
+
+
+def test_average_of_k_tiles_equals_k_accumulated_frames():
+    """Sec. 4.1.1: averaging k redundantly rendered tiles gives the tile of a
+    k-times higher sampling rate, i.e. what accumulating the k renders as k
+    frames gives."""
+    rng = np.random.default_rng(43)
+    k = 6
+    rgba = rng.random((k, 64, 4))
+    avg = o.composite_tile(*_frags(rgba, np.zeros((k, 64))), o.AVERAGE)
+    frames = [o.composite_tile(*_frags(rgba[i:i + 1], np.zeros((1, 64))), o.BLEND_ORDERED)
+              for i in range(k)]
+    np.testing.assert_allclose(avg, o.accumulate(frames), rtol=0, atol=1e-15)
+
+
+# --- pixel operations (Sec. 3.1.2) ------------------------------------------------
+def test_pixel_op_identities():
+    rng = np.random.default_rng(44)
+    img = rng.random((8, 8, 4))
+    np.testing.assert_array_equal(o.pixel_op(img, o.PIXELOP_NONE, 3.0), img)
+    np.testing.assert_array_equal(o.pixel_op(img, o.PIXELOP_EXPOSURE, 1.0), img)
+    dy = rng.integers(0, 256, (4, 4, 4)) / 256.0
+    got = o.pixel_op(dy, o.PIXELOP_EXPOSURE, 2.0)
+    np.testing.assert_array_equal(got[..., :3], 2.0 * dy[..., :3])
+    np.testing.assert_array_equal(got[..., 3], dy[..., 3])
+
+
+def test_reinhard_closed_forms():
+    img = np.array([[1.0, 3.0, 0.0, 0.25], [0.5, 1.5, 7.0, 1.0]])
+    got = o.pixel_op(img, o.PIXELOP_REINHARD, 1.0)
+    np.testing.assert_array_equal(got, [[0.5, 0.75, 0.0, 0.25], [1.0 / 3.0, 0.6, 0.875, 1.0]])
+    got = o.pixel_op(img, o.PIXELOP_REINHARD, 2.0)
+    np.testing.assert_array_equal(got[0], [2.0 / 3.0, 6.0 / 7.0, 0.0, 0.25])
+    np.testing.assert_array_equal(got[1, :3], [0.5, 0.75, 14.0 / 15.0])
+    big = o.pixel_op(np.array([[1e300, 1e300, 1e300, 1.0]]), o.PIXELOP_REINHARD, 1.0)
+    np.testing.assert_allclose(big[0, :3], 1.0, rtol=1e-15)
