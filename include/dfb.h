@@ -60,8 +60,20 @@ enum dfb_mode {
                             front-to-back "over" (Sec. 4.2, Listing 4)        */
   DFB_BLEND_ORDERED = 1, /* "over" in (key, submit index) order for every
                             pixel: the rank-order list tree of Sec. 4.2       */
-  DFB_ZCOMPOSITE = 2     /* nearest (depth, key, submit index) fragment wins,
+  DFB_ZCOMPOSITE = 2,    /* nearest (depth, key, submit index) fragment wins,
                             RGBA copied unchanged (depth compositing, Sec. 2.1)*/
+  DFB_AVERAGE = 3        /* per-pixel mean of the tile's fragments, equal
+                            weights, depth ignored: redundantly rendered tiles
+                            of the image-parallel renderer (Sec. 4.1.1)       */
+};
+
+/* Pixel operation run on the finished value just before the RGBA8 display
+   conversion (Sec. 3.1.2; the paper leaves the formula to the user).  Both act
+   on premultiplied RGB with alpha unchanged; e is the operation's exposure. */
+enum dfb_pixel_op {
+  DFB_PIXELOP_NONE = 0,
+  DFB_PIXELOP_EXPOSURE = 1,  /* rgb -> e * rgb                                */
+  DFB_PIXELOP_REINHARD = 2   /* rgb -> e*rgb / (1 + e*rgb), per channel        */
 };
 
 /* Storage type of the submitted fragment RGBA (depth is always FP32). */
@@ -146,8 +158,15 @@ DFB_API int dfb_destroy(dfb_handle h);
 
 /* Background colour (unpremultiplied RGB and coverage A): the generation-0
    background tile of Sec. 4.2, blended behind every pixel in the blend modes
-   and shown by empty tiles in DFB_ZCOMPOSITE.  Default (0,0,0,0). */
+   and DFB_AVERAGE and shown by empty tiles in DFB_ZCOMPOSITE.  Default
+   (0,0,0,0). */
 DFB_API int dfb_set_background(dfb_handle h, float r, float g, float b, float a);
+
+/* Pixel operation of the RGBA8 output (enum dfb_pixel_op) with its exposure,
+   from the next dfb_end_frame on.  The colour, accumulation and variance
+   buffers are not affected.  Errors: INVALID_ARG (unknown op, exposure not
+   finite or negative). */
+DFB_API int dfb_set_pixel_op(dfb_handle h, int op, float exposure);
 
 /* Begin a frame (Sec. 3.1).  accumulate = 0 restarts the progressive
    accumulation with this frame; non-zero adds this frame to it.

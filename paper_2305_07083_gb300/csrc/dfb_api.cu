@@ -124,6 +124,8 @@ struct dfb_ctx {
   int accumN = 0;          // frames in the accumulation after the last frame
   int pendingN = 0;        // frames in the accumulation after the open frame
   float bg[4] = {0, 0, 0, 0};
+  int pixelOp = DFB_PIXELOP_NONE;
+  float exposure = 1.0f;
   std::vector<FragRec> recs;
   std::vector<int> declared;             // gen-0 children per tile, -1 = none
   std::vector<int> recvGen1, childGen1;  // generation-1 arrivals per tile
@@ -546,6 +548,8 @@ void fill_frame_args(const dfb_ctx* h, FrameArgs& a, int tileBase, const FragRec
   a.bgG = h->bg[1] * h->bg[3];
   a.bgB = h->bg[2] * h->bg[3];
   a.bgA = h->bg[3];
+  a.pixelOp = h->pixelOp;
+  a.exposure = h->exposure;
   a.srecs = srecs;
   a.blocks = blocks;
   a.color = h->color;
@@ -583,7 +587,8 @@ void finish_stats(dfb_ctx* h) {
   s.accumulated = h->pendingN;
   const int eb = elt_bytes(h->cfg.dtype);
   const int64_t rgbaPx = 4 * eb;
-  if (h->cfg.mode == DFB_BLEND_ORDERED) s.fragment_bytes = s.fragment_pixels * rgbaPx;
+  if (h->cfg.mode == DFB_BLEND_ORDERED || h->cfg.mode == DFB_AVERAGE)
+    s.fragment_bytes = s.fragment_pixels * rgbaPx;  // no depth read
   else if (h->cfg.mode == DFB_BLEND_DEPTH) s.fragment_bytes = s.fragment_pixels * (rgbaPx + 4);
   else s.fragment_bytes = s.fragment_pixels * 4 + px * rgbaPx;  // depth + one winner
   int64_t st = 0;
@@ -687,7 +692,7 @@ int dfb_create_ex(const dfb_config* cfg, dfb_handle* out) {
   if (cfg->width < 1 || cfg->height < 1 || !is_pow2(T) || T < 4 || T > 256)
     return DFB_ERR_INVALID_ARG;
   if ((int64_t)cfg->width * cfg->height > (int64_t)1 << 31) return DFB_ERR_INVALID_ARG;
-  if (cfg->mode < DFB_BLEND_DEPTH || cfg->mode > DFB_ZCOMPOSITE) return DFB_ERR_INVALID_ARG;
+  if (cfg->mode < DFB_BLEND_DEPTH || cfg->mode > DFB_AVERAGE) return DFB_ERR_INVALID_ARG;
   if (cfg->dtype < DFB_F32 || cfg->dtype > DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;
   if (cfg->flags & ~(DFB_FLAG_ACCUMULATE | DFB_FLAG_WRITE_COLOR | DFB_FLAG_PACK_RGBA8 |
                      DFB_FLAG_DEFER_ALLOC))
@@ -743,6 +748,15 @@ int dfb_set_background(dfb_handle h, float r, float g, float b, float a) {
   if (!h) return DFB_ERR_INVALID_ARG;
   if (!isfinite(r) || !isfinite(g) || !isfinite(b) || !isfinite(a)) return DFB_ERR_INVALID_ARG;
   h->bg[0] = r; h->bg[1] = g; h->bg[2] = b; h->bg[3] = a;
+  return DFB_OK;
+}
+
+int dfb_set_pixel_op(dfb_handle h, int op, float exposure) {
+  if (!h) return DFB_ERR_INVALID_ARG;
+  if (op < DFB_PIXELOP_NONE || op > DFB_PIXELOP_REINHARD) return DFB_ERR_INVALID_ARG;
+  if (!isfinite(exposure) || exposure < 0.0f) return DFB_ERR_INVALID_ARG;
+  h->pixelOp = op;
+  h->exposure = exposure;
   return DFB_OK;
 }
 

@@ -215,7 +215,7 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
     // Items of tiles with more than kN fragments belong to the long-tile
     // kernel: they get an empty slot that the consumers skip.
     const bool staged = n <= kN;
-    const uint32_t dBytes = mode != DFB_BLEND_ORDERED ? (uint32_t)P * 4u : 0u;
+    const uint32_t dBytes = mode == DFB_BLEND_DEPTH || mode == DFB_ZCOMPOSITE ? (uint32_t)P * 4u : 0u;
     const uint32_t cBytes = mode != DFB_ZCOMPOSITE ? (uint32_t)P * px : 0u;
     const uint32_t fragBytes = staged ? (uint32_t)n * (dBytes + cBytes) : 0u;
     // accumulation state of the item's pixels: one contiguous run per buffer
@@ -308,10 +308,21 @@ __device__ __forceinline__ bool composite_staged(int mode, int n, int P, const u
                                                  float& c0, float& c1, float& c2, float& al) {
   constexpr int px = Bytes<DT>::px;
   const float* sD = reinterpret_cast<const float*>(base);
-  const int dStride = mode != DFB_BLEND_ORDERED ? P : 0;  // floats per depth slab
+  // floats per depth slab (no depth is staged in the modes that ignore it)
+  const int dStride = mode == DFB_BLEND_DEPTH || mode == DFB_ZCOMPOSITE ? P : 0;
   const unsigned char* sC = base + (size_t)n * dStride * 4;
   if (mode == DFB_BLEND_ORDERED) {
     for (int i = 0; i < n; ++i) over(Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]), c0, c1, c2, al);
+  } else if (mode == DFB_AVERAGE) {
+    // equal-weight mean of the redundant tiles, summed in list order
+    for (int i = 0; i < n; ++i) {
+      const float4 f = Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]);
+      c0 += f.x; c1 += f.y; c2 += f.z; al += f.w;
+    }
+    if (n > 0) {
+      const float k = (float)n;
+      c0 = __fdiv_rn(c0, k); c1 = __fdiv_rn(c1, k); c2 = __fdiv_rn(c2, k); al = __fdiv_rn(al, k);
+    }
   } else if (mode == DFB_ZCOMPOSITE) {
     uint64_t best = ~0ull;
     for (int i = 0; i < n; ++i) {
@@ -408,6 +419,20 @@ __device__ __forceinline__ bool composite_streamed(int mode, int n, const FragRe
       for (int u = 0; u < 8; ++u)
         if (ib + u < n) over(c[u], c0, c1, c2, al);
     }
+    return true;
+  }
+  if (mode == DFB_AVERAGE) {
+    for (int ib = 0; ib < n; ib += 8) {
+      float4 c[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (ib + u < n) c[u] = Px<DT>::global(list[ib + u].rgba, p, list[ib + u].scale);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (ib + u < n) { c0 += c[u].x; c1 += c[u].y; c2 += c[u].z; al += c[u].w; }
+    }
+    const float k = (float)n;
+    c0 = __fdiv_rn(c0, k); c1 = __fdiv_rn(c1, k); c2 = __fdiv_rn(c2, k); al = __fdiv_rn(al, k);
     return true;
   }
   if (mode == DFB_ZCOMPOSITE) {
@@ -567,7 +592,8 @@ __device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& 
       vsum = (M.x + M.y + M.z) * iN1;
       out = mean;
     }
-    if (flags & DFB_FLAG_PACK_RGBA8) A->rgba8[w.pix] = pack_rgba8(out, tb);
+    if (flags & DFB_FLAG_PACK_RGBA8)
+      A->rgba8[w.pix] = pack_rgba8(pixel_op(out, A->pixelOp, A->exposure), tb);
   }
   if (acc && warp * 32 < w.P) {
     // one partial per warp of 32 pixels, summed per tile by k_tile_variance

@@ -105,6 +105,18 @@ __device__ __forceinline__ void over(float4 f, float& c0, float& c1, float& c2, 
   al = fmaf(t, f.w, al);
 }
 
+// Pixel operation before the display conversion (enum dfb_pixel_op): RGB
+// transformed, alpha unchanged.
+__device__ __forceinline__ float4 pixel_op(float4 v, int op, float e) {
+  if (op == DFB_PIXELOP_EXPOSURE) return make_float4(e * v.x, e * v.y, e * v.z, v.w);
+  if (op == DFB_PIXELOP_REINHARD) {
+    const float x = e * v.x, y = e * v.y, z = e * v.z;
+    return make_float4(__fdiv_rn(x, 1.0f + x), __fdiv_rn(y, 1.0f + y), __fdiv_rn(z, 1.0f + z),
+                       v.w);
+  }
+  return v;
+}
+
 // sRGB code of a linear value: the number of code boundaries <= x, after
 // clamping x to [0, 1] (NaN -> 0), read from the bucket table (SrgbTables).
 __device__ __forceinline__ uint32_t srgb_code(float x, const SrgbTables* tb) {

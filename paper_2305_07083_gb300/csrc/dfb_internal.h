@@ -76,6 +76,8 @@ struct FrameArgs {
   int kahanFirst;              // 1: first compensated frame (comp reads as 0)
   float invN, invNm1;          // 1/n and 1/(n-1) (0 when n == 1)
   float bgR, bgG, bgB, bgA;    // premultiplied background colour and coverage
+  int pixelOp;                 // enum dfb_pixel_op applied before the RGBA8 pack
+  float exposure;
   const FragRec* srecs;        // records grouped by global tile, (key, index) order
   const TileBlock* blocks;     // per global tile
   float4* color;               // row-major image

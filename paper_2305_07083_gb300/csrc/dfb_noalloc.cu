@@ -127,7 +127,7 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   // ---- validation (host only) ----
   const int T = tile_size;
   if (width < 1 || height < 1 || T < 4 || T > 256 || (T & (T - 1))) return DFB_ERR_INVALID_ARG;
-  if (mode < DFB_BLEND_DEPTH || mode > DFB_ZCOMPOSITE) return DFB_ERR_INVALID_ARG;
+  if (mode < DFB_BLEND_DEPTH || mode > DFB_AVERAGE) return DFB_ERR_INVALID_ARG;
   if (dtype < DFB_F32 || dtype > DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;
   if (n < 0 || (n > 0 && (!tile_ids || !order_keys || !rgba || !depth))) return DFB_ERR_INVALID_ARG;
   if (dtype == DFB_FP8E4M3 && n > 0 && !scales) return DFB_ERR_INVALID_ARG;
@@ -226,6 +226,8 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   a.bgG = bg[1] * bg[3];
   a.bgB = bg[2] * bg[3];
   a.bgA = bg[3];
+  a.pixelOp = DFB_PIXELOP_NONE;
+  a.exposure = 1.0f;
   a.srecs = srecs;
   a.blocks = blocks;
   a.color = reinterpret_cast<float4*>(color_out);

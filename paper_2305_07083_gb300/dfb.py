@@ -16,7 +16,8 @@ import numpy as np
 from ._build import LIB
 
 # enums (include/dfb.h)
-DFB_BLEND_DEPTH, DFB_BLEND_ORDERED, DFB_ZCOMPOSITE = 0, 1, 2
+DFB_BLEND_DEPTH, DFB_BLEND_ORDERED, DFB_ZCOMPOSITE, DFB_AVERAGE = 0, 1, 2, 3
+DFB_PIXELOP_NONE, DFB_PIXELOP_EXPOSURE, DFB_PIXELOP_REINHARD = 0, 1, 2
 DFB_F32, DFB_F16, DFB_BF16, DFB_FP8E4M3 = 0, 1, 2, 3
 DFB_OK = 0
 DFB_ERR_INVALID_ARG, DFB_ERR_TILE_RANGE, DFB_ERR_STATE, DFB_ERR_INCOMPLETE = -1, -2, -3, -4
@@ -78,6 +79,7 @@ def lib():
         "dfb_create_ex": (C.c_int, [C.POINTER(dfb_config), C.POINTER(H)]),
         "dfb_destroy": (C.c_int, [H]),
         "dfb_set_background": (C.c_int, [H, C.c_float, C.c_float, C.c_float, C.c_float]),
+        "dfb_set_pixel_op": (C.c_int, [H, C.c_int, C.c_float]),
         "dfb_begin_frame": (C.c_int, [H, C.c_int]),
         "dfb_set_tile_children": (C.c_int, [H, C.c_int, C.c_int]),
         "dfb_submit_tile": (C.c_int, [H, C.c_int, C.c_float, P, P]),
@@ -180,6 +182,10 @@ def dfb_destroy(h):
 
 def dfb_set_background(h, r, g, b, a):
     return _check(lib().dfb_set_background(h, r, g, b, a), "dfb_set_background")
+
+
+def dfb_set_pixel_op(h, op, exposure=1.0):
+    return _check(lib().dfb_set_pixel_op(h, int(op), float(exposure)), "dfb_set_pixel_op")
 
 
 def dfb_begin_frame(h, accumulate=0):

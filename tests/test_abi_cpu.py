@@ -52,7 +52,7 @@ def test_error_strings_and_version():
 
 @pytest.mark.parametrize("W,H,T,mode,dtype,flags", [
     (0, 64, 16, 0, 0, 1), (64, -1, 16, 0, 0, 1), (64, 64, 12, 0, 0, 1), (64, 64, 2, 0, 0, 1),
-    (64, 64, 512, 0, 0, 1), (64, 64, 16, 3, 0, 1), (64, 64, 16, 0, 4, 1), (64, 64, 16, 0, 0, 64)])
+    (64, 64, 512, 0, 0, 1), (64, 64, 16, 4, 0, 1), (64, 64, 16, 0, 4, 1), (64, 64, 16, 0, 0, 64)])
 def test_create_rejects_bad_config(W, H, T, mode, dtype, flags):
     with pytest.raises(D.DfbError) as e:
         D.dfb_create_ex(W, H, T, mode, dtype, flags)
@@ -344,3 +344,19 @@ def test_tuning_shapes():
             D.dfb_set_tuning(h, *shape)
         assert e.value.code == D.DFB_ERR_INVALID_ARG
     D.dfb_destroy(h)
+
+
+def test_pixel_op_validation():
+    h = _deferred()
+    for op, e in ((D.DFB_PIXELOP_NONE, 1.0), (D.DFB_PIXELOP_EXPOSURE, 0.0),
+                  (D.DFB_PIXELOP_REINHARD, 4.0)):
+        D.dfb_set_pixel_op(h, op, e)
+    for op, e in ((3, 1.0), (-1, 1.0), (D.DFB_PIXELOP_EXPOSURE, -1.0),
+                  (D.DFB_PIXELOP_REINHARD, math.nan), (D.DFB_PIXELOP_EXPOSURE, math.inf)):
+        with pytest.raises(D.DfbError) as e_:
+            D.dfb_set_pixel_op(h, op, e)
+        assert e_.value.code == D.DFB_ERR_INVALID_ARG
+    D.dfb_destroy(h)
+    a = D.dfb_create_ex(64, 64, 16, D.DFB_AVERAGE, D.DFB_F32,
+                        D.DFB_FLAGS_DEFAULT | D.DFB_FLAG_DEFER_ALLOC)
+    D.dfb_destroy(a)

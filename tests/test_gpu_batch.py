@@ -32,6 +32,9 @@ def mixed_frames(dtype):
     counts = np.random.default_rng(34).integers(0, 20, 4)
     out.append((scenes.random_scene(64, 64, 32, counts, seed=34, depth_levels=4),
                 D.DFB_ZCOMPOSITE))
+    counts = np.random.default_rng(35).integers(0, 5, 12)
+    counts[7] = 30                                    # long tile of 16 work items
+    out.append((scenes.random_scene(256, 192, 64, counts, seed=35), D.DFB_AVERAGE))
     return out
 
 

@@ -17,7 +17,7 @@ from tests.gpu_helpers import GpuFrameBuffer, composite_once
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-5
-MODES = [D.DFB_BLEND_DEPTH, D.DFB_BLEND_ORDERED, D.DFB_ZCOMPOSITE]
+MODES = [D.DFB_BLEND_DEPTH, D.DFB_BLEND_ORDERED, D.DFB_ZCOMPOSITE, D.DFB_AVERAGE]
 
 
 def oracle_frame(sc, mode, rgba64=None, bg=(0, 0, 0, 0), tiles=None):
