@@ -99,6 +99,19 @@ def whole_job_value(units_per_rank, world, ms_max):
     return world * units_per_rank / (ms_max / 1e3)
 
 
+def cpu_model():
+    """Host CPU model name (lscpu), else the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def make_pool():
     import multiprocessing as mp
     cores = len(os.sched_getaffinity(0))
@@ -485,7 +498,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "cpu": cpu_model(), "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -648,6 +661,7 @@ def main():
                                             min_seconds=10.0)
         pool.close()
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "cpu": cpu_model(),
                                "sample": "frame 0 composited %d times (%d tile tasks, %d fragment-"
                                          "pixels, %.1f s): BLEND_DEPTH FP64 per-pixel sort + over; "
                                          "accumulation, variance and pack not included; %d spawned "

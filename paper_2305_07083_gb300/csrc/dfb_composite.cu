@@ -77,7 +77,7 @@ constexpr int kMetaQ = 8;                // tile blocks fetched ahead
 constexpr uint32_t kWindowBytes = kSortWindow * kP * 8;
 
 struct ItemMeta {
-  int frame, tile, chunk, n, off, staged;
+  int n, staged;
   uint32_t start;      // byte offset of the item's data in the ring
   uint32_t stateOff;   // offset of the item's state rows from `start`
   unsigned long long end;  // producer's head position after this item
@@ -203,7 +203,7 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
       break;
     }
     const TileBlock* blk = queue + q;
-    const int n = blk->n, off = blk->off;
+    const int n = blk->n;
     FragRec r{};
     if (lane < n && lane < kN) r = blk->recs[lane];
     const int4 loc = qLoc[q];
@@ -246,11 +246,7 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
       meta->scale[lane] = r.scale;
     }
     if (lane == 0) {
-      meta->frame = cur.f;
-      meta->tile = cur.tile;
-      meta->chunk = cur.chunk;
       meta->n = n;
-      meta->off = off;
       meta->staged = staged ? 1 : 0;
       meta->start = start;
       meta->stateOff = fragBytes;
