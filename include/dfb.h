@@ -94,8 +94,11 @@ enum dfb_status {
   DFB_ERR_OOM = -5,         /* device or pinned allocation failed               */
   DFB_ERR_TIMEOUT = -6,     /* a device-side wait gave up                        */
   DFB_ERR_CUDA = -7,        /* a CUDA call failed (including: no device)         */
-  DFB_ERR_CAPACITY = -8     /* request larger than dfb_composite_noalloc's fixed
+  DFB_ERR_CAPACITY = -8,    /* request larger than dfb_composite_noalloc's fixed
                                scratch (see its limits below)                   */
+  DFB_ERR_CHECK = -9        /* a device-side bounds check of the checked build
+                               (libdfb_checked.so) failed; the access was
+                               skipped and the launch ended early             */
 };
 
 /* Configuration flags. */

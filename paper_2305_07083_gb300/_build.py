@@ -1,8 +1,10 @@
-"""Build libdfb.so in-tree with nvcc for sm_103a (GB300).
+"""Build libdfb.so in-tree with nvcc for sm_103a (GB300), and its checked
+twin libdfb_checked.so (-DDFB_CHECKED: device-side bounds checks that report
+DFB_ERR_CHECK instead of touching memory out of range).
 
-Both translation units compile in parallel; the link uses the static CUDA
-runtime so the library loads without a GPU driver (its first CUDA call then
-reports DFB_ERR_CUDA).
+All translation units of both libraries compile in parallel; the link uses
+the static CUDA runtime so the library loads without a GPU driver (its first
+CUDA call then reports DFB_ERR_CUDA).
 """
 
 from __future__ import annotations
@@ -16,6 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdfb.so")
+LIB_CHECKED = os.path.join(PKG, "libdfb_checked.so")
+VARIANTS = [(LIB, "normal", []), (LIB_CHECKED, "checked", ["-DDFB_CHECKED"])]
 SOURCES = ["dfb_composite.cu", "dfb_kernels.cu", "dfb_api.cu", "dfb_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "dfb_internal.h"), os.path.join(CSRC, "dfb_device.cuh"),
            os.path.join(ROOT, "include", "dfb.h")]
@@ -32,38 +36,48 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, s) for s in SOURCES] + HEADERS + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
+    todo = [v for v in VARIANTS if force or _stale(v[0])]
+    if not todo:
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    objs, procs = [], []
-    for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
-        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
-        objs.append(obj)
-    for cmd, p in procs:
+    jobs = []
+    for lib, tag, extra in todo:
+        os.makedirs(os.path.join(BUILD, tag), exist_ok=True)
+        objs = []
+        for src in SOURCES:
+            obj = os.path.join(BUILD, tag, src.replace(".cu", ".o"))
+            cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+            if verbose:
+                cmd.insert(1, "-Xptxas=-v")
+            jobs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+            objs.append(obj)
+        jobs.append((lib, objs))
+    links = []
+    for job in jobs:
+        if isinstance(job[1], list):
+            links.append(job)
+            continue
+        cmd, p = job
         out, _ = p.communicate()
         if p.returncode != 0:
             raise RuntimeError("nvcc failed: %s\n%s" % (" ".join(cmd), out.decode(errors="replace")))
         if verbose and out:
             sys.stdout.write(out.decode(errors="replace"))
-    tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
-    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
-    if r.returncode != 0:
-        raise RuntimeError("link failed: %s\n%s" % (" ".join(cmd), r.stdout.decode(errors="replace")))
-    os.replace(tmp, LIB)
+    for lib, objs in links:
+        tmp = lib + ".tmp"
+        cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+        if r.returncode != 0:
+            raise RuntimeError("link failed: %s\n%s" % (" ".join(cmd), r.stdout.decode(errors="replace")))
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -679,6 +679,7 @@ const char* dfb_error_string(int s) {
     case DFB_ERR_TIMEOUT: return "device wait timed out";
     case DFB_ERR_CUDA: return "CUDA error";
     case DFB_ERR_CAPACITY: return "request exceeds the fixed scratch of dfb_composite_noalloc";
+    case DFB_ERR_CHECK: return "device-side check failed (checked build)";
     default: return "unknown status";
   }
 }
@@ -994,7 +995,8 @@ int take_device_error(dfb_ctx* h) {
   if (e != cudaSuccess) return cuda_status(e);
   if (!v) return DFB_OK;
   e = cudaMemset(h->lastErr, 0, sizeof(unsigned));
-  return e != cudaSuccess ? cuda_status(e) : DFB_ERR_TIMEOUT;
+  if (e != cudaSuccess) return cuda_status(e);
+  return (v & dfb::kErrCheck) ? DFB_ERR_CHECK : DFB_ERR_TIMEOUT;
 }
 
 int end_one(dfb_ctx* h, cudaStream_t s) {

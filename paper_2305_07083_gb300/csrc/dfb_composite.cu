@@ -132,7 +132,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, const
 
 __device__ __forceinline__ void give_up(const LaunchCtl& ctl, volatile int* abort) {
   *abort = 1;
-  atomicOr(ctl.err, 1u);
+  atomicOr(ctl.err, kErrTimeout);
 }
 
 // Insert k into the sorted per-thread window kb[0..m-1] (stride kP),
@@ -185,6 +185,9 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
     const int it = blockIdx.x + kk * (int)gridDim.x;
     if (it >= totalItems || lane != 0) return;
     const ItemLoc L = locate(frames, itemBase, nFrames, it);
+    if (!DFB_CHECK(L.f >= 0 && L.f < nFrames && L.tile >= 0 && L.tile < frames[L.f].nTiles,
+                   ctl.err))
+      return;
     const int q = kk % kMetaQ;
     qLoc[q] = make_int4(L.f, L.tile, L.chunk, L.gt);
     fence_proxy_async();  // the slot's previous block was read through the generic proxy
@@ -238,6 +241,12 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
     }
     if (!ok) break;
     if (tailItem == k) tail = head;  // nothing outstanding: the padding is free too
+    if (!DFB_CHECK((uint64_t)(head % ringBytes) + need <= ringBytes && head + need - tail <= ringBytes &&
+                       (!staged || n <= kN) && (cur.chunk + 1) * P <= T * T,
+                   ctl.err)) {
+      ok = false;
+      break;
+    }
     const uint32_t start = (uint32_t)(head % ringBytes);
     head += need;
     ItemMeta* meta = metas + s;
@@ -282,7 +291,7 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
         const uint64_t t0 = global_ns();
         while (!mbar_try_wait(&bars[qq], (par >> qq) & 1u)) {
           if (global_ns() - t0 > ctl.waitNs) {
-            if (lane == 0) atomicOr(ctl.err, 2u);
+            if (lane == 0) atomicOr(ctl.err, kErrDrain);
             break;
           }
         }
@@ -542,7 +551,7 @@ __device__ __forceinline__ PixWork prepare(const FrameArgs* frames, const int* i
 __device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& w, int lane,
                                              int warp, float c0, float c1, float c2, float al,
                                              bool covered, float4 S, float4 M, float4 CP,
-                                             const SrgbTables* tb) {
+                                             const SrgbTables* tb, unsigned* err) {
   const unsigned flags = A->flags;
   const bool acc = (flags & DFB_FLAG_ACCUMULATE) != 0;
   float vsum = 0.0f;
@@ -553,7 +562,9 @@ __device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& 
       c0 = A->bgR; c1 = A->bgG; c2 = A->bgB; al = A->bgA;
     }
     const float4 col = make_float4(c0, c1, c2, al);
-    if (flags & DFB_FLAG_WRITE_COLOR) A->color[w.pix] = col;
+    const bool pixOk = DFB_CHECK(w.pix < (size_t)A->W * A->H, err);
+    const bool stateOk = DFB_CHECK(w.sidx < (size_t)A->nTiles * A->T * A->T, err);
+    if ((flags & DFB_FLAG_WRITE_COLOR) && pixOk) A->color[w.pix] = col;
     float4 out = col;
     if (acc) {
       float4 Sn, tot;
@@ -569,7 +580,7 @@ __device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& 
   }
         DFB_KAHAN(x) DFB_KAHAN(y) DFB_KAHAN(z) DFB_KAHAN(w)
 #undef DFB_KAHAN
-        A->comp[w.sidx] = cn;
+        if (stateOk) A->comp[w.sidx] = cn;
       } else {
         Sn = make_float4(S.x + col.x, S.y + col.y, S.z + col.z, S.w + col.w);
         tot = Sn;
@@ -583,12 +594,14 @@ __device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& 
         M.z = fmaf(col.z - S.z * iN1, col.z - mean.z, M.z);
         M.w = fmaf(col.w - S.w * iN1, col.w - mean.w, M.w);
       }
-      A->accum[w.sidx] = Sn;
-      A->m2[w.sidx] = M;
+      if (stateOk) {
+        A->accum[w.sidx] = Sn;
+        A->m2[w.sidx] = M;
+      }
       vsum = (M.x + M.y + M.z) * iN1;
       out = mean;
     }
-    if (flags & DFB_FLAG_PACK_RGBA8)
+    if ((flags & DFB_FLAG_PACK_RGBA8) && pixOk)
       A->rgba8[w.pix] = pack_rgba8(pixel_op(out, A->pixelOp, A->exposure), tb);
   }
   if (acc && warp * 32 < w.P) {
@@ -596,8 +609,8 @@ __device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& 
     float v = vsum;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0)
-      A->varPartial[(size_t)w.tile * A->slots + ((w.chunk * w.P + warp * 32) >> 5)] = v;
+    const size_t slot = (size_t)w.tile * A->slots + ((w.chunk * w.P + warp * 32) >> 5);
+    if (lane == 0 && DFB_CHECK(slot < (size_t)A->nTiles * A->slots, err)) A->varPartial[slot] = v;
   }
 }
 
@@ -605,7 +618,7 @@ template <int DT, int G>
 __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                          int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
                          ItemMeta* metas, uint64_t* fullB, uint64_t* emptyB, volatile int* abort,
-                         const SrgbTables* tb) {
+                         const SrgbTables* tb, uint32_t ringBytes) {
   const int group = threadIdx.x / kP;
   const int t = threadIdx.x - group * kP;  // pixel of the item, 0 .. kP-1
   const int lane = t & 31, warp = t >> 5;
@@ -628,15 +641,21 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
     const int n = meta->n;
     const int P = w.P;
     const unsigned char* base = ring + meta->start;
+    const bool accRead = w.active && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1;
+    const uint32_t stateRows = accRead ? ((A->kahan && !A->kahanFirst) ? 3u : 2u) : 0u;
+    const bool inRing = DFB_CHECK(n <= kN && (uint64_t)meta->start + meta->stateOff +
+                                                     (uint64_t)stateRows * P * 16u <= ringBytes,
+                                  ctl.err);
     float c0 = 0.f, c1 = 0.f, c2 = 0.f, al = 0.f;
     bool covered = true;
-    if (w.active) covered = composite_staged<DT>(A->mode, n, P, base, meta, t, w.p, c0, c1, c2, al);
+    if (w.active && inRing)
+      covered = composite_staged<DT>(A->mode, n, P, base, meta, t, w.p, c0, c1, c2, al);
     // the item's accumulation state: from the ring into registers, then the
     // ring space goes back to the producer before the epilogue's math and
     // stores
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 S = zero4, M = zero4, CP = zero4;
-    if (w.active && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1) {
+    if (accRead && inRing) {
       const float4* sState = reinterpret_cast<const float4*>(base + meta->stateOff);
       S = sState[t];
       M = sState[P + t];
@@ -644,7 +663,7 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&emptyB[s]);  // ring space free for the producer
-    finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, tb);
+    finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, tb, ctl.err);
   }
 }
 
@@ -680,7 +699,7 @@ __global__ void __launch_bounds__(Shape<G>::threads, PER) k_composite(
                  fullB, emptyB, queueB, abort);
   else
     consumer<DT, G>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
-                    tb);
+                    tb, ringBytes);
 }
 
 // Tiles with more than kN fragments, after the main kernel: the work items of
@@ -693,7 +712,8 @@ __global__ void __launch_bounds__(Shape<G>::threads, PER) k_composite(
 template <int DT>
 __global__ void __launch_bounds__(kP) k_composite_long(const FrameArgs* __restrict__ frames,
                                                        const int* __restrict__ itemBase,
-                                                       int nFrames, LongList lng) {
+                                                       int nFrames, LongList lng,
+                                                       unsigned* err) {
   extern __shared__ __align__(16) unsigned char lsmem[];
   SrgbTables* tb = reinterpret_cast<SrgbTables*>(lsmem);
   uint64_t* window = reinterpret_cast<uint64_t*>(lsmem + sizeof(SrgbTables));
@@ -714,6 +734,9 @@ __global__ void __launch_bounds__(kP) k_composite_long(const FrameArgs* __restri
       if (frames[mid].tileBase <= gt) lo = mid; else hi = mid - 1;
     }
     const FrameArgs* A = frames + lo;
+    if (!DFB_CHECK(gt >= A->tileBase && gt < A->tileBase + A->nTiles && c >= 0 && c < A->chunks,
+                   err))
+      continue;
     const TileBlock* blk = A->blocks + gt;
     const int n = blk->n, off = blk->off;
     {
@@ -731,7 +754,7 @@ __global__ void __launch_bounds__(kP) k_composite_long(const FrameArgs* __restri
         M = A->m2[w.sidx];
         if (A->kahan && !A->kahanFirst) CP = A->comp[w.sidx];
       }
-      finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, tb);
+      finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, tb, err);
     }
   }
 }
@@ -852,16 +875,17 @@ cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int n
     const size_t smem = sizeof(SrgbTables) + kWindowBytes;
     switch (dtype) {
       case DFB_F32:
-        k_composite_long<DFB_F32><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng);
+        k_composite_long<DFB_F32><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng, ctl.err);
         break;
       case DFB_F16:
-        k_composite_long<DFB_F16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng);
+        k_composite_long<DFB_F16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng, ctl.err);
         break;
       case DFB_BF16:
-        k_composite_long<DFB_BF16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng);
+        k_composite_long<DFB_BF16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng, ctl.err);
         break;
       default:
-        k_composite_long<DFB_FP8E4M3><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng);
+        k_composite_long<DFB_FP8E4M3><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng,
+                                                             ctl.err);
         break;
     }
     e = cudaGetLastError();

@@ -106,6 +106,20 @@ struct LongList {
   int items = 0;
 };
 
+// Bits of a launch's device error word.
+constexpr unsigned kErrTimeout = 1u;   // a wait ran out
+constexpr unsigned kErrDrain = 2u;     // a copy in flight did not land while giving up
+constexpr unsigned kErrCheck = 8u;     // a device-side check of the checked build failed
+
+// Device-side checks, compiled in by -DDFB_CHECKED (libdfb_checked.so): a
+// failed check sets kErrCheck in the error word and the guarded access is
+// skipped.  In the normal build the condition is not evaluated.
+#ifdef DFB_CHECKED
+#define DFB_CHECK(cond, err) ((cond) || (atomicOr((err), ::dfb::kErrCheck), false))
+#else
+#define DFB_CHECK(cond, err) (true)
+#endif
+
 // Controls of one composite launch.
 struct LaunchCtl {
   unsigned long long waitNs;  // bound on every barrier wait inside the kernel

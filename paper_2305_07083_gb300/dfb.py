@@ -13,7 +13,11 @@ import os
 
 import numpy as np
 
-from ._build import LIB
+from ._build import LIB as _LIB_NORMAL, LIB_CHECKED
+
+# DFB_CHECKED=1 in the environment loads the checked build (device-side bounds
+# checks that report DFB_ERR_CHECK); it must be set before the first call.
+LIB = LIB_CHECKED if os.environ.get("DFB_CHECKED") == "1" else _LIB_NORMAL
 
 # enums (include/dfb.h)
 DFB_BLEND_DEPTH, DFB_BLEND_ORDERED, DFB_ZCOMPOSITE, DFB_AVERAGE = 0, 1, 2, 3
@@ -22,6 +26,7 @@ DFB_F32, DFB_F16, DFB_BF16, DFB_FP8E4M3 = 0, 1, 2, 3
 DFB_OK = 0
 DFB_ERR_INVALID_ARG, DFB_ERR_TILE_RANGE, DFB_ERR_STATE, DFB_ERR_INCOMPLETE = -1, -2, -3, -4
 DFB_ERR_OOM, DFB_ERR_TIMEOUT, DFB_ERR_CUDA, DFB_ERR_CAPACITY = -5, -6, -7, -8
+DFB_ERR_CHECK = -9
 DFB_FLAG_ACCUMULATE, DFB_FLAG_WRITE_COLOR, DFB_FLAG_PACK_RGBA8, DFB_FLAG_DEFER_ALLOC = 1, 2, 4, 8
 DFB_FLAGS_DEFAULT = DFB_FLAG_ACCUMULATE | DFB_FLAG_WRITE_COLOR | DFB_FLAG_PACK_RGBA8
 DFB_PTR_AUTO, DFB_PTR_DEVICE, DFB_PTR_HOST = 0, 1, 2
@@ -72,7 +77,7 @@ def lib():
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB):
-        raise RuntimeError("libdfb.so is not built (%s); call paper_2305_07083_gb300.build()" % LIB)
+        raise RuntimeError("%s is not built; call paper_2305_07083_gb300.build()" % LIB)
     L = C.CDLL(LIB)
     sig = {
         "dfb_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(H)]),

@@ -35,17 +35,19 @@ def declared_symbols():
     return sorted(set(re.findall(r"DFB_API\s+[\w\s\*]+?\b(dfb_\w+)\s*\(", text)))
 
 
-def test_exports_every_declared_symbol():
+@pytest.mark.parametrize("lib", ["normal", "checked"])
+def test_exports_every_declared_symbol(lib):
+    from paper_2305_07083_gb300 import _build
     syms = declared_symbols()
     assert len(syms) >= 25
-    L = C.CDLL(D.LIB)
+    L = C.CDLL(_build.LIB if lib == "normal" else _build.LIB_CHECKED)
     for s in syms:
         assert hasattr(L, s), s
 
 
 def test_error_strings_and_version():
     assert D.dfb_version() >= 10000
-    for code in (0, -1, -2, -3, -4, -5, -6, -7):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7, -8, -9):
         assert D.dfb_error_string(code) not in ("", "unknown status")
     assert D.dfb_error_string(-99) == "unknown status"
 
