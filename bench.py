@@ -58,6 +58,36 @@ def _oracle_tile(args):
     return o.composite_tile(rgba.astype(np.float64), depth, keys, sidx, o.BLEND_DEPTH).shape[0]
 
 
+def _oracle_tile_rgba(args):
+    from oracle import dfb_oracle as o
+    rgba, depth, keys, sidx = args
+    return o.composite_tile(rgba.astype(np.float64), depth, keys, sidx, o.BLEND_DEPTH)
+
+
+def oracle_error(sc, rgba, gpu_color, pool, n_tiles=64):
+    """Per-channel max-abs and RMS difference between the GPU colour of a
+    frame and the oracle on a seeded sample of its tiles."""
+    from oracle import dfb_oracle as o
+    lists, _, _ = o.bucket(sc.tile_ids, sc.keys, sc.n_tiles)
+    tiles = np.random.default_rng(321).choice(sc.n_tiles, size=min(n_tiles, sc.n_tiles),
+                                             replace=False)
+    work = []
+    for t in tiles:
+        idx = np.array(lists[t], dtype=np.int64)
+        work.append((rgba[idx], sc.depth[idx], sc.keys[idx], idx))
+    res = pool.map(_oracle_tile_rgba, work, chunksize=2)
+    diffs = []
+    tiles_x = sc.W // sc.T
+    for t, want in zip(tiles, res):
+        y0, x0 = (t // tiles_x) * sc.T, (t % tiles_x) * sc.T
+        got = gpu_color[y0:y0 + sc.T, x0:x0 + sc.T].reshape(-1, 4).astype(np.float64)
+        diffs.append(got - want)
+    d = np.concatenate(diffs)
+    return {"tiles": len(tiles), "channels": "RGBA",
+            "max_abs": [float(v) for v in np.abs(d).max(axis=0)],
+            "rms": [float(v) for v in np.sqrt((d * d).mean(axis=0))]}
+
+
 def cpu_oracle_rate(sc, rgba, n_tiles_sample, pool, min_seconds=0.0, max_passes=64):
     """Fragment-pixels/s of the oracle compositing a seeded sample of tiles,
     repeated until at least ``min_seconds`` of work has been timed."""
@@ -576,6 +606,19 @@ def main():
     algo_bytes = frag_b + state_avg
     achieved = algo_bytes / (comp_ms / 1e3) / 1e9
 
+    # GPU colour of frame 0 (outside the timed region): the oracle leg below
+    # reports the per-channel error against it
+    gpu_frame0 = None
+    if pool is not None:
+        r0 = Runner(sc, [frames[0]], depth, D.DFB_F32, tune=tune)
+        D.dfb_begin_frame(r0.h, 0)
+        D.dfb_submit_tiles(r0.h, r0.tile_ids, r0.keys, r0.rptr[0], r0.dptr, None,
+                           D.DFB_PTR_DEVICE)
+        D.dfb_end_frame(r0.h, stream)
+        gpu_frame0 = np.empty((sc.H, sc.W, 4), np.float32)
+        D.dfb_read_color(r0.h, gpu_frame0)
+        r0.close()
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -659,13 +702,16 @@ def main():
     if pool is not None:
         rate, fpx, dt, nt = cpu_oracle_rate(sc, frame0, sc.n_tiles, pool,
                                             min_seconds=10.0)
-        pool.close()
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "cpu": cpu_model(),
                                "sample": "frame 0 composited %d times (%d tile tasks, %d fragment-"
                                          "pixels, %.1f s): BLEND_DEPTH FP64 per-pixel sort + over; "
                                          "accumulation, variance and pack not included; %d spawned "
                                          "processes" % (nt // sc.n_tiles, nt, fpx, dt, cores)}
+        err = oracle_error(sc, frame0, gpu_frame0, pool)
+        pool.close()
+        out["error_vs_oracle"] = dict(err, frame="frame 0, FP32 storage, colour buffer",
+                                      tolerance=1e-5)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:

@@ -344,23 +344,27 @@ def test_read_before_any_frame_is_state_error():
 
 
 # --- the full-size workload, in the launch configuration the benchmark times -------------
-def test_full_size_2048_sampled_tiles():
-    """2048x2048, 64 bricks, 3 accumulated frames: every output of a seeded
-    sample of tiles (plus the fullest tile) against the oracle."""
+@pytest.mark.parametrize("dtype", [D.DFB_F32, D.DFB_F16, D.DFB_BF16, D.DFB_FP8E4M3])
+def test_full_size_2048_sampled_tiles(dtype):
+    """2048x2048, 64 bricks, 3 accumulated frames in each storage dtype (the
+    launch shape the benchmark uses for it): every output of a seeded sample
+    of tiles (plus the fullest tile) against the oracle fed the same stored
+    values."""
     sc = scenes.scene_2048(seed=0, jitter_sigma=0.02)
     counts = sc.counts()
     rng = np.random.default_rng(1)
     sample = sorted(set(rng.choice(sc.n_tiles, 24, replace=False).tolist()) |
                     {int(np.argmax(counts)), int(np.argmin(counts))})
-    fb = GpuFrameBuffer(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH)
+    fb = GpuFrameBuffer(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH, dtype)
     imgs = []
     for f in range(3):
-        rgba = sc.frame_rgba(f)
+        stored, scales = scenes.store_rgba(sc.frame_rgba(f), dtype)
         fb.begin(f > 0)
-        fb.submit_pool(sc.tile_ids, sc.keys, rgba, sc.depth)
+        fb.submit_pool(sc.tile_ids, sc.keys, stored, sc.depth, scales)
         fb.end()
         imgs.append(o.composite_frame(sc.W, sc.H, sc.T, o.BLEND_DEPTH, sc.tile_ids, sc.keys,
-                                      rgba.astype(np.float64), sc.depth, tiles=sample))
+                                      o.dequantize(stored, dtype, scales), sc.depth,
+                                      tiles=sample))
         fb.keep.clear()
     col, acc = fb.color(), fb.accum()
     px, tv = fb.variance()
