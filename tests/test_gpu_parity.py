@@ -51,7 +51,8 @@ def test_single_frame_256_eight_bricks(mode):
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("W,H,T", [(200, 136, 64), (37, 29, 16), (13, 9, 4), (70, 33, 8)])
+@pytest.mark.parametrize("W,H,T", [(200, 136, 64), (37, 29, 16), (13, 9, 4), (70, 33, 8),
+                                   (300, 130, 128), (260, 300, 256)])
 def test_ragged_frames_random_counts(mode, W, H, T):
     tiles = (-(-W // T)) * (-(-H // T))
     counts = np.random.default_rng(W * 7 + H).integers(0, 7, tiles)
