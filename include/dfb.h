@@ -4,14 +4,14 @@
  * The operations follow Usher et al., "Scalable Ray Tracing Using the
  * Distributed FrameBuffer" (EuroVis 2019):
  *   - a frame is bracketed by begin/end and fed tile by tile with setTile
- *     (Sec. 3.1, "Tile Processing Pipeline");
+ *     (Sec. 3.1, the tile processing pipeline);
  *   - a tile carries RGBA colour and depth for TxT pixels (Listing 1, Tile);
  *   - per tile, a dependency tree of generations tells the owner how many
  *     inputs to wait for (Sec. 3.1.1, Listing 3: a generation-0 background
  *     tile declares the number of generation-1 children);
- *   - the AlphaBlend tile operation sorts every pixel's fragments by depth and
- *     blends them (Sec. 4.2, Listing 4); with a rank-order tree the tiles are
- *     blended in list order instead (Sec. 4.2);
+ *   - the AlphaBlend tile operation orders each pixel's fragments by depth
+ *     before combining them (Sec. 4.2, Listing 4); with a rank-order tree the
+ *     tiles are combined in list order instead (Sec. 4.2);
  *   - progressive refinement keeps accumulation and variance tiles
  *     (Listing 1, TileOperation; Sec. 4.1.1 uses the variance to steer work);
  *   - the finished tile is converted to the RGBA8 or RGBAF32 display format

@@ -15,12 +15,12 @@ to the code; the list of readings is:
 * Tile colour is premultiplied RGBA (Listing 1 stores ``float color[4*T*T]``
   without saying which).
 * Blending is the Porter-Duff "over" operator applied front to back (Sec. 4.2
-  says only that AlphaBlend sorts the pixels by depth and blends them).
+  names the depth ordering of AlphaBlend but not its blend operator).
 * Ties in depth are broken by (order key, submit index); NaN depth reads as
   +inf; -0.0 reads as +0.0.
 * The background (the generation-0 tile of Sec. 4.2 / Listing 3) is blended
   behind every fragment as ``rgb*a`` with coverage ``a``.
-* Z-compositing (Sec. 2.1, "depth compositing") outputs the RGBA of the
+* Z-compositing (depth compositing, Sec. 2.1) outputs the RGBA of the
   nearest fragment unchanged; a pixel no fragment covers (nearest depth +inf,
   or no fragment at all) shows the premultiplied background.
 * The accumulation buffer of Listing 1 holds the running sum of frames; the
@@ -34,8 +34,8 @@ to the code; the list of readings is:
 * FP16 / BF16 storage upcasts exactly; FP8 e4m3 storage decodes the code and
   multiplies by the fragment's FP32 scale.
 * The image-parallel tile operation with redundantly assigned tiles
-  (Sec. 4.1.1: the tiles rendered with different seeds are averaged into one
-  tile equivalent to a higher sampling rate) weighs every tile of an image
+  (Sec. 4.1.1: renders of one tile made with different seeds are averaged,
+  which amounts to rendering it with more samples) weighs every tile of an image
   tile equally: the per-pixel mean of the k tiles' RGBA, ignoring depth.  The
   mean then goes over the background like the other tile operations; a tile
   that received nothing shows the background.
@@ -215,8 +215,8 @@ def composite_tile(rgba, depth, keys, sidx, mode: int, bg=(0.0, 0.0, 0.0, 0.0)):
     keys: (n,) order keys; sidx: (n,) submit indices.  Returns (P, 4).
 
     BLEND_DEPTH: per pixel, sort the fragments by (depth, key, submit index)
-    and blend front to back (Sec. 4.2: "sorts the pixels by depth and blends
-    them"), then the background.  BLEND_ORDERED: blend in (key, submit index)
+    and blend front to back (Sec. 4.2: depth order, then blending), then the
+    background.  BLEND_ORDERED: blend in (key, submit index)
     order for every pixel (Sec. 4.2, tree built as a list).  ZCOMPOSITE: the
     RGBA of the per-pixel minimum of (depth, key, submit index), or the
     premultiplied background where that depth is +inf.  AVERAGE: the mean of

@@ -258,7 +258,7 @@ def test_accumulate_fsum_and_constant():
 
 def test_redundant_passes_average_equals_accumulation():
     """Sec. 4.1.1: averaging k redundantly rendered tiles equals accumulating
-    k passes (a higher sampling rate)."""
+    k passes (more samples per pixel)."""
     rng = np.random.default_rng(12)
     k = 6
     passes = [rng.uniform(0, 1, (16, 4)) for _ in range(k)]
@@ -420,9 +420,9 @@ def test_average_ignores_depth_and_order():
 
 
 def test_average_of_k_tiles_equals_k_accumulated_frames():
-    """Sec. 4.1.1: averaging k redundantly rendered tiles gives the tile of a
-    k-times higher sampling rate, i.e. what accumulating the k renders as k
-    frames gives."""
+    """Sec. 4.1.1: averaging k redundantly rendered tiles gives the tile
+    rendered with k times the samples, i.e. what accumulating the k renders as
+    k frames gives."""
     rng = np.random.default_rng(43)
     k = 6
     rgba = rng.random((k, 64, 4))
