@@ -1022,6 +1022,7 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
   lng.base = lng.tiles + nLong;
   lng.n = nLong;
   lng.items = nLong * h->chunks;
+  for (int t : h->longTiles) lng.maxFragments = std::max(lng.maxFragments, h->fragCount[t]);
   // The bucketing reads only library-owned buffers, so it runs on the side
   // stream, overlapping the previous frame's composite; under stream capture
   // everything stays on `s`.
@@ -1083,7 +1084,7 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
   if (st != DFB_OK) return st;
   cudaError_t e = cudaSuccess;
   size_t r = 0;
-  int tileBase = 0, items = 0, nLong = 0;
+  int tileBase = 0, items = 0, nLong = 0, maxLong = 0;
   std::vector<int> longChunks;
   const int dtype = hs[0]->cfg.dtype;
   bool anyAcc = false;
@@ -1099,6 +1100,7 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
     for (int t : h->longTiles) {
       b.hLong[nLong++] = tileBase + t;
       longChunks.push_back(h->chunks);
+      maxLong = std::max(maxLong, h->fragCount[t]);
     }
     fill_frame_args(h, b.hFrames[i], tileBase, b.srecs, b.blocks);
     b.hItemBase[i] = items;
@@ -1126,6 +1128,7 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
                         bs);
   dfb::LongList lng;
   lng.n = nLong;
+  lng.maxFragments = maxLong;
   lng.tiles = b.dLong;
   lng.base = b.dLong + nLong;
   for (int i = 0; i < nLong; ++i) {
@@ -1519,6 +1522,7 @@ int dfb_graph_create(const dfb_handle* hs, int n, dfb_graph* out) {
     for (int t : h->longTiles) {
       longs.push_back(tileBase + t);
       longChunks.push_back(h->chunks);
+      g->lng.maxFragments = std::max(g->lng.maxFragments, h->fragCount[t]);
     }
     for (const FragRec& fr : h->recs) {
       FragRec r = fr;

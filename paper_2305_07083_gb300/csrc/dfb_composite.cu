@@ -410,10 +410,17 @@ __device__ __forceinline__ bool composite_staged(int mode, int n, int P, const u
   return true;
 }
 
+// Long lists (more than kN fragments), fragments read from HBM.  In
+// BLEND_DEPTH, `sD` (when not null) holds the item's depth slabs in shared
+// memory (stride P): the pixel then first takes a speculative pass in list
+// order (as composite_staged does), and only if its depths are out of order
+// the exact path below, which works in rounds of a per-pixel window of the
+// kSortWindow nearest fragments not yet blended.
 template <int DT>
 __device__ __forceinline__ bool composite_streamed(int mode, int n, const FragRec* list,
                                                    uint64_t* kbAll, int t, int p,
-                                                   float& c0, float& c1, float& c2, float& al) {
+                                                   float& c0, float& c1, float& c2, float& al,
+                                                   const float* sD = nullptr, int P = 0) {
   if (mode == DFB_BLEND_ORDERED) {
     for (int ib = 0; ib < n; ib += 8) {
       float4 c[8];
@@ -459,6 +466,37 @@ __device__ __forceinline__ bool composite_streamed(int mode, int n, const FragRe
     c0 = f.x; c1 = f.y; c2 = f.z; al = f.w;
     return true;
   }
+  if (sD) {
+    uint32_t last = 0, emptyBits = 0;
+    bool inOrder = true;
+    for (int ib = 0; ib < n; ib += 8) {
+      float4 f[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (ib + u < n) f[u] = Px<DT>::global(list[ib + u].rgba, p, list[ib + u].scale);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (ib + u < n) {
+          const uint32_t key = depth_bits(sD[(ib + u) * P + t]);
+          if (key != kInfBits) {
+            inOrder = inOrder && key >= last;
+            last = key;
+            over(f[u], c0, c1, c2, al);
+          } else {
+            emptyBits |= __float_as_uint(f[u].x) | __float_as_uint(f[u].y) |
+                         __float_as_uint(f[u].z) | __float_as_uint(f[u].w);
+          }
+        }
+    }
+    if (inOrder) {
+      if (emptyBits)
+        for (int i = 0; i < n; ++i)
+          if (depth_bits(sD[i * P + t]) == kInfBits)
+            over(Px<DT>::global(list[i].rgba, p, list[i].scale), c0, c1, c2, al);
+      return true;
+    }
+    c0 = c1 = c2 = al = 0.0f;
+  }
   // rounds: each round keeps the window's nearest keys above the last blended
   uint64_t* kb = kbAll + t;
   uint64_t lo = 0;
@@ -469,7 +507,8 @@ __device__ __forceinline__ bool composite_streamed(int mode, int n, const FragRe
     for (int ib = 0; ib < n; ib += 8) {
       float z[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) z[u] = (ib + u < n) ? __ldg(list[ib + u].depth + p) : 0.0f;
+      for (int u = 0; u < 8; ++u)
+        z[u] = (ib + u < n) ? (sD ? sD[(ib + u) * P + t] : __ldg(list[ib + u].depth + p)) : 0.0f;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int i = ib + u;
@@ -702,24 +741,40 @@ __global__ void __launch_bounds__(Shape<G>::threads, PER) k_composite(
                     tb, ringBytes);
 }
 
+// Depth slabs a long-tile item can stage in shared memory (1 KB each at 256
+// pixels per item); longer lists read their depths from HBM.
+constexpr int kLongStage = 160;
+
 // Tiles with more than kN fragments, after the main kernel: the work items of
 // all long tiles are spread over the CTAs (kP threads, one pixel per thread).
-// The fragments are streamed from HBM in rounds of a per-pixel sort window
-// held in shared memory (composite_streamed), then the pixel goes through the
-// same epilogue as in the main kernel.  Long lists are rare, and keeping this
-// path out of k_composite keeps that kernel's register count low enough for
-// more resident warps.
+// In BLEND_DEPTH the item's depth slabs (up to `stageN` of them) are first
+// copied into shared memory with bulk copies, so that the pixel's
+// speculative in-order pass and, where needed, its exact windowed rounds
+// read depths from there; RGBA is read from HBM in batches of 8 fragments.
+// Two CTAs per SM (128 registers) measured faster than one CTA without the
+// register cap.
+// The pixel then goes through the same epilogue as in the main kernel.  Long
+// lists are rare, and keeping this path out of k_composite keeps that
+// kernel's register count low enough for more resident warps.
 template <int DT>
-__global__ void __launch_bounds__(kP) k_composite_long(const FrameArgs* __restrict__ frames,
+__global__ void __launch_bounds__(kP, 2) k_composite_long(const FrameArgs* __restrict__ frames,
                                                        const int* __restrict__ itemBase,
-                                                       int nFrames, LongList lng,
-                                                       unsigned* err) {
-  extern __shared__ __align__(16) unsigned char lsmem[];
+                                                       int nFrames, LongList lng, int stageN,
+                                                       LaunchCtl ctl) {
+  extern __shared__ __align__(128) unsigned char lsmem[];
   SrgbTables* tb = reinterpret_cast<SrgbTables*>(lsmem);
-  uint64_t* window = reinterpret_cast<uint64_t*>(lsmem + sizeof(SrgbTables));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(lsmem + sizeof(SrgbTables));
+  uint64_t* window = reinterpret_cast<uint64_t*>(lsmem + sizeof(SrgbTables) + 128);
+  float* sDepth = reinterpret_cast<float*>(lsmem + sizeof(SrgbTables) + 128 + kWindowBytes);
   load_srgb(tb, kP);
-  __syncthreads();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) {
+    mbar_init(bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  bool inFlight = false;  // a staging copy may still land (after a timed-out wait)
   for (int u = blockIdx.x; u < lng.items; u += gridDim.x) {
     int j = 0, hj = lng.n - 1;  // long tile with the largest item base <= u
     while (j < hj) {
@@ -735,27 +790,57 @@ __global__ void __launch_bounds__(kP) k_composite_long(const FrameArgs* __restri
     }
     const FrameArgs* A = frames + lo;
     if (!DFB_CHECK(gt >= A->tileBase && gt < A->tileBase + A->nTiles && c >= 0 && c < A->chunks,
-                   err))
+                   ctl.err))
       continue;
     const TileBlock* blk = A->blocks + gt;
     const int n = blk->n, off = blk->off;
-    {
-      const int item = __ldg(itemBase + lo) + (gt - A->tileBase) * A->chunks + c;
-      const PixWork w = prepare(frames, itemBase, nFrames, item, t);
-      float c0 = 0.f, c1 = 0.f, c2 = 0.f, al = 0.f;
-      bool covered = true;
-      if (w.active)
-        covered = composite_streamed<DT>(A->mode, n, A->srecs + off, window, t, w.p, c0, c1, c2,
-                                         al);
-      const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      float4 S = zero4, M = zero4, CP = zero4;
-      if (w.active && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1) {
-        S = A->accum[w.sidx];
-        M = A->m2[w.sidx];
-        if (A->kahan && !A->kahanFirst) CP = A->comp[w.sidx];
+    const FragRec* list = A->srecs + off;
+    const int item = __ldg(itemBase + lo) + (gt - A->tileBase) * A->chunks + c;
+    const PixWork w = prepare(frames, itemBase, nFrames, item, t);
+    const bool stage = A->mode == DFB_BLEND_DEPTH && n <= stageN;
+    if (stage) {
+      // one bulk copy per fragment's depth slab, issued by warp 0
+      const uint32_t slab = (uint32_t)w.P * 4u;
+      if (t == 0) mbar_arrive_expect_tx(bar, (uint32_t)n * slab);
+      if (warp == 0) {
+        __syncwarp();
+        for (int i = lane; i < n; i += 32)
+          bulk_g2s(sDepth + (size_t)i * w.P, list[i].depth + (size_t)c * w.P, slab, bar);
       }
-      finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, tb, err);
+      inFlight = true;
+      bool got = mbar_try_wait(bar, parity);
+      const uint64_t t0 = global_ns();
+      while (!got && global_ns() - t0 <= ctl.waitNs) got = mbar_try_wait(bar, parity);
+      if (!__syncthreads_and(got)) {
+        if (t == 0) atomicOr(ctl.err, kErrTimeout);
+        break;
+      }
+      inFlight = false;
+      parity ^= 1u;
     }
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f, al = 0.f;
+    bool covered = true;
+    if (w.active)
+      covered = composite_streamed<DT>(A->mode, n, list, window, t, w.p, c0, c1, c2, al,
+                                       stage ? sDepth : nullptr, w.P);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 S = zero4, M = zero4, CP = zero4;
+    if (w.active && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1) {
+      S = A->accum[w.sidx];
+      M = A->m2[w.sidx];
+      if (A->kahan && !A->kahanFirst) CP = A->comp[w.sidx];
+    }
+    finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, tb, ctl.err);
+    __syncthreads();  // every thread is done with the staged depths
+  }
+  if (inFlight && t == 0) {
+    // leave no bulk copy in flight into this CTA's shared memory
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+      if (global_ns() - t0 > ctl.waitNs) {
+        atomicOr(ctl.err, kErrDrain);
+        break;
+      }
   }
 }
 
@@ -868,24 +953,41 @@ cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int n
     int dev = 0;
     e = cudaGetDevice(&dev);
     if (e == cudaSuccess && (dev < 0 || dev >= 64)) e = cudaErrorInvalidDevice;
-    if (e == cudaSuccess && !sms[dev])
+    if (e == cudaSuccess && !sms[dev]) {
       e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+      const int maxSmem = (int)(sizeof(SrgbTables) + 128 + kWindowBytes) + kLongStage * kP * 4;
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_composite_long<DFB_F32>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_composite_long<DFB_F16>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_composite_long<DFB_BF16>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_composite_long<DFB_FP8E4M3>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
+      if (e != cudaSuccess) sms[dev] = 0;
+    }
     if (e != cudaSuccess) return e;
     const int grid = lng.items < 8 * sms[dev] ? lng.items : 8 * sms[dev];
-    const size_t smem = sizeof(SrgbTables) + kWindowBytes;
+    const int stageN = lng.maxFragments < kLongStage ? lng.maxFragments : kLongStage;
+    const size_t smem = sizeof(SrgbTables) + 128 + kWindowBytes + (size_t)stageN * kP * 4;
     switch (dtype) {
       case DFB_F32:
-        k_composite_long<DFB_F32><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng, ctl.err);
+        k_composite_long<DFB_F32><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng, stageN, ctl);
         break;
       case DFB_F16:
-        k_composite_long<DFB_F16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng, ctl.err);
+        k_composite_long<DFB_F16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng, stageN, ctl);
         break;
       case DFB_BF16:
-        k_composite_long<DFB_BF16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng, ctl.err);
+        k_composite_long<DFB_BF16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng, stageN,
+                                                          ctl);
         break;
       default:
         k_composite_long<DFB_FP8E4M3><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng,
-                                                             ctl.err);
+                                                             stageN, ctl);
         break;
     }
     e = cudaGetLastError();

@@ -104,6 +104,7 @@ struct LongList {
   const int* base = nullptr;
   int n = 0;
   int items = 0;
+  int maxFragments = 0;  // longest list among them
 };
 
 // Bits of a launch's device error word.

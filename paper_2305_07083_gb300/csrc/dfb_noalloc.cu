@@ -179,6 +179,9 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   lng.base = longIn + nLong;
   lng.n = nLong;
   lng.items = nLong * chunksPerTile;
+  for (int i = 0; i < nLong; ++i)
+    lng.maxFragments = perTile[longTiles[i]] > lng.maxFragments ? perTile[longTiles[i]]
+                                                                 : lng.maxFragments;
   static_assert(sizeof(void*) == sizeof(uint64_t), "64-bit pointers");
 
   // ---- inputs into the scratch (plain copies; the host arrays may be pageable) ----
