@@ -948,29 +948,31 @@ cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int n
     case DFB_BF16: e = launch_dt<DFB_BF16>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
     default: e = launch_dt<DFB_FP8E4M3>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
   }
+  // One-time set-up of the long-tile kernel per device, done on any launch
+  // (so that it never first happens inside a stream capture).
+  static int sms[64] = {0};
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess && (dev < 0 || dev >= 64)) e = cudaErrorInvalidDevice;
+  if (e == cudaSuccess && !sms[dev]) {
+    int count = 0;
+    e = cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+    const int maxSmem = (int)(sizeof(SrgbTables) + 128 + kWindowBytes) + kLongStage * kP * 4;
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_composite_long<DFB_F32>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_composite_long<DFB_F16>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_composite_long<DFB_BF16>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_composite_long<DFB_FP8E4M3>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
+    if (e == cudaSuccess) sms[dev] = count;
+  }
   if (e == cudaSuccess && lng.n > 0 && lng.items > 0) {
-    static int sms[64] = {0};
-    int dev = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess && (dev < 0 || dev >= 64)) e = cudaErrorInvalidDevice;
-    if (e == cudaSuccess && !sms[dev]) {
-      e = cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
-      const int maxSmem = (int)(sizeof(SrgbTables) + 128 + kWindowBytes) + kLongStage * kP * 4;
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_composite_long<DFB_F32>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_composite_long<DFB_F16>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_composite_long<DFB_BF16>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_composite_long<DFB_FP8E4M3>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
-      if (e != cudaSuccess) sms[dev] = 0;
-    }
-    if (e != cudaSuccess) return e;
     const int grid = lng.items < 8 * sms[dev] ? lng.items : 8 * sms[dev];
     const int stageN = lng.maxFragments < kLongStage ? lng.maxFragments : kLongStage;
     const size_t smem = sizeof(SrgbTables) + 128 + kWindowBytes + (size_t)stageN * kP * 4;
