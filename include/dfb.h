@@ -210,7 +210,10 @@ DFB_API int dfb_submit_tiles_ex(dfb_handle h, int n, const dfb_tile_desc* tiles,
    frame then stays open so the missing tiles can still be submitted), then
    enqueue the compositing, accumulation, variance and pack kernels on
    `stream` (a cudaStream_t; NULL = the legacy default stream) and return
-   without waiting.  Errors: STATE, INCOMPLETE, OOM, CUDA. */
+   without waiting.  Refused with STATE on a stream that is being captured
+   into a CUDA graph (the captured record upload would replay stale records;
+   dfb_graph_create captures frames correctly).
+   Errors: STATE, INCOMPLETE, OOM, CUDA. */
 DFB_API int dfb_end_frame(dfb_handle h, void* stream);
 
 /* ---- Prepared submissions ------------------------------------------------------

@@ -1024,12 +1024,9 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
   lng.items = nLong * h->chunks;
   for (int t : h->longTiles) lng.maxFragments = std::max(lng.maxFragments, h->fragCount[t]);
   // The bucketing reads only library-owned buffers, so it runs on the side
-  // stream, overlapping the previous frame's composite; under stream capture
-  // everything stays on `s`.
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  const bool side = cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
-                    cap == cudaStreamCaptureStatusNone;
-  if (!side) cudaGetLastError();
+  // stream, overlapping the previous frame's composite (dfb_end_frames has
+  // refused a capturing stream).
+  const bool side = true;
   cudaError_t e = cudaSuccess;
   cudaStream_t bs = side ? h->bucketStream : s;
   if (e == cudaSuccess && h->lastStreamSet && h->lastStream != s)
@@ -1112,12 +1109,9 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
   }
   b.hItemBase[n] = items;
   // Uploads and bucketing touch only this set, so they run on the device's
-  // side stream (not under stream capture), overlapping earlier work on `s`.
-  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  const bool side = cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
-                    cap == cudaStreamCaptureStatusNone;
-  if (!side) cudaGetLastError();
-  cudaStream_t bs = side ? bd.side : s;
+  // side stream, overlapping earlier work on `s`.
+  const bool side = true;
+  cudaStream_t bs = bd.side;
   if (e == cudaSuccess && side && b.used) e = cudaStreamWaitEvent(bs, b.released, 0);
   if (e == cudaSuccess && nRec)
     e = cudaMemcpyAsync(b.dRecs, b.hRecs, sizeof(FragRec) * nRec, cudaMemcpyHostToDevice, bs);
@@ -1180,11 +1174,18 @@ int dfb_end_frames(const dfb_handle* hs, int n, void* stream) {
     const int st = check_trees(hs[i]);
     if (st != DFB_OK) return st;
   }
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    // A captured end of frame would replay an upload from a staging buffer
+    // that later frames overwrite: refused (dfb_graph_* captures batches).
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) cudaGetLastError();
+    else if (cap != cudaStreamCaptureStatusNone) return DFB_ERR_STATE;
+  }
   for (int i = 0; i < n; ++i) {
     const int st = allocate(hs[i]);
     if (st != DFB_OK) return st;
   }
-  cudaStream_t s = (cudaStream_t)stream;
   const int st = n == 1 ? end_one(hs[0], s) : end_batch(hs, n, s);
   if (st != DFB_OK) return st;
   for (int i = 0; i < n; ++i) {

@@ -153,3 +153,29 @@ def test_run_frames_with_prepared_sets_equals_individual_frames():
     finally:
         for s in sets:
             D.dfb_tileset_destroy(s)
+
+
+def test_end_frame_inside_a_stream_capture_is_refused():
+    """Capturing dfb_end_frame would replay stale records; the call is
+    refused with STATE and the frame stays open for an ordinary end."""
+    import torch
+    sc = scenes.scene_single_frame_256(seed=2)
+    fb = GpuFrameBuffer(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH)
+    fb.begin(0)
+    fb.submit_pool(sc.tile_ids, sc.keys, sc.rgba, sc.depth)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    code = None
+    with torch.cuda.graph(g, stream=s):
+        x = torch.zeros(4, device="cuda")
+        x += 1                                        # the graph is not empty
+        try:
+            D.dfb_end_frame(fb.h, s)
+        except D.DfbError as e:
+            code = e.code
+    assert code == D.DFB_ERR_STATE
+    fb.end()
+    want = o.composite_frame(sc.W, sc.H, sc.T, o.BLEND_DEPTH, sc.tile_ids, sc.keys,
+                             sc.rgba.astype(np.float64), sc.depth)
+    assert np.max(np.abs(fb.color() - want)) <= TOL
