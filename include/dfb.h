@@ -247,9 +247,9 @@ DFB_API int dfb_submit_tileset(dfb_handle h, dfb_tileset s);
    may be NULL = no accumulation), submit sets[i], then end all frames with
    one batched launch on `stream` (dfb_end_frames).  Everything is validated
    before any frame is begun: handles distinct and not inside a frame, sets
-   matching their handles, one dtype.  If the launch itself fails (OOM, CUDA)
-   the frames stay open, as after a failed dfb_end_frames.  Errors:
-   INVALID_ARG, STATE, OOM, CUDA. */
+   matching their handles, one dtype, a stream that is not being captured.
+   If the launch itself fails (OOM, CUDA) the frames stay open, as after a
+   failed dfb_end_frames.  Errors: INVALID_ARG, STATE, OOM, CUDA. */
 DFB_API int dfb_run_frames(const dfb_handle* hs, const dfb_tileset* sets, const int* accumulate,
                            int n, void* stream);
 

@@ -1781,6 +1781,11 @@ int dfb_run_frames(const dfb_handle* hs, const dfb_tileset* sets, const int* acc
     if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
       return DFB_ERR_INVALID_ARG;
   }
+  {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;  // as in dfb_end_frames
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) cudaGetLastError();
+    else if (cap != cudaStreamCaptureStatusNone) return DFB_ERR_STATE;
+  }
   for (int i = 0; i < n; ++i) {
     int st = dfb_begin_frame(hs[i], accumulate ? accumulate[i] : 0);
     if (st == DFB_OK) {
