@@ -296,13 +296,23 @@ def timed(run, steps, warmup, stream, dist=None, sampler=None, read_back=None):
     return ms, tm, clocks, launches
 
 
+def _code_only(text):
+    """C/C++ source without comments and whitespace (what changes the kernel)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return re.sub(r"\s+", "", text)
+
+
 def kernel_source_hash():
+    """Hash of the composite kernel's code (comments and whitespace ignored),
+    which ties a committed ncu summary to the kernel it measured."""
     h = hashlib.sha256()
     for f in ("paper_2305_07083_gb300/csrc/dfb_composite.cu",
               "paper_2305_07083_gb300/csrc/dfb_device.cuh",
               "paper_2305_07083_gb300/csrc/dfb_internal.h"):
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

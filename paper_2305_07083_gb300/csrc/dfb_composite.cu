@@ -5,8 +5,10 @@
 // Listing 4 (sort the pixel's fragments by depth -- ties by order key, then
 // submit index -- and blend them front to back with the premultiplied "over"
 // operator, then the generation-0 background of Listing 3), the ordered
-// "list" form of Sec. 4.2 (blend in key order), or depth compositing
-// (Sec. 2.1: the nearest fragment's RGBA).  The epilogue updates the
+// "list" form of Sec. 4.2 (blend in key order), depth compositing (Sec. 2.1:
+// the nearest fragment's RGBA), or the mean of redundantly rendered tiles
+// (Sec. 4.1.1), and an optional pixel operation before the display
+// conversion (Sec. 3.1.2).  The epilogue updates the
 // progressive accumulation and variance tiles of Listing 1 (running sum,
 // Kahan-compensated past a threshold; Welford M2; per-tile variance for
 // Sec. 4.1.1) and writes the RGBA8 display format of Sec. 3.1.
@@ -14,10 +16,10 @@
 // The work is bound by HBM bandwidth (~0.4 flop per byte), so the design goal
 // is to keep enough bytes in flight:
 //   * CTA = G consumer groups of 8 warps (one pixel per thread, 256 pixels =
-//     one work item; the groups take alternate items) + 1 producer warp;
-//     either 1 CTA per SM with G = 2 or 2 CTAs per SM with G = 1.  CTAs are
-//     persistent and walk the work items of all frames of the launch with a
-//     static stride.
+//     one work item; the groups take alternate items) + 1 producer warp, PER
+//     CTAs per SM (FP32: G = 2, PER = 2; narrower formats: G = 1, PER = 3;
+//     the kernel needs 56 registers).  CTAs are persistent and walk the work
+//     items of all frames of the launch with a static stride.
 //   * The producer warp fetches each item's tile block (fragment count,
 //     list offset and sorted records, written by the bucketing) with one bulk
 //     copy kMetaQ items ahead, so locating an item's fragments needs no
@@ -32,9 +34,9 @@
 //     the producer streams into the same ring space; consumers read every
 //     input from shared memory, sort and blend, take the state into
 //     registers and release the ring space before the epilogue.
-//   * Items with more than kStageFragments fragments are streamed from HBM
-//     by the consumers in rounds of a per-pixel sort window (held in ring
-//     space the item reserves).
+//   * Items of tiles with more than kStageFragments fragments get an empty
+//     slot here and are composited afterwards by k_composite_long, which
+//     stages their depth slabs in shared memory and streams their RGBA.
 //   * The epilogue writes one variance partial per warp with plain stores;
 //     a small second kernel sums each tile's partials in a fixed order.
 // Every wait is bounded in time; on expiry the kernel sets an error bit,
