@@ -3,11 +3,12 @@ not allocate GPU memory (for instance a simulation that owns the whole device
 through its own pool, or real-time code that cannot afford the device-wide
 synchronisation a cudaMalloc may cause).
 
-Two calls in a row, through the C ABI, are checked against the handle-based
-path (dfb_create / dfb_submit_tiles / dfb_end_frame), which allocates its own
+Calls in a row, through the C ABI, are checked against the handle-based path
+(dfb_create / dfb_submit_tiles / dfb_end_frame), which allocates its own
 buffers.  The second call is smaller than the first, so leftovers of the first
-call in the shared scratch array would show up as wrong pixels.  This file is
-collected last on purpose."""
+call in the shared scratch array would show up as wrong pixels; the last two
+have tiles with more than 16 fragments.  This file is collected last on
+purpose."""
 
 import numpy as np
 import pytest
@@ -55,6 +56,13 @@ def test_two_calls_in_a_row_match_the_handle_path():
     small = scenes.random_scene(200, 136, 16, counts, seed=22, special_depths=True)
     calls.append((small, D.DFB_BLEND_ORDERED, D.DFB_F16, (0.2, 0.4, 0.6, 0.5)))
     assert small.n < big.n
+    # long tiles (more than 16 fragments) go through the long-tile kernel,
+    # whose list also lives in the fixed scratch
+    counts = np.random.default_rng(23).integers(0, 4, 4 * 3)
+    counts[[1, 6, 10]] = [20, 37, 17]
+    longs = scenes.random_scene(256, 192, 64, counts, seed=23, alpha_max=0.3)
+    calls.append((longs, D.DFB_BLEND_DEPTH, D.DFB_F32, (0.1, 0.2, 0.3, 1.0)))
+    calls.append((longs, D.DFB_AVERAGE, D.DFB_BF16, (0.0, 0.0, 0.0, 0.0)))
     for sc, mode, dtype, bg in calls:
         stored, scales = scenes.store_rgba(sc.rgba, dtype)
         want_c, want_8 = handle_path(sc, mode, dtype, stored, scales, bg)
