@@ -32,7 +32,8 @@
  *   - Ownership: the caller owns every pointer it passes.  A device pointer
  *     given to a submit call is borrowed until the work of the dfb_end_frame
  *     call that consumes it has finished on its stream.  A host pointer is
- *     copied before the submit call returns.  The handle owns the resident
+ *     copied before the submit call returns, unless it is submitted as
+ *     DFB_PTR_HOST_BORROWED: then it is borrowed like a device pointer.  The handle owns the resident
  *     framebuffers (colour, accumulation, variance, RGBA8).
  *   - Threads: a handle must not be used by two threads at once.
  */
@@ -112,7 +113,13 @@ enum dfb_status {
 /* Where the pointers of a bulk submit live. */
 #define DFB_PTR_AUTO 0   /* ask the CUDA runtime for each pointer */
 #define DFB_PTR_DEVICE 1 /* all device (or managed) memory         */
-#define DFB_PTR_HOST 2   /* all host memory (pageable or pinned)   */
+#define DFB_PTR_HOST 2   /* all host memory (pageable or pinned), copied to the
+                            device before the submit call returns           */
+#define DFB_PTR_HOST_BORROWED 3 /* host memory copied to the device
+                            asynchronously: like a device pointer, it is
+                            borrowed until the work of the dfb_end_frame call
+                            that consumes it has finished (dfb_sync, or the
+                            stream), and must not change before            */
 
 typedef struct dfb_config {
   int width;         /* frame width in pixels, >= 1                          */

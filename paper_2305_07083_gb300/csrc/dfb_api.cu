@@ -439,7 +439,7 @@ int append_records(dfb_ctx* h, int n, const dfb_tile_desc* tiles, int where) {
   for (int i = 0; i < n; ++i) {
     bool devR, devD;
     if (where == DFB_PTR_DEVICE) devR = devD = true;
-    else if (where == DFB_PTR_HOST) devR = devD = false;
+    else if (where == DFB_PTR_HOST || where == DFB_PTR_HOST_BORROWED) devR = devD = false;
     else {
       devR = is_device_ptr(tiles[i].rgba);
       devD = is_device_ptr(tiles[i].depth);
@@ -482,7 +482,9 @@ int append_records(dfb_ctx* h, int n, const dfb_tile_desc* tiles, int where) {
       }
     }
     cudaError_t e = cudaEventRecord(h->copyDone, h->copyStream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(h->copyDone);  // sources reusable now
+    // DFB_PTR_HOST: the sources are reusable when the call returns;
+    // DFB_PTR_HOST_BORROWED: the caller keeps them until the frame is done
+    if (e == cudaSuccess && where != DFB_PTR_HOST_BORROWED) e = cudaEventSynchronize(h->copyDone);
     if (e != cudaSuccess) return cuda_status(e);
     h->hostCopies = true;
   }
@@ -820,7 +822,7 @@ int dfb_submit_tiles(dfb_handle h, int n, const int* tile_ids, const float* orde
   if (!h || n < 0) return DFB_ERR_INVALID_ARG;
   if (!h->inFrame) return DFB_ERR_STATE;
   if (n == 0) return DFB_OK;
-  if (where < DFB_PTR_AUTO || where > DFB_PTR_HOST) return DFB_ERR_INVALID_ARG;
+  if (where < DFB_PTR_AUTO || where > DFB_PTR_HOST_BORROWED) return DFB_ERR_INVALID_ARG;
   // validate everything first: nothing is submitted if an entry is bad
   const int st = validate_arrays(h, n, tile_ids, order_keys, rgba, depth, scales);
   if (st != DFB_OK) return st;
@@ -846,7 +848,7 @@ int dfb_submit_tiles_ex(dfb_handle h, int n, const dfb_tile_desc* tiles, int whe
   if (!h || n < 0) return DFB_ERR_INVALID_ARG;
   if (!h->inFrame) return DFB_ERR_STATE;
   if (n == 0) return DFB_OK;
-  if (!tiles || where < DFB_PTR_AUTO || where > DFB_PTR_HOST) return DFB_ERR_INVALID_ARG;
+  if (!tiles || where < DFB_PTR_AUTO || where > DFB_PTR_HOST_BORROWED) return DFB_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {
     const int st = validate_tile(h, &tiles[i]);
     if (st != DFB_OK) return st;

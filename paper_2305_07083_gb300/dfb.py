@@ -29,7 +29,7 @@ DFB_ERR_OOM, DFB_ERR_TIMEOUT, DFB_ERR_CUDA, DFB_ERR_CAPACITY = -5, -6, -7, -8
 DFB_ERR_CHECK = -9
 DFB_FLAG_ACCUMULATE, DFB_FLAG_WRITE_COLOR, DFB_FLAG_PACK_RGBA8, DFB_FLAG_DEFER_ALLOC = 1, 2, 4, 8
 DFB_FLAGS_DEFAULT = DFB_FLAG_ACCUMULATE | DFB_FLAG_WRITE_COLOR | DFB_FLAG_PACK_RGBA8
-DFB_PTR_AUTO, DFB_PTR_DEVICE, DFB_PTR_HOST = 0, 1, 2
+DFB_PTR_AUTO, DFB_PTR_DEVICE, DFB_PTR_HOST, DFB_PTR_HOST_BORROWED = 0, 1, 2, 3
 
 ELEMENT_BYTES = {DFB_F32: 4, DFB_F16: 2, DFB_BF16: 2, DFB_FP8E4M3: 1}
 

@@ -12,7 +12,7 @@ from harness import scenes
 from oracle import dfb_oracle as o
 from paper_2305_07083_gb300 import dfb as D
 
-from tests.gpu_helpers import GpuFrameBuffer, composite_once
+from tests.gpu_helpers import GpuFrameBuffer, composite_once, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -127,6 +127,34 @@ def test_host_pointers_equal_device_pointers():
     a = composite_once(sc, D.DFB_BLEND_DEPTH, where="device").color()
     b = composite_once(sc, D.DFB_BLEND_DEPTH, where="host").color()
     np.testing.assert_array_equal(a, b)
+
+
+def test_borrowed_host_pointers_back_to_back():
+    """DFB_PTR_HOST_BORROWED: host tiles copied asynchronously (the caller
+    keeps them until the frame is done); frames ended back to back without a
+    sync give the same accumulation as device pointers."""
+    sc = scenes.scene_data_parallel(192, 128, 32, (3, 2, 2), seed=14, jitter_sigma=0.05)
+    frames = [np.ascontiguousarray(sc.frame_rgba(f)) for f in range(4)]
+    depth = np.ascontiguousarray(sc.depth, np.float32)
+    rb, db = sc.T * sc.T * 16, sc.T * sc.T * 4
+    outs = []
+    for where in (D.DFB_PTR_HOST_BORROWED, D.DFB_PTR_DEVICE):
+        fb = GpuFrameBuffer(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH)
+        bufs = frames if where != D.DFB_PTR_DEVICE else [to_dev(f) for f in frames]
+        dep = depth if where != D.DFB_PTR_DEVICE else to_dev(depth)
+        if where == D.DFB_PTR_DEVICE:
+            import torch
+            torch.cuda.synchronize()
+        for f, buf in enumerate(bufs):
+            fb.begin(accumulate=f > 0)
+            D.dfb_submit_tiles(fb.h, sc.tile_ids, sc.keys, D.pool_pointers(buf, sc.n, rb),
+                               D.pool_pointers(dep, sc.n, db), None, where)
+            fb.end()
+        D.dfb_sync(fb.h)
+        outs.append((fb.accum(), fb.rgba8()))
+        fb.close()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
 
 
 def test_repeatable_and_order_independent():
