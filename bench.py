@@ -697,6 +697,8 @@ def main():
             "value": world * fpx_frame * N_FRAMES * args.steps / (ms16 / 1e3),
             "ms_per_step": ms16 / args.steps, "speedup_vs_f32": ms / ms16,
             "roofline": {"achieved": a16, "frac": a16 / hbm_peak, "avg_launch_ms": c16,
+                         "traffic": ncu_traffic("composite_f16_2048.md"),
+                         "kernel": "k_composite<BLEND_DEPTH,F16>",
                          "algorithmic_bytes_per_launch": ab16}}}
         r16.close()
         del f16
