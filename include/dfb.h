@@ -69,12 +69,14 @@ enum dfb_mode {
 };
 
 /* Pixel operation run on the finished value just before the RGBA8 display
-   conversion (Sec. 3.1.2; the paper leaves the formula to the user).  Both act
+   conversion (Sec. 3.1.2; the paper leaves the formula to the user).  All act
    on premultiplied RGB with alpha unchanged; e is the operation's exposure. */
 enum dfb_pixel_op {
   DFB_PIXELOP_NONE = 0,
   DFB_PIXELOP_EXPOSURE = 1,  /* rgb -> e * rgb                                */
-  DFB_PIXELOP_REINHARD = 2   /* rgb -> e*rgb / (1 + e*rgb), per channel        */
+  DFB_PIXELOP_REINHARD = 2,  /* rgb -> e*rgb / (1 + e*rgb), per channel        */
+  DFB_PIXELOP_CURVE = 3      /* rgb -> the user's tone curve of each channel
+                                at e*rgb (dfb_set_pixel_curve)                */
 };
 
 /* Storage type of the submitted fragment RGBA (depth is always FP32). */
@@ -175,8 +177,25 @@ DFB_API int dfb_set_background(dfb_handle h, float r, float g, float b, float a)
 /* Pixel operation of the RGBA8 output (enum dfb_pixel_op) with its exposure,
    from the next dfb_end_frame on.  The colour, accumulation and variance
    buffers are not affected.  Errors: INVALID_ARG (unknown op, exposure not
-   finite or negative). */
+   finite or negative), STATE (DFB_PIXELOP_CURVE before any
+   dfb_set_pixel_curve on this handle). */
 DFB_API int dfb_set_pixel_op(dfb_handle h, int op, float exposure);
+
+/* Load a user tone curve per colour channel and select DFB_PIXELOP_CURVE
+   (the exposure set last is kept): the user-supplied pixel operation of
+   Sec. 3.1.2, fused into the RGBA8 pack.
+   curves: host array of 3*n floats, channel-major (n samples of R, then G,
+   then B); sample j of a channel is the curve's value at
+   x_j = x_max * j / (n - 1).  The curve is piecewise linear between samples;
+   the input x = e * rgb is clamped to [0, x_max] first (NaN reads as 0).
+   The result is a linear value that the sRGB pack then encodes.
+   The samples are copied into a device buffer of the handle (4096 samples
+   per channel at most) before the call returns; the call first waits for the
+   handle's frames in flight.  A CUDA graph captured from this handle reads
+   that buffer when it runs, with the n and x_max of its capture.
+   Errors: INVALID_ARG (null curves, n outside [2, 4096], x_max not finite or
+   <= 0, a sample not finite), OOM, CUDA. */
+DFB_API int dfb_set_pixel_curve(dfb_handle h, const float* curves, int n, float x_max);
 
 /* Begin a frame (Sec. 3.1).  accumulate = 0 restarts the progressive
    accumulation with this frame; non-zero adds this frame to it.

@@ -43,7 +43,10 @@ to the code; the list of readings is:
   display conversion; the paper leaves their formula to the user.  Two
   standard operators are provided, on premultiplied RGB with alpha
   unchanged: an exposure scale ``e * rgb`` and Reinhard's global operator
-  per channel, ``e*rgb / (1 + e*rgb)``.
+  per channel, ``e*rgb / (1 + e*rgb)``.  A third is the user's own tone
+  curve per channel, given as n samples over [0, x_max] (sample j at
+  x_max * j / (n - 1)) and read piecewise linearly at ``e * rgb`` clamped to
+  [0, x_max], NaN read as 0.
 """
 
 from __future__ import annotations
@@ -59,7 +62,7 @@ BLEND_ORDERED = 1    # blend in order-key order: the "list" tree of Sec. 4.2
 ZCOMPOSITE = 2       # nearest fragment wins (Sec. 2.1, depth compositing)
 AVERAGE = 3          # mean of redundantly rendered tiles (Sec. 4.1.1)
 
-PIXELOP_NONE, PIXELOP_EXPOSURE, PIXELOP_REINHARD = 0, 1, 2
+PIXELOP_NONE, PIXELOP_EXPOSURE, PIXELOP_REINHARD, PIXELOP_CURVE = 0, 1, 2, 3
 
 F32, F16, BF16, FP8E4M3 = 0, 1, 2, 3
 
@@ -353,9 +356,24 @@ def pack_rgba8(img):
     return b[..., 0] | (b[..., 1] << 8) | (b[..., 2] << 16) | (b[..., 3] << 24)
 
 
-def pixel_op(img, op: int, exposure: float = 1.0):
+def tone_curve(x, samples, x_max: float):
+    """A user tone curve (Sec. 3.1.2 leaves the operation to the user): the
+    polyline through (x_max * j / (n - 1), samples[j]), j = 0 .. n-1, at x
+    clamped to [0, x_max]; NaN reads as 0."""
+    t = np.asarray(samples, dtype=np.float64)
+    n = t.shape[0]
+    x = np.asarray(x, dtype=np.float64)
+    x = np.where(np.isnan(x), 0.0, x)
+    x = np.minimum(np.maximum(x, 0.0), x_max)
+    f = x * ((n - 1) / x_max)               # position in sample steps
+    j = np.minimum(np.floor(f).astype(np.int64), n - 2)
+    return t[j] + (f - j) * (t[j + 1] - t[j])
+
+
+def pixel_op(img, op: int, exposure: float = 1.0, curves=None, x_max: float = 1.0):
     """A pixel operation on finished pixels (Sec. 3.1.2), before the display
-    conversion: RGB transformed, alpha unchanged."""
+    conversion: RGB transformed, alpha unchanged.  ``curves`` (3 x n
+    samples, one row per channel) and ``x_max`` define PIXELOP_CURVE."""
     img = np.array(img, dtype=np.float64)
     if op == PIXELOP_NONE:
         return img
@@ -364,6 +382,9 @@ def pixel_op(img, op: int, exposure: float = 1.0):
         img[..., :3] = x
     elif op == PIXELOP_REINHARD:
         img[..., :3] = x / (1.0 + x)
+    elif op == PIXELOP_CURVE:
+        for c in range(3):
+            img[..., c] = tone_curve(x[..., c], curves[c], x_max)
     else:
         raise ValueError("unknown pixel operation")
     return img

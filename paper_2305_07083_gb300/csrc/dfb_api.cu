@@ -126,6 +126,9 @@ struct dfb_ctx {
   float bg[4] = {0, 0, 0, 0};
   int pixelOp = DFB_PIXELOP_NONE;
   float exposure = 1.0f;
+  float* curve = nullptr;  // 3 * kMaxCurve floats once a tone curve is loaded
+  int curveN = 0;
+  float curveXMax = 1.0f;
   std::vector<FragRec> recs;
   std::vector<int> declared;             // gen-0 children per tile, -1 = none
   std::vector<int> recvGen1, childGen1;  // generation-1 arrivals per tile
@@ -552,6 +555,10 @@ void fill_frame_args(const dfb_ctx* h, FrameArgs& a, int tileBase, const FragRec
   a.bgA = h->bg[3];
   a.pixelOp = h->pixelOp;
   a.exposure = h->exposure;
+  a.curve = h->curve;
+  a.curveN = h->curveN;
+  a.curveXMax = h->curveXMax;
+  a.curveScale = h->curveN > 1 ? (float)(h->curveN - 1) / h->curveXMax : 0.0f;
   a.srecs = srecs;
   a.blocks = blocks;
   a.color = h->color;
@@ -743,6 +750,7 @@ int dfb_destroy(dfb_handle h) {
   if (!h) return DFB_OK;
   if (h->allocated && h->lastStreamSet) cudaEventSynchronize(h->frameDone);
   free_device(h);
+  if (h->curve) cudaFree(h->curve);
   delete h;
   return DFB_OK;
 }
@@ -756,10 +764,39 @@ int dfb_set_background(dfb_handle h, float r, float g, float b, float a) {
 
 int dfb_set_pixel_op(dfb_handle h, int op, float exposure) {
   if (!h) return DFB_ERR_INVALID_ARG;
-  if (op < DFB_PIXELOP_NONE || op > DFB_PIXELOP_REINHARD) return DFB_ERR_INVALID_ARG;
+  if (op < DFB_PIXELOP_NONE || op > DFB_PIXELOP_CURVE) return DFB_ERR_INVALID_ARG;
   if (!isfinite(exposure) || exposure < 0.0f) return DFB_ERR_INVALID_ARG;
+  if (op == DFB_PIXELOP_CURVE && !h->curve) return DFB_ERR_STATE;
   h->pixelOp = op;
   h->exposure = exposure;
+  return DFB_OK;
+}
+
+int dfb_set_pixel_curve(dfb_handle h, const float* curves, int n, float x_max) {
+  if (!h || !curves || n < 2 || n > dfb::kMaxCurve) return DFB_ERR_INVALID_ARG;
+  if (!isfinite(x_max) || x_max <= 0.0f) return DFB_ERR_INVALID_ARG;
+  for (int i = 0; i < 3 * n; ++i)
+    if (!isfinite(curves[i])) return DFB_ERR_INVALID_ARG;
+  cudaError_t e = cudaSuccess;
+  if (!h->curve) {
+    e = cudaMalloc(&h->curve, sizeof(float) * 3 * (size_t)dfb::kMaxCurve);
+    if (e != cudaSuccess) {
+      h->curve = nullptr;
+      return e == cudaErrorMemoryAllocation ? DFB_ERR_OOM : DFB_ERR_CUDA;
+    }
+  } else if (h->allocated && h->lastStreamSet) {
+    // frames in flight may still read the previous samples
+    e = cudaEventSynchronize(h->frameDone);
+    if (e != cudaSuccess) return DFB_ERR_CUDA;
+  }
+  // the legacy stream, waited for: the DMA of a pageable source has landed
+  // when the call returns
+  e = cudaMemcpyAsync(h->curve, curves, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  if (e != cudaSuccess) return DFB_ERR_CUDA;
+  h->curveN = n;
+  h->curveXMax = x_max;
+  h->pixelOp = DFB_PIXELOP_CURVE;
   return DFB_OK;
 }
 

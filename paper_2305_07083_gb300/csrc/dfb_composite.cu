@@ -643,7 +643,7 @@ __device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& 
       out = mean;
     }
     if ((flags & DFB_FLAG_PACK_RGBA8) && pixOk)
-      A->rgba8[w.pix] = pack_rgba8(pixel_op(out, A->pixelOp, A->exposure), tb);
+      A->rgba8[w.pix] = pack_rgba8(pixel_op(out, A), tb);
   }
   if (acc && warp * 32 < w.P) {
     // one partial per warp of 32 pixels, summed per tile by k_tile_variance

@@ -105,16 +105,35 @@ __device__ __forceinline__ void over(float4 f, float& c0, float& c1, float& c2, 
   al = fmaf(t, f.w, al);
 }
 
-// Pixel operation before the display conversion (enum dfb_pixel_op): RGB
-// transformed, alpha unchanged.
-__device__ __forceinline__ float4 pixel_op(float4 v, int op, float e) {
-  if (op == DFB_PIXELOP_EXPOSURE) return make_float4(e * v.x, e * v.y, e * v.z, v.w);
-  if (op == DFB_PIXELOP_REINHARD) {
-    const float x = e * v.x, y = e * v.y, z = e * v.z;
+// Value of a user tone curve at x: piecewise linear between the samples t[j]
+// at x_j = xMax * j / (n - 1), with x clamped to [0, xMax] (NaN -> 0) and
+// scale = (n - 1) / xMax.
+__device__ __forceinline__ float curve_at(const float* __restrict__ t, int n, float xMax,
+                                          float scale, float x) {
+  x = fminf(fmaxf(x, 0.0f), xMax);  // fmaxf(NaN, 0) = 0
+  const float f = x * scale;
+  const int i = min((int)f, n - 2);
+  const float fr = f - (float)i;
+  const float a = __ldg(t + i), b = __ldg(t + i + 1);
+  return fmaf(fr, b - a, a);
+}
+
+// Pixel operation before the display conversion (enum dfb_pixel_op) of the
+// frame's settings: RGB transformed, alpha unchanged.
+__device__ __forceinline__ float4 pixel_op(float4 v, const FrameArgs* A) {
+  const int op = A->pixelOp;
+  if (op == DFB_PIXELOP_NONE) return v;
+  const float e = A->exposure;
+  const float x = e * v.x, y = e * v.y, z = e * v.z;
+  if (op == DFB_PIXELOP_EXPOSURE) return make_float4(x, y, z, v.w);
+  if (op == DFB_PIXELOP_REINHARD)
     return make_float4(__fdiv_rn(x, 1.0f + x), __fdiv_rn(y, 1.0f + y), __fdiv_rn(z, 1.0f + z),
                        v.w);
-  }
-  return v;
+  const int n = A->curveN;
+  const float xm = A->curveXMax, sc = A->curveScale;
+  const float* t = A->curve;
+  return make_float4(curve_at(t, n, xm, sc, x), curve_at(t + n, n, xm, sc, y),
+                     curve_at(t + 2 * n, n, xm, sc, z), v.w);
 }
 
 // sRGB code of a linear value: the number of code boundaries <= x, after

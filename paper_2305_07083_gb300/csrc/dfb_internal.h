@@ -78,6 +78,9 @@ struct FrameArgs {
   float bgR, bgG, bgB, bgA;    // premultiplied background colour and coverage
   int pixelOp;                 // enum dfb_pixel_op applied before the RGBA8 pack
   float exposure;
+  int curveN;                  // DFB_PIXELOP_CURVE: samples per channel (>= 2)
+  float curveXMax;             // DFB_PIXELOP_CURVE: input range [0, curveXMax]
+  float curveScale;            // (curveN - 1) / curveXMax
   const FragRec* srecs;        // records grouped by global tile, (key, index) order
   const TileBlock* blocks;     // per global tile
   float4* color;               // row-major image
@@ -87,7 +90,11 @@ struct FrameArgs {
   uint32_t* rgba8;
   float* tileVar;
   float* varPartial;           // [nTiles * slots] per-warp partial sums
+  const float* curve;          // DFB_PIXELOP_CURVE: 3 * curveN samples, channel-major
 };
+
+// Samples per channel of a user tone curve (DFB_PIXELOP_CURVE), at most.
+constexpr int kMaxCurve = 4096;
 
 // Launch shape of the composite kernel, chosen by the autotuner.
 struct TuneParams {

@@ -230,6 +230,10 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   a.bgB = bg[2] * bg[3];
   a.bgA = bg[3];
   a.pixelOp = DFB_PIXELOP_NONE;
+  a.curve = nullptr;
+  a.curveN = 0;
+  a.curveXMax = 1.0f;
+  a.curveScale = 0.0f;
   a.exposure = 1.0f;
   a.srecs = srecs;
   a.blocks = blocks;

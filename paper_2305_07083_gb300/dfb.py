@@ -21,7 +21,7 @@ LIB = LIB_CHECKED if os.environ.get("DFB_CHECKED") == "1" else _LIB_NORMAL
 
 # enums (include/dfb.h)
 DFB_BLEND_DEPTH, DFB_BLEND_ORDERED, DFB_ZCOMPOSITE, DFB_AVERAGE = 0, 1, 2, 3
-DFB_PIXELOP_NONE, DFB_PIXELOP_EXPOSURE, DFB_PIXELOP_REINHARD = 0, 1, 2
+DFB_PIXELOP_NONE, DFB_PIXELOP_EXPOSURE, DFB_PIXELOP_REINHARD, DFB_PIXELOP_CURVE = 0, 1, 2, 3
 DFB_F32, DFB_F16, DFB_BF16, DFB_FP8E4M3 = 0, 1, 2, 3
 DFB_OK = 0
 DFB_ERR_INVALID_ARG, DFB_ERR_TILE_RANGE, DFB_ERR_STATE, DFB_ERR_INCOMPLETE = -1, -2, -3, -4
@@ -85,6 +85,7 @@ def lib():
         "dfb_destroy": (C.c_int, [H]),
         "dfb_set_background": (C.c_int, [H, C.c_float, C.c_float, C.c_float, C.c_float]),
         "dfb_set_pixel_op": (C.c_int, [H, C.c_int, C.c_float]),
+        "dfb_set_pixel_curve": (C.c_int, [H, P, C.c_int, C.c_float]),
         "dfb_begin_frame": (C.c_int, [H, C.c_int]),
         "dfb_set_tile_children": (C.c_int, [H, C.c_int, C.c_int]),
         "dfb_submit_tile": (C.c_int, [H, C.c_int, C.c_float, P, P]),
@@ -191,6 +192,15 @@ def dfb_set_background(h, r, g, b, a):
 
 def dfb_set_pixel_op(h, op, exposure=1.0):
     return _check(lib().dfb_set_pixel_op(h, int(op), float(exposure)), "dfb_set_pixel_op")
+
+
+def dfb_set_pixel_curve(h, curves, x_max=1.0):
+    """curves: 3 x n samples (one row per channel), copied to the device."""
+    c = np.ascontiguousarray(curves, dtype=np.float32)
+    if c.ndim != 2 or c.shape[0] != 3:
+        raise ValueError("curves must have shape (3, n)")
+    return _check(lib().dfb_set_pixel_curve(h, c.ctypes.data, int(c.shape[1]), float(x_max)),
+                  "dfb_set_pixel_curve")
 
 
 def dfb_begin_frame(h, accumulate=0):

@@ -175,9 +175,13 @@ class Server:
         far the host runs ahead (a batch waits for the previous batch before
         reusing its staging buffers).
 
+        With `keep_results`, a finished job's frame is copied out of the
+        pooled pinned buffer into its own array (`job.result`); otherwise the
+        client takes it in place and the buffer goes back to the pool.
+
         With `trace`, the stats also split the host time by phase (admit,
-        prepare, launch, retire) and sum the device time of every batched
-        launch (CUDA events around each step on the stream).
+        deliver, prepare, launch, retire) and sum the device time of every
+        batched launch (CUDA events around each step on the stream).
         """
         import torch
         stream = self.stream if self.stream is not None else torch.cuda.current_stream()
@@ -185,7 +189,7 @@ class Server:
         queue, active, inflight = [], [], []
         used = 0
         st = ServerStats()
-        phase = {"admit": 0.0, "prepare": 0.0, "launch": 0.0, "retire": 0.0}
+        phase = {"admit": 0.0, "deliver": 0.0, "prepare": 0.0, "launch": 0.0, "retire": 0.0}
         step_events = []
         t0 = time.perf_counter()
 
@@ -225,15 +229,17 @@ class Server:
                 active.append(job)
             st.peak_active = max(st.peak_active, len(active))
             st.peak_footprint = max(st.peak_footprint, used)
+            tm = time.perf_counter()
             observe(False)
+            tb = time.perf_counter()
+            phase["admit"] += tm - ta
+            phase["deliver"] += tb - tm
             if not active:
                 if inflight:
                     observe(True)
                 elif pending:
                     time.sleep(max(0.0, min(pending[0].arrival - now, 0.001)))
                 continue
-            tb = time.perf_counter()
-            phase["admit"] += tb - ta
             # one step: the next frame of every active job in one launch
             fpx = 0
             sets, acc = [], []

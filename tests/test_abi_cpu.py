@@ -353,12 +353,47 @@ def test_pixel_op_validation():
     for op, e in ((D.DFB_PIXELOP_NONE, 1.0), (D.DFB_PIXELOP_EXPOSURE, 0.0),
                   (D.DFB_PIXELOP_REINHARD, 4.0)):
         D.dfb_set_pixel_op(h, op, e)
-    for op, e in ((3, 1.0), (-1, 1.0), (D.DFB_PIXELOP_EXPOSURE, -1.0),
-                  (D.DFB_PIXELOP_REINHARD, math.nan), (D.DFB_PIXELOP_EXPOSURE, math.inf)):
+    for op, e in ((4, 1.0), (-1, 1.0), (D.DFB_PIXELOP_EXPOSURE, -1.0),
+                  (D.DFB_PIXELOP_REINHARD, math.nan), (D.DFB_PIXELOP_EXPOSURE, math.inf),
+                  (D.DFB_PIXELOP_CURVE, -2.0)):
         with pytest.raises(D.DfbError) as e_:
             D.dfb_set_pixel_op(h, op, e)
         assert e_.value.code == D.DFB_ERR_INVALID_ARG
+    # the curve operation needs a curve loaded first
+    with pytest.raises(D.DfbError) as e_:
+        D.dfb_set_pixel_op(h, D.DFB_PIXELOP_CURVE, 1.0)
+    assert e_.value.code == D.DFB_ERR_STATE
     D.dfb_destroy(h)
     a = D.dfb_create_ex(64, 64, 16, D.DFB_AVERAGE, D.DFB_F32,
                         D.DFB_FLAGS_DEFAULT | D.DFB_FLAG_DEFER_ALLOC)
     D.dfb_destroy(a)
+
+
+def test_pixel_curve_validation():
+    """Argument checks of dfb_set_pixel_curve, all made before any CUDA call."""
+    h = _deferred()
+    good = np.linspace(0.0, 1.0, 8, dtype=np.float32)
+    bad_cases = [
+        (np.stack([good] * 3)[:, :1], 1.0),                       # n = 1
+        (np.zeros((3, 4097), np.float32), 1.0),                   # n > 4096
+        (np.stack([good] * 3), 0.0),                              # x_max = 0
+        (np.stack([good] * 3), -1.0),
+        (np.stack([good] * 3), math.nan),
+        (np.stack([good] * 3), math.inf),
+        (np.stack([good, good, np.where(good > 0.5, np.nan, good)]), 1.0),   # a NaN sample
+        (np.stack([good, np.full(8, np.inf, np.float32), good]), 1.0),
+    ]
+    for curves, xm in bad_cases:
+        with pytest.raises(D.DfbError) as e_:
+            D.dfb_set_pixel_curve(h, curves, xm)
+        assert e_.value.code == D.DFB_ERR_INVALID_ARG
+    assert D.lib().dfb_set_pixel_curve(h, None, 8, 1.0) == D.DFB_ERR_INVALID_ARG
+    assert D.lib().dfb_set_pixel_curve(None, np.stack([good] * 3).ctypes.data, 8,
+                                       1.0) == D.DFB_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        D.dfb_set_pixel_curve(h, good, 1.0)                        # not 3 rows
+    # nothing was loaded, so the operation still cannot be selected
+    with pytest.raises(D.DfbError) as e_:
+        D.dfb_set_pixel_op(h, D.DFB_PIXELOP_CURVE, 1.0)
+    assert e_.value.code == D.DFB_ERR_STATE
+    D.dfb_destroy(h)

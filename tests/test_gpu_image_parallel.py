@@ -131,3 +131,61 @@ def test_pixel_ops_before_the_pack(op, e):
     want8 = o.pack_rgba8(o.pixel_op(o.accumulate(imgs), op, e))
     d8 = np.abs(o.unpack_rgba8(fb.rgba8()) - o.unpack_rgba8(want8))
     assert d8.max() <= 1
+
+
+def _curves(n, x_max, seed):
+    """Three seeded tone curves: increasing, decreasing and wiggly, in [0, 1]."""
+    rng = np.random.default_rng(seed)
+    up = np.cumsum(rng.random(n)); up = (up - up[0]) / (up[-1] - up[0])
+    down = 1.0 - up[::-1]
+    wig = 0.5 + 0.4 * np.sin(np.linspace(0.0, 7.0, n)) * rng.random(n)
+    return np.stack([up, down, wig]).astype(np.float32)
+
+
+def test_user_tone_curve_before_the_pack():
+    """DFB_PIXELOP_CURVE: the user's curves, swapped between frames (with a
+    different sample count), and a switch back to a built-in operation."""
+    sc = scenes.scene_data_parallel(192, 128, 32, (3, 3, 3), seed=11, jitter_sigma=0.05)
+    plain = GpuFrameBuffer(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH)
+    fb = GpuFrameBuffer(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH)
+    settings = [(17, 1.5, 1.3), (5, 0.75, 1.0), (2, 1.0, 2.0), (4096, 3.0, 0.8), (None, None, 2.5)]
+    imgs = []
+    for f, (n, xm, e) in enumerate(settings):
+        if n is None:
+            D.dfb_set_pixel_op(fb.h, D.DFB_PIXELOP_REINHARD, e)
+        else:
+            curves = _curves(n, xm, 60 + f)
+            D.dfb_set_pixel_op(fb.h, D.DFB_PIXELOP_EXPOSURE, e)
+            D.dfb_set_pixel_curve(fb.h, curves, xm)          # selects the curve, keeps e
+        rgba = sc.frame_rgba(f)
+        for b in (plain, fb):
+            b.begin(accumulate=f > 0)
+            b.submit_pool(sc.tile_ids, sc.keys, rgba, sc.depth)
+            b.end()
+        imgs.append(o.composite_frame(sc.W, sc.H, sc.T, o.BLEND_DEPTH, sc.tile_ids, sc.keys,
+                                      rgba.astype(np.float64), sc.depth))
+        mean = o.accumulate(imgs)
+        if n is None:
+            want = o.pixel_op(mean, o.PIXELOP_REINHARD, e)
+        else:
+            want = o.pixel_op(mean, o.PIXELOP_CURVE, e, curves.astype(np.float64), xm)
+        d8 = np.abs(o.unpack_rgba8(fb.rgba8()) - o.unpack_rgba8(o.pack_rgba8(want)))
+        assert d8.max() <= 1, (f, n)
+        assert np.mean(d8 == 0) > 0.99, (f, n)
+        np.testing.assert_array_equal(fb.accum(), plain.accum())
+    # with a curve loaded the operation can be selected again
+    D.dfb_set_pixel_op(fb.h, D.DFB_PIXELOP_CURVE, 1.0)
+
+
+def test_identity_curve_matches_no_operation():
+    sc = scenes.scene_data_parallel(128, 128, 32, (2, 2, 2), seed=12, jitter_sigma=0.05)
+    plain = GpuFrameBuffer(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH)
+    fb = GpuFrameBuffer(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH)
+    D.dfb_set_pixel_curve(fb.h, np.stack([np.linspace(0.0, 1.0, 257)] * 3), 1.0)
+    for b in (plain, fb):
+        b.begin(accumulate=False)
+        b.submit_pool(sc.tile_ids, sc.keys, sc.frame_rgba(0), sc.depth)
+        b.end()
+    d8 = np.abs(o.unpack_rgba8(fb.rgba8()) - o.unpack_rgba8(plain.rgba8()))
+    assert d8.max() <= 1
+    assert np.mean(d8 == 0) > 0.999

@@ -63,6 +63,41 @@ def _exposure_on_alpha(img, op, exposure=1.0):
     return _real_pixel_op(img, op, exposure)
 
 
+_real_tone_curve = o.tone_curve
+
+
+def _curve_nearest_sample(x, samples, x_max):
+    t = np.asarray(samples, dtype=np.float64)
+    n = t.shape[0]
+    x = np.minimum(np.maximum(np.nan_to_num(np.asarray(x, float)), 0.0), x_max)
+    return t[np.rint(x * (n - 1) / x_max).astype(np.int64)]
+
+
+def _curve_no_clamp_above(x, samples, x_max):
+    x = np.asarray(x, dtype=np.float64)
+    inside = _real_tone_curve(x, samples, x_max)
+    t = np.asarray(samples, dtype=np.float64)
+    n = t.shape[0]
+    slope = (t[-1] - t[-2]) * (n - 1) / x_max
+    return np.where(x > x_max, t[-1] + (x - x_max) * slope, inside)
+
+
+def _curve_step_count_n(x, samples, x_max):
+    # spaces the samples x_max / n apart instead of x_max / (n - 1)
+    t = np.asarray(samples, dtype=np.float64)
+    n = t.shape[0]
+    return _real_tone_curve(x, t, x_max * (n - 1) / n)
+
+
+def _exposure_after_curve(img, op, exposure=1.0, curves=None, x_max=1.0):
+    if op == o.PIXELOP_CURVE:
+        img = np.array(img, dtype=np.float64)
+        for c in range(3):
+            img[..., c] = exposure * _real_tone_curve(img[..., c], curves[c], x_max)
+        return img
+    return _real_pixel_op(img, op, exposure, curves, x_max)
+
+
 MUTANTS = [
     ("over_front_to_back", _wrong_sign, [pins.test_equal_layers_closed_form]),
     ("over_front_to_back", _back_to_front_formula, [pins.test_golden_hand_derived_pixels]),
@@ -75,6 +110,12 @@ MUTANTS = [
     ("average_tiles", _average_first_tile_only, [pins.test_average_closed_form]),
     ("pixel_op", _reinhard_without_exposure, [pins.test_reinhard_closed_forms]),
     ("pixel_op", _exposure_on_alpha, [pins.test_pixel_op_identities]),
+    ("tone_curve", _curve_nearest_sample, [pins.test_tone_curve_samples_clamp_and_identity,
+                                           pins.test_tone_curve_chord_bound_on_a_parabola]),
+    ("tone_curve", _curve_no_clamp_above, [pins.test_tone_curve_samples_clamp_and_identity]),
+    ("tone_curve", _curve_step_count_n, [pins.test_tone_curve_samples_clamp_and_identity,
+                                         pins.test_tone_curve_chord_bound_on_a_parabola]),
+    ("pixel_op", _exposure_after_curve, [pins.test_pixel_op_curve_per_channel_after_exposure]),
 ]
 
 

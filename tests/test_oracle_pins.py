@@ -453,3 +453,65 @@ def test_reinhard_closed_forms():
     np.testing.assert_array_equal(got[1, :3], [0.5, 0.75, 14.0 / 15.0])
     big = o.pixel_op(np.array([[1e300, 1e300, 1e300, 1.0]]), o.PIXELOP_REINHARD, 1.0)
     np.testing.assert_allclose(big[0, :3], 1.0, rtol=1e-15)
+
+
+# --- user tone curve (Sec. 3.1.2: the pixel operation is the user's) -----------
+def test_tone_curve_samples_clamp_and_identity():
+    # x_max = 2 and n = 9 put the samples at exact multiples of 1/4
+    t = np.array([0.1, 0.7, -0.2, 3.0, 0.5, 0.5, 1.25, 0.0, 2.0])
+    xs = np.arange(9) / 4.0
+    np.testing.assert_array_equal(o.tone_curve(xs, t, 2.0), t)
+    # halfway between two samples: their mean
+    np.testing.assert_allclose(o.tone_curve(xs[:-1] + 0.125, t, 2.0), 0.5 * (t[:-1] + t[1:]),
+                               rtol=0, atol=1e-15)
+    # below 0, NaN -> the first sample; above x_max -> the last
+    got = o.tone_curve(np.array([-3.0, np.nan, 2.0, 7.5, np.inf]), t, 2.0)
+    np.testing.assert_array_equal(got, [0.1, 0.1, 2.0, 2.0, 2.0])
+    # the identity polyline is the clamp
+    rng = np.random.default_rng(45)
+    x = rng.uniform(-1.0, 4.0, 1000)
+    ident = np.linspace(0.0, 3.0, 33)
+    np.testing.assert_allclose(o.tone_curve(x, ident, 3.0), np.clip(x, 0.0, 3.0), rtol=0,
+                               atol=1e-15)
+
+
+def test_tone_curve_chord_bound_on_a_parabola():
+    # the polyline through samples of x^2 (spacing h) lies above the parabola
+    # by at most h^2 / 4 (the chord error of a function with f'' = 2)
+    n, xm = 17, 2.0
+    h = xm / (n - 1)
+    t = np.linspace(0.0, xm, n) ** 2
+    x = np.random.default_rng(46).uniform(0.0, xm, 5000)
+    err = o.tone_curve(x, t, xm) - x * x
+    assert err.min() >= -1e-15
+    assert err.max() <= h * h / 4 + 1e-15
+    assert err.max() >= 0.9 * h * h / 4         # the bound is reached between samples
+
+
+def test_pixel_op_curve_per_channel_after_exposure():
+    rng = np.random.default_rng(47)
+    img = rng.random((6, 6, 4))
+    xm = 4.0
+    curves = np.stack([np.linspace(0.0, xm, 5),               # identity
+                       np.linspace(1.0, 0.0, 5),              # 1 - x / 4
+                       np.full(5, 0.25)])                     # constant
+    got = o.pixel_op(img, o.PIXELOP_CURVE, 3.0, curves, xm)
+    np.testing.assert_allclose(got[..., 0], np.clip(3.0 * img[..., 0], 0.0, xm), rtol=0,
+                               atol=1e-15)
+    np.testing.assert_allclose(got[..., 1], 1.0 - np.clip(3.0 * img[..., 1], 0.0, xm) / xm,
+                               rtol=0, atol=1e-15)
+    np.testing.assert_array_equal(got[..., 2], 0.25)
+    np.testing.assert_array_equal(got[..., 3], img[..., 3])
+
+
+def test_tone_curve_sampled_from_reinhard():
+    # Reinhard's curve x / (1 + x) sampled finely reproduces PIXELOP_REINHARD
+    # within the chord bound (|f''| <= 2 on x >= 0)
+    n, xm = 4096, 8.0
+    h = xm / (n - 1)
+    xs = np.linspace(0.0, xm, n)
+    curves = np.stack([xs / (1.0 + xs)] * 3)
+    img = np.random.default_rng(48).random((16, 16, 4)) * np.array([2.0, 2.0, 2.0, 1.0])
+    a = o.pixel_op(img, o.PIXELOP_CURVE, 1.5, curves, xm)
+    b = o.pixel_op(img, o.PIXELOP_REINHARD, 1.5)
+    assert np.abs(a - b).max() <= h * h / 4 + 1e-15
