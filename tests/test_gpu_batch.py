@@ -179,3 +179,52 @@ def test_end_frame_inside_a_stream_capture_is_refused():
     want = o.composite_frame(sc.W, sc.H, sc.T, o.BLEND_DEPTH, sc.tile_ids, sc.keys,
                              sc.rgba.astype(np.float64), sc.depth)
     assert np.max(np.abs(fb.color() - want)) <= TOL
+
+
+def test_pixel_ops_per_handle_in_one_launch():
+    """Each handle's pixel operation (tone curves of different lengths,
+    Reinhard, exposure, none) applies to its own frame inside one batched
+    launch and one graph replay; the RGBA8 equals the handle alone and the
+    oracle within 1 LSB."""
+    dtype = D.DFB_F32
+    frames = mixed_frames(dtype)
+    rng = np.random.default_rng(36)
+
+    def curve(n):
+        c = np.sort(rng.random((3, n)), axis=1)
+        return c.astype(np.float32)
+    ops = [(D.DFB_PIXELOP_CURVE, 1.4, curve(33), 1.25), (D.DFB_PIXELOP_REINHARD, 3.0, None, None),
+           (D.DFB_PIXELOP_NONE, 1.0, None, None), (D.DFB_PIXELOP_EXPOSURE, 0.6, None, None),
+           (D.DFB_PIXELOP_CURVE, 1.0, curve(5), 2.0)]
+
+    def setup():
+        fbs = make_buffers(frames, dtype)
+        for fb, (op, e, c, xm) in zip(fbs, ops):
+            D.dfb_set_pixel_op(fb.h, D.DFB_PIXELOP_EXPOSURE, e)
+            if op == D.DFB_PIXELOP_CURVE:
+                D.dfb_set_pixel_curve(fb.h, c, xm)
+            else:
+                D.dfb_set_pixel_op(fb.h, op, e)
+        return fbs
+    alone = []
+    for fb in setup():
+        fb.end()
+        alone.append(fb.rgba8())
+    fbs = setup()
+    D.dfb_end_frames([fb.h for fb in fbs])
+    for (sc, mode), fb, p0, (op, e, c, xm) in zip(frames, fbs, alone, ops):
+        p1 = fb.rgba8()
+        np.testing.assert_array_equal(p1, p0)
+        col = o.composite_frame(sc.W, sc.H, sc.T, mode, sc.tile_ids, sc.keys,
+                                o.dequantize(fb.stored, dtype, fb.scales), sc.depth)
+        want = o.pack_rgba8(o.pixel_op(col, op, e, None if c is None else c.astype(np.float64),
+                                       1.0 if xm is None else xm))
+        assert np.abs(o.unpack_rgba8(p1) - o.unpack_rgba8(want)).max() <= 1
+    fbs = setup()
+    g = D.dfb_graph_create([fb.h for fb in fbs])
+    try:
+        D.dfb_graph_launch(g)
+        for fb, p0 in zip(fbs, alone):
+            np.testing.assert_array_equal(fb.rgba8(), p0)
+    finally:
+        D.dfb_graph_destroy(g)
