@@ -192,7 +192,8 @@ DFB_API int dfb_set_pixel_op(dfb_handle h, int op, float exposure);
    The samples are copied into a device buffer of the handle (4096 samples
    per channel at most) before the call returns; the call first waits for the
    handle's frames in flight.  A CUDA graph captured from this handle reads
-   that buffer when it runs, with the n and x_max of its capture.
+   that buffer when it runs, with the n and x_max of its capture; the caller
+   must not load a curve while such a replay is in flight.
    Errors: INVALID_ARG (null curves, n outside [2, 4096], x_max not finite or
    <= 0, a sample not finite), OOM, CUDA. */
 DFB_API int dfb_set_pixel_curve(dfb_handle h, const float* curves, int n, float x_max);

@@ -683,10 +683,13 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
     const int P = w.P;
     const unsigned char* base = ring + meta->start;
     const bool accRead = w.active && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1;
-    const uint32_t stateRows = accRead ? ((A->kahan && !A->kahanFirst) ? 3u : 2u) : 0u;
-    const bool inRing = DFB_CHECK(n <= kN && (uint64_t)meta->start + meta->stateOff +
-                                                     (uint64_t)stateRows * P * 16u <= ringBytes,
-                                  ctl.err);
+    // checked build: the item's fragments and state rows lie inside the ring
+    const bool inRing = DFB_CHECK(
+        n <= kN && (uint64_t)meta->start + meta->stateOff +
+                           (uint64_t)(accRead ? ((A->kahan && !A->kahanFirst) ? 3u : 2u) : 0u) *
+                               P * 16u <=
+                       ringBytes,
+        ctl.err);
     float c0 = 0.f, c1 = 0.f, c2 = 0.f, al = 0.f;
     bool covered = true;
     if (w.active && inRing)
