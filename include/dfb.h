@@ -33,9 +33,14 @@
  *     given to a submit call is borrowed until the work of the dfb_end_frame
  *     call that consumes it has finished on its stream.  A host pointer is
  *     copied before the submit call returns, unless it is submitted as
- *     DFB_PTR_HOST_BORROWED: then it is borrowed like a device pointer.  The handle owns the resident
- *     framebuffers (colour, accumulation, variance, RGBA8).
+ *     DFB_PTR_HOST_BORROWED: then it is borrowed like a device pointer.
+ *     The handle owns the resident framebuffers (colour, accumulation,
+ *     variance, RGBA8).
  *   - Threads: a handle must not be used by two threads at once.
+ *   - Device: a handle lives on the device that was current when it first
+ *     allocated device memory (at creation, or at its first frame with
+ *     DFB_FLAG_DEFER_ALLOC).  Calls that enqueue device work with another
+ *     device current return DFB_ERR_STATE.
  */
 #ifndef DFB_H
 #define DFB_H
@@ -195,7 +200,8 @@ DFB_API int dfb_set_pixel_op(dfb_handle h, int op, float exposure);
    that buffer when it runs, with the n and x_max of its capture; the caller
    must not load a curve while such a replay is in flight.
    Errors: INVALID_ARG (null curves, n outside [2, 4096], x_max not finite or
-   <= 0, a sample not finite), OOM, CUDA. */
+   <= 0, a sample not finite), STATE (another device is current than the
+   handle's or the curve's), OOM, CUDA. */
 DFB_API int dfb_set_pixel_curve(dfb_handle h, const float* curves, int n, float x_max);
 
 /* Begin a frame (Sec. 3.1).  accumulate = 0 restarts the progressive

@@ -127,6 +127,7 @@ struct dfb_ctx {
   int pixelOp = DFB_PIXELOP_NONE;
   float exposure = 1.0f;
   float* curve = nullptr;  // 3 * kMaxCurve floats once a tone curve is loaded
+  int curveDevice = -1;    // device of `curve`
   int curveN = 0;
   float curveXMax = 1.0f;
   std::vector<FragRec> recs;
@@ -332,10 +333,12 @@ void free_device(dfb_ctx* h) {
 }
 
 int allocate(dfb_ctx* h) {
-  if (h->allocated) return DFB_OK;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return DFB_ERR_CUDA;
+  // device work of a handle stays on its device (its buffers live there)
+  if (h->allocated) return dev == h->device ? DFB_OK : DFB_ERR_STATE;
+  if (h->curve && dev != h->curveDevice) return DFB_ERR_STATE;
   h->device = dev;
   int st = ensure_table(dev);
   if (st != DFB_OK) return st;
@@ -777,13 +780,18 @@ int dfb_set_pixel_curve(dfb_handle h, const float* curves, int n, float x_max) {
   if (!isfinite(x_max) || x_max <= 0.0f) return DFB_ERR_INVALID_ARG;
   for (int i = 0; i < 3 * n; ++i)
     if (!isfinite(curves[i])) return DFB_ERR_INVALID_ARG;
-  cudaError_t e = cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return DFB_ERR_CUDA;
+  if ((h->allocated && dev != h->device) || (h->curve && dev != h->curveDevice))
+    return DFB_ERR_STATE;
   if (!h->curve) {
     e = cudaMalloc(&h->curve, sizeof(float) * 3 * (size_t)dfb::kMaxCurve);
     if (e != cudaSuccess) {
       h->curve = nullptr;
       return e == cudaErrorMemoryAllocation ? DFB_ERR_OOM : DFB_ERR_CUDA;
     }
+    h->curveDevice = dev;
   } else if (h->allocated && h->lastStreamSet) {
     // frames in flight may still read the previous samples
     e = cudaEventSynchronize(h->frameDone);
