@@ -1073,12 +1073,10 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
   // The bucketing reads only library-owned buffers, so it runs on the side
   // stream, overlapping the previous frame's composite (dfb_end_frames has
   // refused a capturing stream).
-  const bool side = true;
   cudaError_t e = cudaSuccess;
-  cudaStream_t bs = side ? h->bucketStream : s;
-  if (e == cudaSuccess && h->lastStreamSet && h->lastStream != s)
-    e = cudaStreamWaitEvent(s, h->frameDone, 0);
-  if (e == cudaSuccess && side && b.used) e = cudaStreamWaitEvent(bs, b.released, 0);
+  cudaStream_t bs = h->bucketStream;
+  if (h->lastStreamSet && h->lastStream != s) e = cudaStreamWaitEvent(s, h->frameDone, 0);
+  if (e == cudaSuccess && b.used) e = cudaStreamWaitEvent(bs, b.released, 0);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b.dStage, staged,
                         kHdrBytes + sizeof(FragRec) * n + sizeof(int) * (2 * nLong + 1),
@@ -1090,8 +1088,8 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
     e = dfb::launch_bucket(b.dRecs, (int)n, h->nTiles, b.counts, b.offsets, b.cursor, b.tmp,
                            b.srecs, b.blocks, bs);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], bs);
-  if (e == cudaSuccess && side) e = cudaEventRecord(b.ready, bs);
-  if (e == cudaSuccess && side) e = cudaStreamWaitEvent(s, b.ready, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(b.ready, bs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b.ready, 0);
   if (e == cudaSuccess && h->hostCopies) e = cudaStreamWaitEvent(s, h->copyDone, 0);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
   if (e == cudaSuccess)
@@ -1157,9 +1155,8 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
   b.hItemBase[n] = items;
   // Uploads and bucketing touch only this set, so they run on the device's
   // side stream, overlapping earlier work on `s`.
-  const bool side = true;
   cudaStream_t bs = bd.side;
-  if (e == cudaSuccess && side && b.used) e = cudaStreamWaitEvent(bs, b.released, 0);
+  if (e == cudaSuccess && b.used) e = cudaStreamWaitEvent(bs, b.released, 0);
   if (e == cudaSuccess && nRec)
     e = cudaMemcpyAsync(b.dRecs, b.hRecs, sizeof(FragRec) * nRec, cudaMemcpyHostToDevice, bs);
   if (e == cudaSuccess)
@@ -1186,8 +1183,8 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
     e = dfb::launch_bucket(b.dRecs, (int)nRec, (int)nTiles, b.counts, b.offsets, b.cursor, b.tmp,
                            b.srecs, b.blocks, bs);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], bs);
-  if (e == cudaSuccess && side) e = cudaEventRecord(b.ready, bs);
-  if (e == cudaSuccess && side) e = cudaStreamWaitEvent(s, b.ready, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(b.ready, bs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b.ready, 0);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
   if (e == cudaSuccess)
     e = dfb::launch_composite(b.dFrames, b.dItemBase, n, items, tileBase, anyAcc, dtype,
