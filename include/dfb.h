@@ -21,7 +21,10 @@
  *
  * Conventions shared by every entry point:
  *   - Return value: DFB_OK (0) or a negative DFB_ERR_* code.  No C++
- *     exception crosses this interface.  dfb_error_string() names a code.
+ *     exception crosses this interface: a host allocation that fails inside
+ *     a call returns DFB_ERR_OOM (an open frame may then hold part of that
+ *     call's tiles: begin the frame again).  dfb_error_string() names a
+ *     code.
  *   - Pixels: a fragment tile is T*T pixels, row-major inside the tile
  *     (pixel p = y*T + x).  Frames are row-major images W*H.  Tiles are
  *     numbered row-major: tile = ty * ceil(W/T) + tx.  Pixels of a submitted

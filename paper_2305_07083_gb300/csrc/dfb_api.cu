@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <mutex>
 #include <new>
+#include <stdexcept>
 #include <vector>
 
 #include "dfb_internal.h"
@@ -673,6 +674,24 @@ int stage_records(dfb_ctx* h, FragRec** out) {
   return buf;
 }
 
+// Every entry point of the C ABI runs its body under this guard, so that no
+// C++ exception crosses the interface: a failed host allocation (a growing
+// record list, tree or staging vector) returns DFB_ERR_OOM; no other
+// exception is thrown by this library, and one from elsewhere returns
+// DFB_ERR_STATE.
+template <typename F>
+int guarded(F&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return DFB_ERR_OOM;
+  } catch (const std::length_error&) {
+    return DFB_ERR_OOM;
+  } catch (...) {
+    return DFB_ERR_STATE;
+  }
+}
+
 }  // namespace
 
 // ============================================================================
@@ -699,211 +718,242 @@ const char* dfb_error_string(int s) {
 int dfb_version(void) { return kVersion; }
 
 int dfb_create_ex(const dfb_config* cfg, dfb_handle* out) {
-  if (!cfg || !out) return DFB_ERR_INVALID_ARG;
-  *out = nullptr;
-  const int T = cfg->tile_size;
-  if (cfg->width < 1 || cfg->height < 1 || !is_pow2(T) || T < 4 || T > 256)
-    return DFB_ERR_INVALID_ARG;
-  if ((int64_t)cfg->width * cfg->height > (int64_t)1 << 31) return DFB_ERR_INVALID_ARG;
-  if (cfg->mode < DFB_BLEND_DEPTH || cfg->mode > DFB_AVERAGE) return DFB_ERR_INVALID_ARG;
-  if (cfg->dtype < DFB_F32 || cfg->dtype > DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;
-  if (cfg->flags & ~(DFB_FLAG_ACCUMULATE | DFB_FLAG_WRITE_COLOR | DFB_FLAG_PACK_RGBA8 |
-                     DFB_FLAG_DEFER_ALLOC))
-    return DFB_ERR_INVALID_ARG;
-  dfb_ctx* h = new (std::nothrow) dfb_ctx();
-  if (!h) return DFB_ERR_OOM;
-  h->cfg = *cfg;
-  if (h->cfg.kahan_after <= 0) h->cfg.kahan_after = 256;
-  h->tilesX = (cfg->width + T - 1) / T;
-  h->tilesY = (cfg->height + T - 1) / T;
-  h->nTiles = h->tilesX * h->tilesY;
-  h->logT = ilog2(T);
-  h->tilePixels = T * T;
-  h->chunks = h->tilePixels < dfb::kItemPixels ? 1 : h->tilePixels / dfb::kItemPixels;
-  h->rgbaBytes = (size_t)h->tilePixels * 4 * elt_bytes(cfg->dtype);
-  h->depthBytes = (size_t)h->tilePixels * 4;
-  h->declared.assign(h->nTiles, -1);
-  h->recvGen1.assign(h->nTiles, 0);
-  h->childGen1.assign(h->nTiles, 0);
-  h->fragCount.assign(h->nTiles, 0);
-  if (!(cfg->flags & DFB_FLAG_DEFER_ALLOC)) {
-    const int st = allocate(h);
-    if (st != DFB_OK) {
-      free_device(h);
+  return guarded([&]() -> int {
+    if (!cfg || !out) return DFB_ERR_INVALID_ARG;
+    *out = nullptr;
+    const int T = cfg->tile_size;
+    if (cfg->width < 1 || cfg->height < 1 || !is_pow2(T) || T < 4 || T > 256)
+      return DFB_ERR_INVALID_ARG;
+    if ((int64_t)cfg->width * cfg->height > (int64_t)1 << 31) return DFB_ERR_INVALID_ARG;
+    if (cfg->mode < DFB_BLEND_DEPTH || cfg->mode > DFB_AVERAGE) return DFB_ERR_INVALID_ARG;
+    if (cfg->dtype < DFB_F32 || cfg->dtype > DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;
+    if (cfg->flags & ~(DFB_FLAG_ACCUMULATE | DFB_FLAG_WRITE_COLOR | DFB_FLAG_PACK_RGBA8 |
+                       DFB_FLAG_DEFER_ALLOC))
+      return DFB_ERR_INVALID_ARG;
+    dfb_ctx* h = new (std::nothrow) dfb_ctx();
+    if (!h) return DFB_ERR_OOM;
+    h->cfg = *cfg;
+    if (h->cfg.kahan_after <= 0) h->cfg.kahan_after = 256;
+    h->tilesX = (cfg->width + T - 1) / T;
+    h->tilesY = (cfg->height + T - 1) / T;
+    h->nTiles = h->tilesX * h->tilesY;
+    h->logT = ilog2(T);
+    h->tilePixels = T * T;
+    h->chunks = h->tilePixels < dfb::kItemPixels ? 1 : h->tilePixels / dfb::kItemPixels;
+    h->rgbaBytes = (size_t)h->tilePixels * 4 * elt_bytes(cfg->dtype);
+    h->depthBytes = (size_t)h->tilePixels * 4;
+    try {
+      h->declared.assign(h->nTiles, -1);
+      h->recvGen1.assign(h->nTiles, 0);
+      h->childGen1.assign(h->nTiles, 0);
+      h->fragCount.assign(h->nTiles, 0);
+    } catch (...) {
       delete h;
-      return st;
+      throw;
     }
-  }
-  *out = h;
-  return DFB_OK;
+    if (!(cfg->flags & DFB_FLAG_DEFER_ALLOC)) {
+      const int st = allocate(h);
+      if (st != DFB_OK) {
+        free_device(h);
+        delete h;
+        return st;
+      }
+    }
+    *out = h;
+    return DFB_OK;
+  });
 }
 
 int dfb_create(int width, int height, int tile_size, int mode, dfb_handle* out) {
-  dfb_config c{};
-  c.width = width;
-  c.height = height;
-  c.tile_size = tile_size;
-  c.mode = mode;
-  c.dtype = DFB_F32;
-  c.flags = DFB_FLAGS_DEFAULT;
-  return dfb_create_ex(&c, out);
+  return guarded([&]() -> int {
+    dfb_config c{};
+    c.width = width;
+    c.height = height;
+    c.tile_size = tile_size;
+    c.mode = mode;
+    c.dtype = DFB_F32;
+    c.flags = DFB_FLAGS_DEFAULT;
+    return dfb_create_ex(&c, out);
+  });
 }
 
 int dfb_destroy(dfb_handle h) {
-  if (!h) return DFB_OK;
-  if (h->allocated && h->lastStreamSet) cudaEventSynchronize(h->frameDone);
-  free_device(h);
-  if (h->curve) cudaFree(h->curve);
-  delete h;
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h) return DFB_OK;
+    if (h->allocated && h->lastStreamSet) cudaEventSynchronize(h->frameDone);
+    free_device(h);
+    if (h->curve) cudaFree(h->curve);
+    delete h;
+    return DFB_OK;
+  });
 }
 
 int dfb_set_background(dfb_handle h, float r, float g, float b, float a) {
-  if (!h) return DFB_ERR_INVALID_ARG;
-  if (!isfinite(r) || !isfinite(g) || !isfinite(b) || !isfinite(a)) return DFB_ERR_INVALID_ARG;
-  h->bg[0] = r; h->bg[1] = g; h->bg[2] = b; h->bg[3] = a;
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h) return DFB_ERR_INVALID_ARG;
+    if (!isfinite(r) || !isfinite(g) || !isfinite(b) || !isfinite(a)) return DFB_ERR_INVALID_ARG;
+    h->bg[0] = r; h->bg[1] = g; h->bg[2] = b; h->bg[3] = a;
+    return DFB_OK;
+  });
 }
 
 int dfb_set_pixel_op(dfb_handle h, int op, float exposure) {
-  if (!h) return DFB_ERR_INVALID_ARG;
-  if (op < DFB_PIXELOP_NONE || op > DFB_PIXELOP_CURVE) return DFB_ERR_INVALID_ARG;
-  if (!isfinite(exposure) || exposure < 0.0f) return DFB_ERR_INVALID_ARG;
-  if (op == DFB_PIXELOP_CURVE && !h->curve) return DFB_ERR_STATE;
-  h->pixelOp = op;
-  h->exposure = exposure;
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h) return DFB_ERR_INVALID_ARG;
+    if (op < DFB_PIXELOP_NONE || op > DFB_PIXELOP_CURVE) return DFB_ERR_INVALID_ARG;
+    if (!isfinite(exposure) || exposure < 0.0f) return DFB_ERR_INVALID_ARG;
+    if (op == DFB_PIXELOP_CURVE && !h->curve) return DFB_ERR_STATE;
+    h->pixelOp = op;
+    h->exposure = exposure;
+    return DFB_OK;
+  });
 }
 
 int dfb_set_pixel_curve(dfb_handle h, const float* curves, int n, float x_max) {
-  if (!h || !curves || n < 2 || n > dfb::kMaxCurve) return DFB_ERR_INVALID_ARG;
-  if (!isfinite(x_max) || x_max <= 0.0f) return DFB_ERR_INVALID_ARG;
-  for (int i = 0; i < 3 * n; ++i)
-    if (!isfinite(curves[i])) return DFB_ERR_INVALID_ARG;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return DFB_ERR_CUDA;
-  if ((h->allocated && dev != h->device) || (h->curve && dev != h->curveDevice))
-    return DFB_ERR_STATE;
-  if (!h->curve) {
-    e = cudaMalloc(&h->curve, sizeof(float) * 3 * (size_t)dfb::kMaxCurve);
-    if (e != cudaSuccess) {
-      h->curve = nullptr;
-      return e == cudaErrorMemoryAllocation ? DFB_ERR_OOM : DFB_ERR_CUDA;
-    }
-    h->curveDevice = dev;
-  } else if (h->allocated && h->lastStreamSet) {
-    // frames in flight may still read the previous samples
-    e = cudaEventSynchronize(h->frameDone);
+  return guarded([&]() -> int {
+    if (!h || !curves || n < 2 || n > dfb::kMaxCurve) return DFB_ERR_INVALID_ARG;
+    if (!isfinite(x_max) || x_max <= 0.0f) return DFB_ERR_INVALID_ARG;
+    for (int i = 0; i < 3 * n; ++i)
+      if (!isfinite(curves[i])) return DFB_ERR_INVALID_ARG;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return DFB_ERR_CUDA;
-  }
-  // the legacy stream, waited for: the DMA of a pageable source has landed
-  // when the call returns
-  e = cudaMemcpyAsync(h->curve, curves, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, 0);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
-  if (e != cudaSuccess) return DFB_ERR_CUDA;
-  h->curveN = n;
-  h->curveXMax = x_max;
-  h->pixelOp = DFB_PIXELOP_CURVE;
-  return DFB_OK;
+    if ((h->allocated && dev != h->device) || (h->curve && dev != h->curveDevice))
+      return DFB_ERR_STATE;
+    if (!h->curve) {
+      e = cudaMalloc(&h->curve, sizeof(float) * 3 * (size_t)dfb::kMaxCurve);
+      if (e != cudaSuccess) {
+        h->curve = nullptr;
+        return e == cudaErrorMemoryAllocation ? DFB_ERR_OOM : DFB_ERR_CUDA;
+      }
+      h->curveDevice = dev;
+    } else if (h->allocated && h->lastStreamSet) {
+      // frames in flight may still read the previous samples
+      e = cudaEventSynchronize(h->frameDone);
+      if (e != cudaSuccess) return DFB_ERR_CUDA;
+    }
+    // the legacy stream, waited for: the DMA of a pageable source has landed
+    // when the call returns
+    e = cudaMemcpyAsync(h->curve, curves, sizeof(float) * 3 * (size_t)n, cudaMemcpyHostToDevice, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) return DFB_ERR_CUDA;
+    h->curveN = n;
+    h->curveXMax = x_max;
+    h->pixelOp = DFB_PIXELOP_CURVE;
+    return DFB_OK;
+  });
 }
 
 int dfb_begin_frame(dfb_handle h, int accumulate) {
-  if (!h) return DFB_ERR_INVALID_ARG;
-  if (h->inFrame) return DFB_ERR_STATE;
-  h->inFrame = true;
-  h->recs.clear();
-  std::fill(h->declared.begin(), h->declared.end(), -1);
-  std::fill(h->recvGen1.begin(), h->recvGen1.end(), 0);
-  std::fill(h->childGen1.begin(), h->childGen1.end(), 0);
-  for (int t : h->touchedDeeper) h->deeper[t].clear();
-  h->touchedDeeper.clear();
-  std::fill(h->fragCount.begin(), h->fragCount.end(), 0);
-  h->longTiles.clear();
-  h->hostCopies = false;
-  h->arenaIdx ^= 1;
-  h->arenas[h->arenaIdx].reset();
-  const bool acc = (h->cfg.flags & DFB_FLAG_ACCUMULATE) && accumulate && h->accumN > 0;
-  h->pendingN = acc ? h->accumN + 1 : 1;
-  h->pendingStats = dfb_frame_stats{};
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h) return DFB_ERR_INVALID_ARG;
+    if (h->inFrame) return DFB_ERR_STATE;
+    h->inFrame = true;
+    h->recs.clear();
+    std::fill(h->declared.begin(), h->declared.end(), -1);
+    std::fill(h->recvGen1.begin(), h->recvGen1.end(), 0);
+    std::fill(h->childGen1.begin(), h->childGen1.end(), 0);
+    for (int t : h->touchedDeeper) h->deeper[t].clear();
+    h->touchedDeeper.clear();
+    std::fill(h->fragCount.begin(), h->fragCount.end(), 0);
+    h->longTiles.clear();
+    h->hostCopies = false;
+    h->arenaIdx ^= 1;
+    h->arenas[h->arenaIdx].reset();
+    const bool acc = (h->cfg.flags & DFB_FLAG_ACCUMULATE) && accumulate && h->accumN > 0;
+    h->pendingN = acc ? h->accumN + 1 : 1;
+    h->pendingStats = dfb_frame_stats{};
+    return DFB_OK;
+  });
 }
 
 int dfb_set_tile_children(dfb_handle h, int tile_id, int n_children) {
-  if (!h) return DFB_ERR_INVALID_ARG;
-  if (!h->inFrame) return DFB_ERR_STATE;
-  if (tile_id < 0 || tile_id >= h->nTiles) return DFB_ERR_TILE_RANGE;
-  if (n_children < 0) return DFB_ERR_INVALID_ARG;
-  if (h->declared[tile_id] >= 0) return DFB_ERR_STATE;
-  h->declared[tile_id] = n_children;
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h) return DFB_ERR_INVALID_ARG;
+    if (!h->inFrame) return DFB_ERR_STATE;
+    if (tile_id < 0 || tile_id >= h->nTiles) return DFB_ERR_TILE_RANGE;
+    if (n_children < 0) return DFB_ERR_INVALID_ARG;
+    if (h->declared[tile_id] >= 0) return DFB_ERR_STATE;
+    h->declared[tile_id] = n_children;
+    return DFB_OK;
+  });
 }
 
 int dfb_submit_tile_ex(dfb_handle h, const dfb_tile_desc* tile) {
-  if (!h) return DFB_ERR_INVALID_ARG;
-  if (!h->inFrame) return DFB_ERR_STATE;
-  const int st = validate_tile(h, tile);
-  if (st != DFB_OK) return st;
-  return append_records(h, 1, tile, DFB_PTR_AUTO);
+  return guarded([&]() -> int {
+    if (!h) return DFB_ERR_INVALID_ARG;
+    if (!h->inFrame) return DFB_ERR_STATE;
+    const int st = validate_tile(h, tile);
+    if (st != DFB_OK) return st;
+    return append_records(h, 1, tile, DFB_PTR_AUTO);
+  });
 }
 
 int dfb_submit_tile(dfb_handle h, int tile_id, float order_key, const void* rgba,
                     const float* depth) {
-  dfb_tile_desc t;
-  t.tile_id = tile_id;
-  t.order_key = order_key;
-  t.rgba = rgba;
-  t.depth = depth;
-  t.scale = 1.0f;
-  t.generation = 1;
-  t.children = 0;
-  if (h && h->cfg.dtype == DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;  // needs a scale
-  return dfb_submit_tile_ex(h, &t);
+  return guarded([&]() -> int {
+    dfb_tile_desc t;
+    t.tile_id = tile_id;
+    t.order_key = order_key;
+    t.rgba = rgba;
+    t.depth = depth;
+    t.scale = 1.0f;
+    t.generation = 1;
+    t.children = 0;
+    if (h && h->cfg.dtype == DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;  // needs a scale
+    return dfb_submit_tile_ex(h, &t);
+  });
 }
 
 int dfb_submit_tiles(dfb_handle h, int n, const int* tile_ids, const float* order_keys,
                      const void* const* rgba, const float* const* depth, const float* scales,
                      int where) {
-  if (!h || n < 0) return DFB_ERR_INVALID_ARG;
-  if (!h->inFrame) return DFB_ERR_STATE;
-  if (n == 0) return DFB_OK;
-  if (where < DFB_PTR_AUTO || where > DFB_PTR_HOST_BORROWED) return DFB_ERR_INVALID_ARG;
-  // validate everything first: nothing is submitted if an entry is bad
-  const int st = validate_arrays(h, n, tile_ids, order_keys, rgba, depth, scales);
-  if (st != DFB_OK) return st;
-  if (where != DFB_PTR_DEVICE) {
-    std::vector<dfb_tile_desc> ts((size_t)n);
-    for (int i = 0; i < n; ++i)
-      ts[i] = dfb_tile_desc{tile_ids[i], order_keys[i], rgba[i], depth[i],
-                            scales ? scales[i] : 1.0f, 1, 0};
-    return append_records(h, n, ts.data(), where);
-  }
-  // device pointers: append directly
-  const size_t base = h->recs.size();
-  h->recs.resize(base + (size_t)n);
-  const int64_t fpx = build_records(h, n, tile_ids, order_keys, rgba, depth, scales,
-                                    h->recs.data() + base, h->recvGen1.data());
-  for (int i = 0; i < n; ++i) count_frags(h, tile_ids[i], 1);
-  h->pendingStats.fragments += n;
-  h->pendingStats.fragment_pixels += fpx;
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h || n < 0) return DFB_ERR_INVALID_ARG;
+    if (!h->inFrame) return DFB_ERR_STATE;
+    if (n == 0) return DFB_OK;
+    if (where < DFB_PTR_AUTO || where > DFB_PTR_HOST_BORROWED) return DFB_ERR_INVALID_ARG;
+    // validate everything first: nothing is submitted if an entry is bad
+    const int st = validate_arrays(h, n, tile_ids, order_keys, rgba, depth, scales);
+    if (st != DFB_OK) return st;
+    if (where != DFB_PTR_DEVICE) {
+      std::vector<dfb_tile_desc> ts((size_t)n);
+      for (int i = 0; i < n; ++i)
+        ts[i] = dfb_tile_desc{tile_ids[i], order_keys[i], rgba[i], depth[i],
+                              scales ? scales[i] : 1.0f, 1, 0};
+      return append_records(h, n, ts.data(), where);
+    }
+    // device pointers: append directly
+    const size_t base = h->recs.size();
+    h->recs.resize(base + (size_t)n);
+    const int64_t fpx = build_records(h, n, tile_ids, order_keys, rgba, depth, scales,
+                                      h->recs.data() + base, h->recvGen1.data());
+    for (int i = 0; i < n; ++i) count_frags(h, tile_ids[i], 1);
+    h->pendingStats.fragments += n;
+    h->pendingStats.fragment_pixels += fpx;
+    return DFB_OK;
+  });
 }
 
 int dfb_submit_tiles_ex(dfb_handle h, int n, const dfb_tile_desc* tiles, int where) {
-  if (!h || n < 0) return DFB_ERR_INVALID_ARG;
-  if (!h->inFrame) return DFB_ERR_STATE;
-  if (n == 0) return DFB_OK;
-  if (!tiles || where < DFB_PTR_AUTO || where > DFB_PTR_HOST_BORROWED) return DFB_ERR_INVALID_ARG;
-  for (int i = 0; i < n; ++i) {
-    const int st = validate_tile(h, &tiles[i]);
-    if (st != DFB_OK) return st;
-  }
-  return append_records(h, n, tiles, where);
+  return guarded([&]() -> int {
+    if (!h || n < 0) return DFB_ERR_INVALID_ARG;
+    if (!h->inFrame) return DFB_ERR_STATE;
+    if (n == 0) return DFB_OK;
+    if (!tiles || where < DFB_PTR_AUTO || where > DFB_PTR_HOST_BORROWED) return DFB_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+      const int st = validate_tile(h, &tiles[i]);
+      if (st != DFB_OK) return st;
+    }
+    return append_records(h, n, tiles, where);
+  });
 }
 
 int dfb_end_frame(dfb_handle h, void* stream) {
-  if (!h) return DFB_ERR_INVALID_ARG;
-  return dfb_end_frames(&h, 1, stream);
+  return guarded([&]() -> int {
+    if (!h) return DFB_ERR_INVALID_ARG;
+    return dfb_end_frames(&h, 1, stream);
+  });
 }
 
 }  // extern "C"
@@ -1206,54 +1256,58 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
 extern "C" {
 
 int dfb_end_frames(const dfb_handle* hs, int n, void* stream) {
-  if (!hs || n < 1) return DFB_ERR_INVALID_ARG;
-  for (int i = 0; i < n; ++i) {
-    if (!hs[i]) return DFB_ERR_INVALID_ARG;
-    for (int j = 0; j < i; ++j)
-      if (hs[j] == hs[i]) return DFB_ERR_INVALID_ARG;
-    if (!hs[i]->inFrame) return DFB_ERR_STATE;
-    if (n > 1 && hs[i]->cfg.dtype != hs[0]->cfg.dtype) return DFB_ERR_INVALID_ARG;
-  }
-  for (int i = 0; i < n; ++i) {
-    const int st = check_trees(hs[i]);
-    if (st != DFB_OK) return st;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
-  {
-    // A captured end of frame would replay an upload from a staging buffer
-    // that later frames overwrite: refused (dfb_graph_* captures batches).
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) cudaGetLastError();
-    else if (cap != cudaStreamCaptureStatusNone) return DFB_ERR_STATE;
-  }
-  for (int i = 0; i < n; ++i) {
-    const int st = allocate(hs[i]);
-    if (st != DFB_OK) return st;
-  }
-  const int st = n == 1 ? end_one(hs[0], s) : end_batch(hs, n, s);
-  if (st != DFB_OK) return st;
-  for (int i = 0; i < n; ++i) {
-    dfb_ctx* h = hs[i];
-    if (h->hostCopies) {
-      cudaEventRecord(h->arenaFree[h->arenaIdx], s);
-      h->arenaUsed[h->arenaIdx] = true;
+  return guarded([&]() -> int {
+    if (!hs || n < 1) return DFB_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+      if (!hs[i]) return DFB_ERR_INVALID_ARG;
+      for (int j = 0; j < i; ++j)
+        if (hs[j] == hs[i]) return DFB_ERR_INVALID_ARG;
+      if (!hs[i]->inFrame) return DFB_ERR_STATE;
+      if (n > 1 && hs[i]->cfg.dtype != hs[0]->cfg.dtype) return DFB_ERR_INVALID_ARG;
     }
-    finish_stats(h);
-    h->stats = h->pendingStats;
-    h->accumN = h->pendingN;
-    h->inFrame = false;
-    h->haveFrame = true;
-    h->lastStream = s;
-    h->lastStreamSet = true;
-  }
-  return DFB_OK;
+    for (int i = 0; i < n; ++i) {
+      const int st = check_trees(hs[i]);
+      if (st != DFB_OK) return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+      // A captured end of frame would replay an upload from a staging buffer
+      // that later frames overwrite: refused (dfb_graph_* captures batches).
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) cudaGetLastError();
+      else if (cap != cudaStreamCaptureStatusNone) return DFB_ERR_STATE;
+    }
+    for (int i = 0; i < n; ++i) {
+      const int st = allocate(hs[i]);
+      if (st != DFB_OK) return st;
+    }
+    const int st = n == 1 ? end_one(hs[0], s) : end_batch(hs, n, s);
+    if (st != DFB_OK) return st;
+    for (int i = 0; i < n; ++i) {
+      dfb_ctx* h = hs[i];
+      if (h->hostCopies) {
+        cudaEventRecord(h->arenaFree[h->arenaIdx], s);
+        h->arenaUsed[h->arenaIdx] = true;
+      }
+      finish_stats(h);
+      h->stats = h->pendingStats;
+      h->accumN = h->pendingN;
+      h->inFrame = false;
+      h->haveFrame = true;
+      h->lastStream = s;
+      h->lastStreamSet = true;
+    }
+    return DFB_OK;
+  });
 }
 
 int dfb_sync(dfb_handle h) {
-  if (!h) return DFB_ERR_INVALID_ARG;
-  if (!h->lastStreamSet) return DFB_OK;
-  const int st = cuda_status(cudaEventSynchronize(h->frameDone));
-  return st != DFB_OK ? st : take_device_error(h);
+  return guarded([&]() -> int {
+    if (!h) return DFB_ERR_INVALID_ARG;
+    if (!h->lastStreamSet) return DFB_OK;
+    const int st = cuda_status(cudaEventSynchronize(h->frameDone));
+    return st != DFB_OK ? st : take_device_error(h);
+  });
 }
 
 }  // extern "C"
@@ -1281,74 +1335,86 @@ int ensure_read_tmp(dfb_ctx* h) {
 extern "C" {
 
 int dfb_read_color(dfb_handle h, float* out) {
-  if (!h || !out) return DFB_ERR_INVALID_ARG;
-  if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_WRITE_COLOR)) return DFB_ERR_STATE;
-  return copy_out(h, out, h->color, sizeof(float4) * (size_t)h->cfg.width * h->cfg.height);
+  return guarded([&]() -> int {
+    if (!h || !out) return DFB_ERR_INVALID_ARG;
+    if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_WRITE_COLOR)) return DFB_ERR_STATE;
+    return copy_out(h, out, h->color, sizeof(float4) * (size_t)h->cfg.width * h->cfg.height);
+  });
 }
 
 int dfb_read_rgba8(dfb_handle h, uint32_t* out) {
-  if (!h || !out) return DFB_ERR_INVALID_ARG;
-  if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_PACK_RGBA8)) return DFB_ERR_STATE;
-  return copy_out(h, out, h->rgba8, sizeof(uint32_t) * (size_t)h->cfg.width * h->cfg.height);
+  return guarded([&]() -> int {
+    if (!h || !out) return DFB_ERR_INVALID_ARG;
+    if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_PACK_RGBA8)) return DFB_ERR_STATE;
+    return copy_out(h, out, h->rgba8, sizeof(uint32_t) * (size_t)h->cfg.width * h->cfg.height);
+  });
 }
 
 int dfb_read_accum(dfb_handle h, float* out) {
-  if (!h || !out) return DFB_ERR_INVALID_ARG;
-  if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
-  const int64_t px = (int64_t)h->cfg.width * h->cfg.height;
-  const bool dev = is_device_ptr(out);
-  float4* dst = (float4*)out;
-  if (!dev) {
-    const int st = ensure_read_tmp(h);
-    if (st != DFB_OK) return st;
-    dst = h->readTmp;
-  }
-  const int n = h->accumN;
-  cudaError_t e = dfb::launch_tiles_to_image(h->accum, n > h->cfg.kahan_after ? h->comp : nullptr,
-                                             1.0f / (float)n, dst, h->cfg.width, h->cfg.height,
-                                             h->cfg.tile_size, h->lastStream);
-  if (e != cudaSuccess) return cuda_status(e);
-  if (dev) return DFB_OK;
-  return copy_out(h, out, h->readTmp, sizeof(float4) * (size_t)px);
-}
-
-int dfb_read_variance(dfb_handle h, float* per_pixel, float* per_tile) {
-  if (!h) return DFB_ERR_INVALID_ARG;
-  if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
-  const int64_t px = (int64_t)h->cfg.width * h->cfg.height;
-  const int n = h->accumN;
-  const float invNm1 = n > 1 ? 1.0f / (float)(n - 1) : 0.0f;
-  if (per_pixel) {
-    const bool dev = is_device_ptr(per_pixel);
-    float4* dst = (float4*)per_pixel;
+  return guarded([&]() -> int {
+    if (!h || !out) return DFB_ERR_INVALID_ARG;
+    if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
+    const int64_t px = (int64_t)h->cfg.width * h->cfg.height;
+    const bool dev = is_device_ptr(out);
+    float4* dst = (float4*)out;
     if (!dev) {
       const int st = ensure_read_tmp(h);
       if (st != DFB_OK) return st;
       dst = h->readTmp;
     }
-    cudaError_t e = dfb::launch_tiles_to_image(h->m2, nullptr, invNm1, dst, h->cfg.width,
-                                               h->cfg.height, h->cfg.tile_size, h->lastStream);
+    const int n = h->accumN;
+    cudaError_t e = dfb::launch_tiles_to_image(h->accum, n > h->cfg.kahan_after ? h->comp : nullptr,
+                                               1.0f / (float)n, dst, h->cfg.width, h->cfg.height,
+                                               h->cfg.tile_size, h->lastStream);
     if (e != cudaSuccess) return cuda_status(e);
-    if (!dev) {
-      const int st = copy_out(h, per_pixel, h->readTmp, sizeof(float4) * (size_t)px);
-      if (st != DFB_OK) return st;
+    if (dev) return DFB_OK;
+    return copy_out(h, out, h->readTmp, sizeof(float4) * (size_t)px);
+  });
+}
+
+int dfb_read_variance(dfb_handle h, float* per_pixel, float* per_tile) {
+  return guarded([&]() -> int {
+    if (!h) return DFB_ERR_INVALID_ARG;
+    if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
+    const int64_t px = (int64_t)h->cfg.width * h->cfg.height;
+    const int n = h->accumN;
+    const float invNm1 = n > 1 ? 1.0f / (float)(n - 1) : 0.0f;
+    if (per_pixel) {
+      const bool dev = is_device_ptr(per_pixel);
+      float4* dst = (float4*)per_pixel;
+      if (!dev) {
+        const int st = ensure_read_tmp(h);
+        if (st != DFB_OK) return st;
+        dst = h->readTmp;
+      }
+      cudaError_t e = dfb::launch_tiles_to_image(h->m2, nullptr, invNm1, dst, h->cfg.width,
+                                                 h->cfg.height, h->cfg.tile_size, h->lastStream);
+      if (e != cudaSuccess) return cuda_status(e);
+      if (!dev) {
+        const int st = copy_out(h, per_pixel, h->readTmp, sizeof(float4) * (size_t)px);
+        if (st != DFB_OK) return st;
+      }
     }
-  }
-  if (per_tile) return copy_out(h, per_tile, h->tileVar, sizeof(float) * h->nTiles);
-  return DFB_OK;
+    if (per_tile) return copy_out(h, per_tile, h->tileVar, sizeof(float) * h->nTiles);
+    return DFB_OK;
+  });
 }
 
 int dfb_get_stats(dfb_handle h, dfb_frame_stats* out) {
-  if (!h || !out) return DFB_ERR_INVALID_ARG;
-  *out = h->stats;
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h || !out) return DFB_ERR_INVALID_ARG;
+    *out = h->stats;
+    return DFB_OK;
+  });
 }
 
 int dfb_get_tiles(dfb_handle h, int* tiles_x, int* tiles_y) {
-  if (!h || !tiles_x || !tiles_y) return DFB_ERR_INVALID_ARG;
-  *tiles_x = h->tilesX;
-  *tiles_y = h->tilesY;
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h || !tiles_x || !tiles_y) return DFB_ERR_INVALID_ARG;
+    *tiles_x = h->tilesX;
+    *tiles_y = h->tilesY;
+    return DFB_OK;
+  });
 }
 
 // Tile-major state buffer -> caller's row-major image (host or device).
@@ -1368,91 +1434,107 @@ int state_out(dfb_ctx* h, float* out, const float4* src) {
 }
 
 int dfb_save_accum(dfb_handle h, float* sum, float* comp, float* m2, int* frames) {
-  if (!h || !sum || !comp || !m2 || !frames) return DFB_ERR_INVALID_ARG;
-  if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
-  const size_t bytes = sizeof(float4) * (size_t)h->cfg.width * h->cfg.height;
-  int st = state_out(h, sum, h->accum);
-  if (st == DFB_OK) {
-    if (h->accumN > h->cfg.kahan_after) st = state_out(h, comp, h->comp);
-    else {
-      const bool dev = is_device_ptr(comp);
-      if (dev) st = cuda_status(cudaMemsetAsync(comp, 0, bytes, h->lastStream));
-      else memset(comp, 0, bytes);
+  return guarded([&]() -> int {
+    if (!h || !sum || !comp || !m2 || !frames) return DFB_ERR_INVALID_ARG;
+    if (!h->haveFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
+    const size_t bytes = sizeof(float4) * (size_t)h->cfg.width * h->cfg.height;
+    int st = state_out(h, sum, h->accum);
+    if (st == DFB_OK) {
+      if (h->accumN > h->cfg.kahan_after) st = state_out(h, comp, h->comp);
+      else {
+        const bool dev = is_device_ptr(comp);
+        if (dev) st = cuda_status(cudaMemsetAsync(comp, 0, bytes, h->lastStream));
+        else memset(comp, 0, bytes);
+      }
     }
-  }
-  if (st == DFB_OK) st = state_out(h, m2, h->m2);
-  if (st == DFB_OK) *frames = h->accumN;
-  return st;
+    if (st == DFB_OK) st = state_out(h, m2, h->m2);
+    if (st == DFB_OK) *frames = h->accumN;
+    return st;
+  });
 }
 
 int dfb_load_accum(dfb_handle h, const float* sum, const float* comp, const float* m2,
                    int frames) {
-  if (!h || !sum || !comp || !m2 || frames < 1) return DFB_ERR_INVALID_ARG;
-  if (h->inFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
-  int st = allocate(h);
-  if (st == DFB_OK) st = ensure_read_tmp(h);
-  if (st != DFB_OK) return st;
-  const size_t bytes = sizeof(float4) * (size_t)h->cfg.width * h->cfg.height;
-  cudaStream_t s = h->lastStreamSet ? h->lastStream : (cudaStream_t)0;
-  const float* srcs[3] = {sum, comp, m2};
-  float4* dsts[3] = {h->accum, h->comp, h->m2};
-  cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
-    e = cudaMemcpyAsync(h->readTmp, srcs[i], bytes, cudaMemcpyDefault, s);
-    if (e == cudaSuccess)
-      e = dfb::launch_image_to_tiles(h->readTmp, dsts[i], h->cfg.width, h->cfg.height,
-                                     h->cfg.tile_size, s);
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_status(e);
-  h->accumN = frames;
-  h->haveFrame = true;
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h || !sum || !comp || !m2 || frames < 1) return DFB_ERR_INVALID_ARG;
+    if (h->inFrame || !(h->cfg.flags & DFB_FLAG_ACCUMULATE)) return DFB_ERR_STATE;
+    int st = allocate(h);
+    if (st == DFB_OK) st = ensure_read_tmp(h);
+    if (st != DFB_OK) return st;
+    const size_t bytes = sizeof(float4) * (size_t)h->cfg.width * h->cfg.height;
+    cudaStream_t s = h->lastStreamSet ? h->lastStream : (cudaStream_t)0;
+    const float* srcs[3] = {sum, comp, m2};
+    float4* dsts[3] = {h->accum, h->comp, h->m2};
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+      e = cudaMemcpyAsync(h->readTmp, srcs[i], bytes, cudaMemcpyDefault, s);
+      if (e == cudaSuccess)
+        e = dfb::launch_image_to_tiles(h->readTmp, dsts[i], h->cfg.width, h->cfg.height,
+                                       h->cfg.tile_size, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    h->accumN = frames;
+    h->haveFrame = true;
+    return DFB_OK;
+  });
 }
 
 int dfb_convert_tiles(const float* src, void* dst, float* scales, int n_tiles, int tile_pixels,
                       int dtype, void* stream) {
-  if (!src || !dst || n_tiles < 0 || tile_pixels < 1) return DFB_ERR_INVALID_ARG;
-  if (dtype != DFB_F16 && dtype != DFB_BF16 && dtype != DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;
-  if (dtype == DFB_FP8E4M3 && !scales) return DFB_ERR_INVALID_ARG;
-  if (n_tiles == 0) return DFB_OK;
-  return cuda_status(dfb::launch_convert(src, dst, scales, n_tiles, tile_pixels, dtype,
-                                         (cudaStream_t)stream));
+  return guarded([&]() -> int {
+    if (!src || !dst || n_tiles < 0 || tile_pixels < 1) return DFB_ERR_INVALID_ARG;
+    if (dtype != DFB_F16 && dtype != DFB_BF16 && dtype != DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;
+    if (dtype == DFB_FP8E4M3 && !scales) return DFB_ERR_INVALID_ARG;
+    if (n_tiles == 0) return DFB_OK;
+    return cuda_status(dfb::launch_convert(src, dst, scales, n_tiles, tile_pixels, dtype,
+                                           (cudaStream_t)stream));
+  });
 }
 
 int dfb_set_timing(dfb_handle h, int enable) {
-  if (!h) return DFB_ERR_INVALID_ARG;
-  h->timing = enable != 0;
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h) return DFB_ERR_INVALID_ARG;
+    h->timing = enable != 0;
+    return DFB_OK;
+  });
 }
 
 int dfb_read_timing(dfb_handle h, dfb_timing* out, int reset) {
-  if (!h || !out) return DFB_ERR_INVALID_ARG;
-  while (h->tCount) {
-    const int st = harvest_one(h);
-    if (st != DFB_OK) return st;
-  }
-  *out = h->tSum;
-  if (reset) h->tSum = dfb_timing{};
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h || !out) return DFB_ERR_INVALID_ARG;
+    while (h->tCount) {
+      const int st = harvest_one(h);
+      if (st != DFB_OK) return st;
+    }
+    *out = h->tSum;
+    if (reset) h->tSum = dfb_timing{};
+    return DFB_OK;
+  });
 }
 
 int dfb_set_tuning(dfb_handle h, int ring_kb, int ctas_per_sm, int groups) {
-  if (!h || !valid_tuning(ring_kb, ctas_per_sm, groups)) return DFB_ERR_INVALID_ARG;
-  h->tune = dfb::TuneParams{ring_kb, ctas_per_sm, groups};
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h || !valid_tuning(ring_kb, ctas_per_sm, groups)) return DFB_ERR_INVALID_ARG;
+    h->tune = dfb::TuneParams{ring_kb, ctas_per_sm, groups};
+    return DFB_OK;
+  });
 }
 
 int dfb_set_wait_limit(dfb_handle h, double seconds) {
-  if (!h || !(seconds > 0.0) || seconds > 3600.0) return DFB_ERR_INVALID_ARG;
-  h->waitNs = (unsigned long long)(seconds * 1e9);
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h || !(seconds > 0.0) || seconds > 3600.0) return DFB_ERR_INVALID_ARG;
+    h->waitNs = (unsigned long long)(seconds * 1e9);
+    return DFB_OK;
+  });
 }
 
 int dfb_inject_stall(dfb_handle h, int item) {
-  if (!h || item < -1) return DFB_ERR_INVALID_ARG;
-  h->stallItem = item;
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h || item < -1) return DFB_ERR_INVALID_ARG;
+    h->stallItem = item;
+    return DFB_OK;
+  });
 }
 
 }  // extern "C"
@@ -1528,32 +1610,10 @@ void graph_free(dfb_graph_t* g) {
   delete g;
 }
 
-}  // namespace
-
-extern "C" {
-
-int dfb_graph_create(const dfb_handle* hs, int n, dfb_graph* out) {
-  if (!hs || n < 1 || !out) return DFB_ERR_INVALID_ARG;
-  *out = nullptr;
-  for (int i = 0; i < n; ++i) {
-    if (!hs[i]) return DFB_ERR_INVALID_ARG;
-    for (int j = 0; j < i; ++j)
-      if (hs[j] == hs[i]) return DFB_ERR_INVALID_ARG;
-    if (!hs[i]->inFrame) return DFB_ERR_STATE;
-    if (hs[i]->cfg.dtype != hs[0]->cfg.dtype) return DFB_ERR_INVALID_ARG;
-  }
-  for (int i = 0; i < n; ++i) {
-    const int st = check_trees(hs[i]);
-    if (st != DFB_OK) return st;
-  }
-  for (int i = 0; i < n; ++i) {
-    const int st = allocate(hs[i]);
-    if (st != DFB_OK) return st;
-    if (hs[i]->lastStreamSet) cudaEventSynchronize(hs[i]->frameDone);
-    if (hs[i]->hostCopies) cudaEventSynchronize(hs[i]->copyDone);
-  }
-  dfb_graph_t* g = new (std::nothrow) dfb_graph_t();
-  if (!g) return DFB_ERR_OOM;
+// The rest of dfb_graph_create once the graph object exists: record
+// tables, device copies, capture.  Frees `g` on a returned error; an
+// exception (a host vector that cannot grow) is the caller's to handle.
+int graph_build(dfb_graph_t* g, const dfb_handle* hs, int n, dfb_graph* out) {
   g->hs.assign(hs, hs + n);
   g->dtype = hs[0]->cfg.dtype;
   std::vector<FragRec> recs;
@@ -1651,82 +1711,127 @@ int dfb_graph_create(const dfb_handle* hs, int n, dfb_graph* out) {
   return DFB_OK;
 }
 
+
+}  // namespace
+
+extern "C" {
+
+int dfb_graph_create(const dfb_handle* hs, int n, dfb_graph* out) {
+  return guarded([&]() -> int {
+    if (!hs || n < 1 || !out) return DFB_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+      if (!hs[i]) return DFB_ERR_INVALID_ARG;
+      for (int j = 0; j < i; ++j)
+        if (hs[j] == hs[i]) return DFB_ERR_INVALID_ARG;
+      if (!hs[i]->inFrame) return DFB_ERR_STATE;
+      if (hs[i]->cfg.dtype != hs[0]->cfg.dtype) return DFB_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n; ++i) {
+      const int st = check_trees(hs[i]);
+      if (st != DFB_OK) return st;
+    }
+    for (int i = 0; i < n; ++i) {
+      const int st = allocate(hs[i]);
+      if (st != DFB_OK) return st;
+      if (hs[i]->lastStreamSet) cudaEventSynchronize(hs[i]->frameDone);
+      if (hs[i]->hostCopies) cudaEventSynchronize(hs[i]->copyDone);
+    }
+    dfb_graph_t* g = new (std::nothrow) dfb_graph_t();
+    if (!g) return DFB_ERR_OOM;
+    try {
+      return graph_build(g, hs, n, out);
+    } catch (...) {
+      graph_free(g);
+      throw;
+    }
+  });
+}
+
 int dfb_graph_launch(dfb_graph g, void* stream) {
-  if (!g || !g->exec) return DFB_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = cudaGraphLaunch(g->exec, s);
-  if (e == cudaSuccess) e = cudaEventRecord(g->done, s);
-  for (size_t i = 0; i < g->hs.size() && e == cudaSuccess; ++i) {
-    dfb_ctx* h = g->hs[i];
-    e = cudaEventRecord(h->frameDone, s);
-    h->lastStream = s;
-    h->lastStreamSet = true;
-    h->haveFrame = true;
-    h->lastErr = g->err;
-    h->launches += (g->nRec ? 4 : 2) + (g->anyAcc ? 2 : 1) + (g->lng.n ? 1 : 0);
-  }
-  g->launched = true;
-  return cuda_status(e);
+  return guarded([&]() -> int {
+    if (!g || !g->exec) return DFB_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaGraphLaunch(g->exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(g->done, s);
+    for (size_t i = 0; i < g->hs.size() && e == cudaSuccess; ++i) {
+      dfb_ctx* h = g->hs[i];
+      e = cudaEventRecord(h->frameDone, s);
+      h->lastStream = s;
+      h->lastStreamSet = true;
+      h->haveFrame = true;
+      h->lastErr = g->err;
+      h->launches += (g->nRec ? 4 : 2) + (g->anyAcc ? 2 : 1) + (g->lng.n ? 1 : 0);
+    }
+    g->launched = true;
+    return cuda_status(e);
+  });
 }
 
 int dfb_graph_set_tuning(dfb_graph g, int ring_kb, int ctas_per_sm, int groups) {
-  if (!g || !valid_tuning(ring_kb, ctas_per_sm, groups)) return DFB_ERR_INVALID_ARG;
-  if (g->launched) cudaEventSynchronize(g->done);
-  g->tune = dfb::TuneParams{ring_kb, ctas_per_sm, groups};
-  return graph_capture(g);
+  return guarded([&]() -> int {
+    if (!g || !valid_tuning(ring_kb, ctas_per_sm, groups)) return DFB_ERR_INVALID_ARG;
+    if (g->launched) cudaEventSynchronize(g->done);
+    g->tune = dfb::TuneParams{ring_kb, ctas_per_sm, groups};
+    return graph_capture(g);
+  });
 }
 
 int dfb_graph_autotune(dfb_graph g, void* stream, int reps, int* ring_kb, int* ctas_per_sm,
                        int* groups, float* best_ms) {
-  if (!g || reps < 1) return DFB_ERR_INVALID_ARG;
-  // {ring KB, CTAs per SM, groups}; shapes whose ring is too small for the
-  // dtype's largest item fail to launch and are skipped
-  static const int cand[][3] = {{110, 2, 2}, {100, 2, 2}, {110, 2, 1}, {72, 3, 1},
-                                {64, 3, 1}, {220, 1, 2}};
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t a = nullptr, b = nullptr;
-  cudaError_t e = cudaEventCreate(&a);
-  if (e == cudaSuccess) e = cudaEventCreate(&b);
-  float best = 1e30f;
-  dfb::TuneParams bestT = dfb::default_tune(g->dtype);
-  for (const auto& c : cand) {
-    if (e != cudaSuccess) break;
-    if (dfb_graph_set_tuning(g, c[0], c[1], c[2]) != DFB_OK) continue;  // does not fit
-    cudaError_t le = cudaGraphLaunch(g->exec, s);  // warm-up
-    if (le == cudaSuccess) le = cudaEventRecord(a, s);
-    for (int r = 0; r < reps && le == cudaSuccess; ++r) le = cudaGraphLaunch(g->exec, s);
-    if (le == cudaSuccess) le = cudaEventRecord(b, s);
-    if (le == cudaSuccess) le = cudaEventSynchronize(b);
-    float ms = 0.f;
-    if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, a, b);
-    if (le != cudaSuccess) {
-      // a shape the device rejects is skipped; an error that persists is not
-      cudaGetLastError();
-      e = cudaDeviceSynchronize();
-      continue;
+  return guarded([&]() -> int {
+    if (!g || reps < 1) return DFB_ERR_INVALID_ARG;
+    // {ring KB, CTAs per SM, groups}; shapes whose ring is too small for the
+    // dtype's largest item fail to launch and are skipped
+    static const int cand[][3] = {{110, 2, 2}, {100, 2, 2}, {110, 2, 1}, {72, 3, 1},
+                                  {64, 3, 1}, {220, 1, 2}};
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    float best = 1e30f;
+    dfb::TuneParams bestT = dfb::default_tune(g->dtype);
+    for (const auto& c : cand) {
+      if (e != cudaSuccess) break;
+      if (dfb_graph_set_tuning(g, c[0], c[1], c[2]) != DFB_OK) continue;  // does not fit
+      cudaError_t le = cudaGraphLaunch(g->exec, s);  // warm-up
+      if (le == cudaSuccess) le = cudaEventRecord(a, s);
+      for (int r = 0; r < reps && le == cudaSuccess; ++r) le = cudaGraphLaunch(g->exec, s);
+      if (le == cudaSuccess) le = cudaEventRecord(b, s);
+      if (le == cudaSuccess) le = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (le == cudaSuccess) le = cudaEventElapsedTime(&ms, a, b);
+      if (le != cudaSuccess) {
+        // a shape the device rejects is skipped; an error that persists is not
+        cudaGetLastError();
+        e = cudaDeviceSynchronize();
+        continue;
+      }
+      if (ms / reps < best) {
+        best = ms / reps;
+        bestT = dfb::TuneParams{c[0], c[1], c[2]};
+      }
     }
-    if (ms / reps < best) {
-      best = ms / reps;
-      bestT = dfb::TuneParams{c[0], c[1], c[2]};
-    }
-  }
-  if (a) cudaEventDestroy(a);
-  if (b) cudaEventDestroy(b);
-  if (e != cudaSuccess) return cuda_status(e);
-  const int st = dfb_graph_set_tuning(g, bestT.ringKB, bestT.ctasPerSm, bestT.groups);
-  if (st != DFB_OK) return st;
-  for (dfb_ctx* h : g->hs) h->tune = bestT;
-  if (ring_kb) *ring_kb = bestT.ringKB;
-  if (ctas_per_sm) *ctas_per_sm = bestT.ctasPerSm;
-  if (groups) *groups = bestT.groups;
-  if (best_ms) *best_ms = best;
-  return DFB_OK;
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int st = dfb_graph_set_tuning(g, bestT.ringKB, bestT.ctasPerSm, bestT.groups);
+    if (st != DFB_OK) return st;
+    for (dfb_ctx* h : g->hs) h->tune = bestT;
+    if (ring_kb) *ring_kb = bestT.ringKB;
+    if (ctas_per_sm) *ctas_per_sm = bestT.ctasPerSm;
+    if (groups) *groups = bestT.groups;
+    if (best_ms) *best_ms = best;
+    return DFB_OK;
+  });
 }
 
 int dfb_graph_destroy(dfb_graph g) {
-  if (!g) return DFB_OK;
-  graph_free(g);
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!g) return DFB_OK;
+    graph_free(g);
+    return DFB_OK;
+  });
 }
 
 }  // extern "C"
@@ -1765,83 +1870,81 @@ extern "C" {
 int dfb_tileset_create(dfb_handle h, int n, const int* tile_ids, const float* order_keys,
                        const void* const* rgba, const float* const* depth, const float* scales,
                        dfb_tileset* out) {
-  if (!h || n < 0 || !out) return DFB_ERR_INVALID_ARG;
-  *out = nullptr;
-  const int st = validate_arrays(h, n, tile_ids, order_keys, rgba, depth, scales);
-  if (st != DFB_OK) return st;
-  dfb_tileset_t* s = new (std::nothrow) dfb_tileset_t();
-  if (!s) return DFB_ERR_OOM;
-  try {
-    s->width = h->cfg.width;
-    s->height = h->cfg.height;
-    s->tileSize = h->cfg.tile_size;
-    s->dtype = h->cfg.dtype;
-    s->recs.resize((size_t)n);
-    std::vector<int> perTile((size_t)h->nTiles, 0);
-    s->fragmentPixels = build_records(h, n, tile_ids, order_keys, rgba, depth, scales,
-                                      s->recs.data(), perTile.data());
-    for (int t = 0; t < h->nTiles; ++t)
-      if (perTile[t]) {
-        s->tiles.push_back(t);
-        s->counts.push_back(perTile[t]);
-      }
-  } catch (const std::bad_alloc&) {
-    delete s;
-    return DFB_ERR_OOM;
-  }
-  *out = s;
-  return DFB_OK;
+  return guarded([&]() -> int {
+    if (!h || n < 0 || !out) return DFB_ERR_INVALID_ARG;
+    *out = nullptr;
+    const int st = validate_arrays(h, n, tile_ids, order_keys, rgba, depth, scales);
+    if (st != DFB_OK) return st;
+    dfb_tileset_t* s = new (std::nothrow) dfb_tileset_t();
+    if (!s) return DFB_ERR_OOM;
+    try {
+      s->width = h->cfg.width;
+      s->height = h->cfg.height;
+      s->tileSize = h->cfg.tile_size;
+      s->dtype = h->cfg.dtype;
+      s->recs.resize((size_t)n);
+      std::vector<int> perTile((size_t)h->nTiles, 0);
+      s->fragmentPixels = build_records(h, n, tile_ids, order_keys, rgba, depth, scales,
+                                        s->recs.data(), perTile.data());
+      for (int t = 0; t < h->nTiles; ++t)
+        if (perTile[t]) {
+          s->tiles.push_back(t);
+          s->counts.push_back(perTile[t]);
+        }
+    } catch (const std::bad_alloc&) {
+      delete s;
+      return DFB_ERR_OOM;
+    }
+    *out = s;
+    return DFB_OK;
+  });
 }
 
 int dfb_tileset_destroy(dfb_tileset s) {
-  delete s;
-  return DFB_OK;
+  return guarded([&]() -> int {
+    delete s;
+    return DFB_OK;
+  });
 }
 
 int dfb_submit_tileset(dfb_handle h, dfb_tileset s) {
-  if (!h || !s) return DFB_ERR_INVALID_ARG;
-  if (!h->inFrame) return DFB_ERR_STATE;
-  if (!same_geometry(h, s)) return DFB_ERR_INVALID_ARG;
-  try {
+  return guarded([&]() -> int {
+    if (!h || !s) return DFB_ERR_INVALID_ARG;
+    if (!h->inFrame) return DFB_ERR_STATE;
+    if (!same_geometry(h, s)) return DFB_ERR_INVALID_ARG;
     submit_set(h, s);
-  } catch (const std::bad_alloc&) {
-    return DFB_ERR_OOM;
-  }
-  return DFB_OK;
+    return DFB_OK;
+  });
 }
 
 int dfb_run_frames(const dfb_handle* hs, const dfb_tileset* sets, const int* accumulate, int n,
                    void* stream) {
-  if (!hs || !sets || n < 1) return DFB_ERR_INVALID_ARG;
-  for (int i = 0; i < n; ++i) {
-    if (!hs[i] || !sets[i]) return DFB_ERR_INVALID_ARG;
-    if (hs[i]->inFrame) return DFB_ERR_STATE;
-    if (!same_geometry(hs[i], sets[i])) return DFB_ERR_INVALID_ARG;
-    if (hs[i]->cfg.dtype != hs[0]->cfg.dtype) return DFB_ERR_INVALID_ARG;
-  }
-  {
-    std::vector<const dfb_ctx*> sorted(hs, hs + n);
-    std::sort(sorted.begin(), sorted.end());
-    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
-      return DFB_ERR_INVALID_ARG;
-  }
-  {
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;  // as in dfb_end_frames
-    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) cudaGetLastError();
-    else if (cap != cudaStreamCaptureStatusNone) return DFB_ERR_STATE;
-  }
-  for (int i = 0; i < n; ++i) {
-    int st = dfb_begin_frame(hs[i], accumulate ? accumulate[i] : 0);
-    if (st == DFB_OK) {
-      try {
-        submit_set(hs[i], sets[i]);
-      } catch (const std::bad_alloc&) {
-        st = DFB_ERR_OOM;
-      }
+  return guarded([&]() -> int {
+    if (!hs || !sets || n < 1) return DFB_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+      if (!hs[i] || !sets[i]) return DFB_ERR_INVALID_ARG;
+      if (hs[i]->inFrame) return DFB_ERR_STATE;
+      if (!same_geometry(hs[i], sets[i])) return DFB_ERR_INVALID_ARG;
+      if (hs[i]->cfg.dtype != hs[0]->cfg.dtype) return DFB_ERR_INVALID_ARG;
     }
-    if (st != DFB_OK) return st;
-  }
-  return dfb_end_frames(hs, n, stream);
+    {
+      std::vector<const dfb_ctx*> sorted(hs, hs + n);
+      std::sort(sorted.begin(), sorted.end());
+      if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+        return DFB_ERR_INVALID_ARG;
+    }
+    {
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;  // as in dfb_end_frames
+      if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) cudaGetLastError();
+      else if (cap != cudaStreamCaptureStatusNone) return DFB_ERR_STATE;
+    }
+    for (int i = 0; i < n; ++i) {
+      const int st = dfb_begin_frame(hs[i], accumulate ? accumulate[i] : 0);
+      if (st != DFB_OK) return st;
+      submit_set(hs[i], sets[i]);
+    }
+    return dfb_end_frames(hs, n, stream);
+  });
 }
 
 }  // extern "C"
