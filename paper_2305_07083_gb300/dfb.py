@@ -134,14 +134,19 @@ def lib():
 
 
 def _ptr(x):
-    """Address of a buffer: torch tensor, numpy array, ctypes object, int or None."""
+    """Address of a buffer: torch tensor, numpy array, ctypes object, int or None.
+    Arrays must be contiguous: the library reads and writes them densely."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
     if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_contiguous") and not x.is_contiguous():
+            raise ValueError("tensor passed to libdfb must be contiguous")
         return x.data_ptr()
     if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array passed to libdfb must be C-contiguous")
         return x.ctypes.data
     return C.addressof(x)
 

@@ -397,3 +397,20 @@ def test_pixel_curve_validation():
         D.dfb_set_pixel_op(h, D.DFB_PIXELOP_CURVE, 1.0)
     assert e_.value.code == D.DFB_ERR_STATE
     D.dfb_destroy(h)
+
+
+def test_binding_rejects_strided_buffers():
+    """The library reads and writes buffers densely, so the binding refuses a
+    strided view instead of handing out its base address."""
+    import torch
+    a = np.zeros((8, 8, 4), np.float32)
+    assert D._ptr(a) == a.ctypes.data
+    with pytest.raises(ValueError):
+        D._ptr(a[:, ::2])
+    with pytest.raises(ValueError):
+        D._ptr(a.transpose(1, 0, 2))
+    t = torch.zeros((8, 8, 4))
+    assert D._ptr(t) == t.data_ptr()
+    with pytest.raises(ValueError):
+        D._ptr(t[:, ::2])
+    assert D._ptr(None) is None and D._ptr(1234) == 1234
