@@ -39,14 +39,20 @@ def load(path: str = DEFAULT_PATH) -> dict:
 
 
 def store(key: str, shape: dict, path: str = DEFAULT_PATH) -> None:
-    """Add or replace one entry; the file is replaced atomically."""
+    """Add or replace one entry; the file is replaced atomically (two
+    processes storing at once keep one of the two entries)."""
     data = load(path)
     data[key] = {k: shape[k] for k in ("ring_kb", "ctas_per_sm", "groups", "ms") if k in shape}
     os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
     fd, tmp = tempfile.mkstemp(dir=os.path.dirname(path) or ".", suffix=".tmp")
-    with os.fdopen(fd, "w") as f:
-        json.dump(data, f, indent=1, sort_keys=True)
-    os.replace(tmp, path)
+    try:
+        with os.fdopen(fd, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except BaseException:
+        if os.path.exists(tmp):
+            os.unlink(tmp)
+        raise
 
 
 def autotune_cached(graph, key: str, stream=None, reps: int = 3, path: str = DEFAULT_PATH,

@@ -2,6 +2,9 @@
 on a miss or an unusable entry (no GPU: the library calls are faked)."""
 
 import json
+import os
+
+import pytest
 
 from paper_2305_07083_gb300 import dfb as D
 from paper_2305_07083_gb300 import tuning
@@ -56,3 +59,13 @@ def test_corrupt_file_is_ignored(tmp_path):
     got = tuning.autotune_cached("g", key, path=str(path), lib=FakeLib())
     assert got["cached"] is False
     assert key in json.load(open(path))
+
+
+def test_failed_store_leaves_the_file_and_no_temporary(tmp_path):
+    path = str(tmp_path / "t.json")
+    tuning.store("a", {"ring_kb": 110, "ctas_per_sm": 2, "groups": 2, "ms": 1.0}, path)
+    before = open(path).read()
+    with pytest.raises(TypeError):
+        tuning.store("b", {"ring_kb": object(), "ctas_per_sm": 2, "groups": 2}, path)   # not JSON
+    assert open(path).read() == before
+    assert sorted(os.listdir(tmp_path)) == ["t.json"]
