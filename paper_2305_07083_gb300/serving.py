@@ -125,6 +125,22 @@ class ServerStats:
                 "gpu_busy_ms": round(self.gpu_ms, 3)}
 
 
+def admit(queue, n_active: int, used: int, budget: int, max_slots: int, footprint) -> list:
+    """Jobs to admit now, taken from the front of `queue` (arrival order,
+    removed from it): while a slot is free and the job's footprint fits the
+    budget.  A job that does not fit stops the admission (no overtaking);
+    when nothing is active the head job is admitted whatever its size, so a
+    job larger than the budget cannot block the server."""
+    out = []
+    while queue and n_active + len(out) < max_slots:
+        fp = footprint(queue[0])
+        if (n_active or out) and used + fp > budget:
+            break
+        out.append(queue.pop(0))
+        used += fp
+    return out
+
+
 class Server:
     def __init__(self, budget_bytes: int, max_slots: int = 64, dtype: int = D.DFB_F16,
                  stream=None, keep_results: bool = True):
@@ -217,15 +233,11 @@ class Server:
                 break
             while pending and pending[0].arrival <= now:
                 queue.append(pending.pop(0))
-            # admission in arrival order: footprint and slots
-            while queue and len(active) < self.max_slots:
-                fp = queue[0].footprint(self.dtype)
-                if active and used + fp > self.budget:
-                    break
-                job = queue.pop(0)
+            for job in admit(queue, len(active), used, self.budget, self.max_slots,
+                             lambda j: j.footprint(self.dtype)):
                 self._open(job)
                 job.admitted = time.perf_counter() - t0
-                used += fp
+                used += job.footprint(self.dtype)
                 active.append(job)
             st.peak_active = max(st.peak_active, len(active))
             st.peak_footprint = max(st.peak_footprint, used)

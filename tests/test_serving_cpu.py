@@ -32,3 +32,23 @@ def test_job_mix_and_footprint():
     fp16 = acc.footprint(D.DFB_F16)
     assert fp16 == 128 * 128 * 68 + 2 * 4 * 64 * 64 * (8 + 4)
     assert acc.footprint(D.DFB_F32) > fp16
+
+
+def test_admission_order_budget_and_slots():
+    fp = lambda j: j[1]
+    # arrival order, budget 10: 4 + 5 fit, 3 would exceed it and stops the rest
+    q = [("a", 4), ("b", 5), ("c", 3), ("d", 1)]
+    got = S.admit(q, 0, 0, 10, 8, fp)
+    assert [j[0] for j in got] == ["a", "b"] and [j[0] for j in q] == ["c", "d"]
+    # no overtaking: "d" (1) would fit but waits behind "c"
+    assert S.admit(q, 2, 9, 10, 8, fp) == [] and len(q) == 2
+    # slots bound the admission even when the budget does not
+    q = [("x%d" % i, 1) for i in range(6)]
+    assert len(S.admit(q, 3, 0, 100, 5, fp)) == 2 and len(q) == 4
+    # an idle server takes the head job even if it alone exceeds the budget
+    q = [("big", 50), ("small", 1)]
+    got = S.admit(q, 0, 0, 10, 8, fp)
+    assert [j[0] for j in got] == ["big"] and q == [("small", 1)]
+    # ... but not while anything is active
+    q = [("big", 50)]
+    assert S.admit(q, 1, 0, 10, 8, fp) == [] and q == [("big", 50)]
