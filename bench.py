@@ -663,7 +663,7 @@ def main():
     D.dfb_sync(run.h)
 
     # ---- e2e: host buffers through the C ABI, copies inside the timed region ----
-    if not args.no_e2e and rank == 0:
+    if not args.no_e2e:
         host_frames = [fr.cpu().pin_memory() for fr in frames]
         host_depth = depth.cpu().pin_memory()
         out8 = torch.empty((sc.H, sc.W), dtype=torch.int32).pin_memory()
@@ -678,13 +678,15 @@ def main():
 
             def read_back():
                 D.dfb_read_rgba8(hrun.h, out8)
-            ems, _, _, _ = timed(hrun, e_steps, 1, stream, None, None, read_back)
-            e2e_ms[where].append(ems / e_steps)
+            ems, _, _, _ = timed(hrun, e_steps, 1, stream, dist, None, read_back)
+            e2e_ms[where].append(max_over_ranks(ems, dist, dev) / e_steps)   # slowest rank
             hrun.close()
-        e2e = {w: (fpx_frame * N_FRAMES / (float(np.mean(v)) / 1e3), float(np.mean(v)), v)
-               for w, v in e2e_ms.items()}
+        # every rank copies and composites its own replica: whole-job units
+        e2e = {w: (whole_job_value(fpx_frame * N_FRAMES, world, float(np.mean(v))),
+                   float(np.mean(v)), v) for w, v in e2e_ms.items()}
         out["e2e"] = {"value": e2e["borrowed"][0], "unit": UNIT,
-                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": sc.W * sc.H * 4,
+                      "h2d_bytes_per_step": h2d * world,
+                      "d2h_bytes_per_step": sc.W * sc.H * 4 * world,
                       "steps": e_steps, "rounds": 2, "ms_per_step": e2e["borrowed"][1],
                       "ms_per_step_rounds": e2e["borrowed"][2],
                       "path": "dfb_submit_tiles(pinned host pointers, DFB_PTR_HOST_BORROWED: "
