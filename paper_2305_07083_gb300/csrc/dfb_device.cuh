@@ -1,6 +1,8 @@
 // Device helpers shared by the DFB kernels: order-preserving depth keys,
-// storage-format decoders, the front-to-back "over" step, the sRGB pack and
-// the mbarrier / bulk-copy PTX wrappers used by the pipelined composite.
+// storage-format decoders, the front-to-back "over" step, the pixel
+// operations (Sec. 3.1.2: exposure, Reinhard, the user's tone curve), the
+// sRGB pack and the mbarrier / bulk-copy PTX wrappers used by the pipelined
+// composite.
 #pragma once
 
 #include <cuda_bf16.h>
