@@ -414,3 +414,35 @@ def test_binding_rejects_strided_buffers():
     with pytest.raises(ValueError):
         D._ptr(t[:, ::2])
     assert D._ptr(None) is None and D._ptr(1234) == 1234
+
+
+def _header_constants():
+    """Integer constants of include/dfb.h: enumerators and #defines."""
+    with open(os.path.join(ROOT, "include", "dfb.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    vals = {}
+    for name, v in re.findall(r"\b(DFB_[A-Z0-9_]+)\s*=\s*(-?\d+)", text):
+        vals[name] = int(v)
+    for name, v in re.findall(r"#define\s+(DFB_[A-Z0-9_]+)\s+(\d+)u?\b", text):
+        vals[name] = int(v)
+    return vals
+
+
+def test_binding_and_oracle_constants_match_the_header():
+    """The header, the binding and the oracle (which defines its enums on its
+    own) agree on every value they share."""
+    from oracle import dfb_oracle as o
+    hdr = _header_constants()
+    assert len(hdr) >= 30
+    for name, v in hdr.items():
+        assert getattr(D, name) == v, name
+    assert D.DFB_FLAGS_DEFAULT == (hdr["DFB_FLAG_ACCUMULATE"] | hdr["DFB_FLAG_WRITE_COLOR"]
+                                   | hdr["DFB_FLAG_PACK_RGBA8"])
+    pairs = {"BLEND_DEPTH": "DFB_BLEND_DEPTH", "BLEND_ORDERED": "DFB_BLEND_ORDERED",
+             "ZCOMPOSITE": "DFB_ZCOMPOSITE", "AVERAGE": "DFB_AVERAGE",
+             "PIXELOP_NONE": "DFB_PIXELOP_NONE", "PIXELOP_EXPOSURE": "DFB_PIXELOP_EXPOSURE",
+             "PIXELOP_REINHARD": "DFB_PIXELOP_REINHARD", "PIXELOP_CURVE": "DFB_PIXELOP_CURVE",
+             "F32": "DFB_F32", "F16": "DFB_F16", "BF16": "DFB_BF16", "FP8E4M3": "DFB_FP8E4M3"}
+    for ours, theirs in pairs.items():
+        assert getattr(o, ours) == hdr[theirs], ours
