@@ -173,13 +173,14 @@ DFB_API int dfb_create(int width, int height, int tile_size, int mode, dfb_handl
 DFB_API int dfb_create_ex(const dfb_config* cfg, dfb_handle* out);
 
 /* Release the handle and its device memory (synchronises its last frame).
-   A null handle is accepted and ignored. */
+   A null handle is accepted and ignored.  Always returns DFB_OK. */
 DFB_API int dfb_destroy(dfb_handle h);
 
 /* Background colour (unpremultiplied RGB and coverage A): the generation-0
    background tile of Sec. 4.2, blended behind every pixel in the blend modes
    and DFB_AVERAGE and shown by empty tiles in DFB_ZCOMPOSITE.  Default
-   (0,0,0,0). */
+   (0,0,0,0); applies from the next dfb_end_frame.  Errors: INVALID_ARG
+   (null handle, a component not finite). */
 DFB_API int dfb_set_background(dfb_handle h, float r, float g, float b, float a);
 
 /* Pixel operation of the RGBA8 output (enum dfb_pixel_op) with its exposure,
@@ -238,7 +239,8 @@ DFB_API int dfb_submit_tiles(dfb_handle h, int n, const int* tile_ids, const flo
                      const float* scales, int where);
 
 /* Bulk setTile with the tree fields and scales: tiles[0..n) in order, with the
-   same all-or-nothing validation and `where` hint as dfb_submit_tiles. */
+   same all-or-nothing validation and `where` hint as dfb_submit_tiles.
+   Errors: as dfb_submit_tiles (STATE, TILE_RANGE, INVALID_ARG, OOM, CUDA). */
 DFB_API int dfb_submit_tiles_ex(dfb_handle h, int n, const dfb_tile_desc* tiles, int where);
 
 /* End the frame: check every declared dependency tree (INCOMPLETE if a
@@ -311,21 +313,27 @@ DFB_API int dfb_read_accum(dfb_handle h, float* out);
 
 /* Copy the per-pixel sample variance (W*H*4 floats, ddof = 1, 0 after one
    frame) and/or the per-tile variance (tiles floats: mean over in-frame
-   pixels of the RGB variances).  Either pointer may be NULL. */
+   pixels of the RGB variances).  Either pointer may be NULL.  Errors:
+   INVALID_ARG (null handle), STATE (accumulation disabled or no frame yet),
+   OOM, CUDA, TIMEOUT / CHECK (reported by the last frame's launch). */
 DFB_API int dfb_read_variance(dfb_handle h, float* per_pixel, float* per_tile);
 
-/* Copy the sRGB RGBA8 frame, W*H uint32 with bytes R,G,B,A in memory order. */
+/* Copy the sRGB RGBA8 frame, W*H uint32 with bytes R,G,B,A in memory order
+   (host or device `out`; a host copy waits for the frame).  Errors:
+   INVALID_ARG (null), STATE (packing disabled or no frame yet), CUDA,
+   TIMEOUT / CHECK (reported by the last frame's launch). */
 DFB_API int dfb_read_rgba8(dfb_handle h, uint32_t* out);
 
-/* Statistics of the last composited frame. */
+/* Statistics of the last composited frame.  Errors: INVALID_ARG (null). */
 DFB_API int dfb_get_stats(dfb_handle h, dfb_frame_stats* out);
 
-/* Tile grid of the handle. */
+/* Tile grid of the handle.  Errors: INVALID_ARG (null). */
 DFB_API int dfb_get_tiles(dfb_handle h, int* tiles_x, int* tiles_y);
 
 /* Checkpoint of the progressive state: running sum, Kahan compensation and
    M2 (each W*H*4 floats, host or device) and the frame count.  Load restores
-   it so accumulation resumes bit-identically. */
+   it so accumulation resumes bit-identically.  Errors: INVALID_ARG (null
+   pointer), STATE (accumulation disabled or no frame yet), OOM, CUDA. */
 DFB_API int dfb_save_accum(dfb_handle h, float* sum, float* comp, float* m2, int* frames);
 DFB_API int dfb_load_accum(dfb_handle h, const float* sum, const float* comp, const float* m2,
                    int frames);
@@ -403,10 +411,13 @@ typedef struct dfb_graph_t* dfb_graph;
    Errors: INVALID_ARG, STATE, INCOMPLETE, OOM, CUDA. */
 DFB_API int dfb_graph_create(const dfb_handle* hs, int n, dfb_graph* out);
 
-/* Replay the captured work on `stream`. */
+/* Replay the captured work on `stream`.  Errors: INVALID_ARG (null or
+   failed graph), CUDA. */
 DFB_API int dfb_graph_launch(dfb_graph g, void* stream);
 
-/* Re-capture with another composite launch shape (see dfb_set_tuning). */
+/* Re-capture with another composite launch shape (see dfb_set_tuning).
+   Errors: INVALID_ARG (a shape not in the list), CUDA (the shape does not fit
+   the device). */
 DFB_API int dfb_graph_set_tuning(dfb_graph g, int ring_kb, int ctas_per_sm, int groups);
 
 /* Autotuner: time `reps` replays of each candidate launch shape (ring size =
@@ -417,7 +428,8 @@ DFB_API int dfb_graph_set_tuning(dfb_graph g, int ring_kb, int ctas_per_sm, int 
 DFB_API int dfb_graph_autotune(dfb_graph g, void* stream, int reps, int* ring_kb,
                                int* ctas_per_sm, int* groups, float* best_ms);
 
-/* Free the graph and its buffers (waits for its last launch). */
+/* Free the graph and its buffers (waits for its last launch).  A null graph
+   is accepted.  Always returns DFB_OK. */
 DFB_API int dfb_graph_destroy(dfb_graph g);
 
 /* Launch shape of this handle's composite kernel: shared-memory ring size per
