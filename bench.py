@@ -265,6 +265,23 @@ class Runner:
                                self.dptr, None, self.where)
             D.dfb_end_frame(self.h, stream)
 
+    def serial_bucket_ms(self, stream, frames=16):
+        """Device time of the bucketing of one frame when nothing else runs:
+        every frame is waited for before the next one is ended, so its
+        bucketing kernel does not share the GPU with a composite."""
+        D = self.D
+        D.dfb_read_timing(self.h, reset=True)
+        D.dfb_set_timing(self.h, True)
+        for f in range(frames):
+            D.dfb_begin_frame(self.h, 0)
+            D.dfb_submit_tiles(self.h, self.tile_ids, self.keys, self.rptr[f % len(self.rptr)],
+                               self.dptr, None, self.where)
+            D.dfb_end_frame(self.h, stream)
+            D.dfb_sync(self.h)
+        D.dfb_set_timing(self.h, False)
+        tm = D.dfb_read_timing(self.h, reset=True)
+        return tm["bucket_ms"] / max(tm["launches"], 1)
+
     def close(self):
         self.D.dfb_destroy(self.h)
 
@@ -355,7 +372,7 @@ def peaks():
 # ----------------------------------------------------------------------------
 # batched form: 32 mixed frames, FP16, one persistent launch in a CUDA graph
 # ----------------------------------------------------------------------------
-def run_batched(dev, stream, steps, warmup):
+def run_batched(dev, stream, steps, warmup, hbm_peak):
     import torch
     from harness import scenes
     from paper_2305_07083_gb300 import dfb as D
@@ -413,6 +430,13 @@ def run_batched(dev, stream, steps, warmup):
     torch.cuda.synchronize()
     batch_ms = e0.elapsed_time(e1) / steps
     counts = np.concatenate([np.bincount(f["tile_ids"], minlength=1) for f in frames])
+    # algorithmic bytes of one graph launch: every frame's fragment bytes (FP16
+    # RGBA + FP32 depth) and output bytes (FP32 colour + RGBA8)
+    algo = 0
+    for h, _, _, _ in h16:
+        st = D.dfb_get_stats(h)
+        algo += st["fragment_bytes"] + st["state_bytes"]
+    achieved = algo / (batch_ms / 1e3) / 1e9
     D.dfb_graph_destroy(g)
     for h, _, _, _ in h16 + h32:
         D.dfb_destroy(h)
@@ -426,7 +450,38 @@ def run_batched(dev, stream, steps, warmup):
             "launch": "one CUDA graph: bucketing + one persistent composite launch + tile variance",
             "autotune": tune,
             "plain_f32_per_frame": {"value": fpx / (plain_ms / 1e3), "ms_per_step": plain_ms},
-            "speedup_vs_plain_f32": plain_ms / batch_ms}
+            "speedup_vs_plain_f32": plain_ms / batch_ms,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "algorithmic_bytes_per_launch": algo,
+                         "timed": "whole graph launch (bucketing kernel + persistent "
+                                  "composite + re-do kernel), CUDA events on the stream",
+                         "bytes": "12 B per fragment-pixel (FP16 RGBA + FP32 depth) + 20 B "
+                                  "per frame pixel (FP32 colour + RGBA8)"}}
+
+
+# ----------------------------------------------------------------------------
+# bucketing of a 1000-brick frame (the largest frames of the serving form)
+# ----------------------------------------------------------------------------
+def run_bucket_1000(dev, stream):
+    import torch
+    from harness import scenes
+    from paper_2305_07083_gb300 import dfb as D
+    W = H = 2048
+    T = 64
+    cam = scenes.orbit_camera(W, H, 7004)
+    tid, key, rgba, depth = scenes.brick_scene_torch(W, H, T, scenes.brick_grid((10, 10, 10)),
+                                                     cam, 7004, dev)
+    sc = _TileSet(W, H, T, tid, key)
+    run = Runner(sc, [rgba], depth, D.DFB_F32)
+    run.serial_bucket_ms(stream, frames=3)  # warm-up
+    ms = run.serial_bucket_ms(stream, frames=16)
+    run.close()
+    counts = np.bincount(tid, minlength=(W // T) * (H // T))
+    del rgba, depth
+    torch.cuda.empty_cache()
+    return {"workload": "2048x2048, 64x64 tiles, 1000 bricks (10x10x10), seeded orbit camera",
+            "fragments": int(len(tid)), "max_fragments_per_tile": int(counts.max()),
+            "bucket_ms_per_frame": ms}
 
 
 # ----------------------------------------------------------------------------
@@ -478,7 +533,7 @@ def run_image_parallel(dev, stream, steps, warmup, hbm_peak, k=4):
 # ----------------------------------------------------------------------------
 # serving: continuous batching of client jobs
 # ----------------------------------------------------------------------------
-def run_serving(dev, stream, duration_s):
+def run_serving(dev, stream, duration_s, client_gap_s=0.008):
     import torch
     from harness import scenes
     from paper_2305_07083_gb300 import dfb as D
@@ -491,9 +546,9 @@ def run_serving(dev, stream, duration_s):
         return dst
     tpl = scenes.serving_templates(dev, seed=0, convert=to_f16)
     torch.cuda.synchronize()
-    # 4 clients, each with exponential gaps of mean 8 ms: 2 ms between
-    # arrivals overall
-    arrivals = S.poisson_arrivals(4, 0.008, duration_s, seed=0)
+    # 4 clients, each with exponential gaps of mean client_gap_s (8 ms: 2 ms
+    # between arrivals overall)
+    arrivals = S.poisson_arrivals(4, client_gap_s, duration_s, seed=0)
     jobs = S.make_jobs(tpl, arrivals, seed=0, accumulate_frames=64)
     # the clients take each finished frame in place (pinned host buffer);
     # the serving tests keep copies to compare every job with its solo run
@@ -505,7 +560,8 @@ def run_serving(dev, stream, duration_s):
     st = srv.run(jobs, time_limit_s=duration_s + 60.0, trace=True)
     srv.close()
     out = st.summary()
-    out.update({"clients": 4, "mean_arrival_gap_ms": 2.0, "arrival_window_s": duration_s,
+    out.update({"clients": 4, "mean_arrival_gap_ms": 1e3 * client_gap_s / 4,
+                "arrival_window_s": duration_s,
                 "jobs_submitted": len(jobs),
                 "jobs": {"blend": sum(j.kind == "blend" for j in jobs),
                          "accumulate": sum(j.kind == "accumulate" for j in jobs)},
@@ -568,8 +624,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f16", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--serving-seconds", type=float, default=3.0,
+    ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="arrival window of the serving run (0 skips it)")
+    ap.add_argument("--serving-heavy-seconds", type=float, default=3.0,
+                    help="arrival window of the serving run at four times the arrival rate "
+                         "(0 skips it)")
     ap.add_argument("--tune", default=None,
                     help="composite launch shape 'ringKB,ctasPerSm,groups' (default: the library's)")
     ap.add_argument("--frames", type=int, default=N_FRAMES,
@@ -610,6 +669,7 @@ def main():
     sampler = ClockSampler(local) if rank == 0 else None
     ms, tm, clocks, launches = timed(run, args.steps, args.warmup, stream, dist, sampler)
     st = D.dfb_get_stats(run.h)
+    bucket_serial = run.serial_bucket_ms(stream)
     ms = max_over_ranks(ms, dist, dev)
     ms_step = ms / args.steps
     value = whole_job_value(fpx_frame * N_FRAMES * args.steps, world, ms)
@@ -657,7 +717,12 @@ def main():
                      "traffic": ncu_traffic("composite_f32_2048.md"),
                      "kernel": "k_composite<BLEND_DEPTH,F32>",
                      "algorithmic_bytes_per_launch": algo_bytes,
-                     "avg_launch_ms": comp_ms, "bucket_ms_per_frame": tm["bucket_ms"] / max(tm["launches"], 1)},
+                     "avg_launch_ms": comp_ms, "bucket_ms_per_frame": bucket_serial,
+                     "bucket_ms_per_frame_overlapped": tm["bucket_ms"] / max(tm["launches"], 1),
+                     "bucket_note": "bucket_ms_per_frame: the bucketing kernel of one frame run "
+                                    "alone (frames ended one at a time); _overlapped: in the "
+                                    "timed step, where it shares the GPU with the previous "
+                                    "frame's composite and waits for its SMs"},
         "clocks": clocks,
     }
     D.dfb_sync(run.h)
@@ -709,6 +774,32 @@ def main():
             f16.append(dst)
         r16 = Runner(sc, f16, depth, D.DFB_F16, tune=tune)
         ms16, tm16, _, _ = timed(r16, args.steps, args.warmup, stream, dist, None)
+        e2e16 = None
+        if not args.no_e2e:
+            # the same end-to-end path with FP16 host tiles (12 B per
+            # fragment-pixel over the host link instead of 20 B)
+            host16 = [t.cpu().pin_memory() for t in f16]
+            host_depth16 = depth.cpu().pin_memory()
+            out8 = torch.empty((sc.H, sc.W), dtype=torch.int32).pin_memory()
+            e_steps = max(1, min(args.steps, 4))
+            h2d16 = N_FRAMES * (host16[0].numel() * 2 + host_depth16.numel() * 4)
+            rounds = []
+            for _ in range(3):
+                hrun = Runner(sc, host16, host_depth16, D.DFB_F16, where="borrowed")
+
+                def read_back16():
+                    D.dfb_read_rgba8(hrun.h, out8)
+                ems, _, _, _ = timed(hrun, e_steps, 1, stream, dist, None, read_back16)
+                rounds.append(max_over_ranks(ems, dist, dev) / e_steps)
+                hrun.close()
+            med = float(np.median(rounds))
+            e2e16 = {"value": whole_job_value(fpx_frame * N_FRAMES, world, med), "unit": UNIT,
+                     "h2d_bytes_per_step": h2d16 * world,
+                     "d2h_bytes_per_step": sc.W * sc.H * 4 * world, "ms_per_step": med,
+                     "ms_per_step_rounds": rounds,
+                     "path": "FP16 pinned host tiles, DFB_PTR_HOST_BORROWED, dfb_end_frame per "
+                             "frame, dfb_read_rgba8 per step"}
+            del host16, host_depth16
         st16 = D.dfb_get_stats(r16.h)
         c16 = tm16["composite_ms"] / max(tm16["launches"], 1)
         ab16 = st16["fragment_bytes"] + state_avg
@@ -719,7 +810,8 @@ def main():
             "roofline": {"achieved": a16, "frac": a16 / hbm_peak, "avg_launch_ms": c16,
                          "traffic": ncu_traffic("composite_f16_2048.md"),
                          "kernel": "k_composite<BLEND_DEPTH,F16>",
-                         "algorithmic_bytes_per_launch": ab16}}}
+                         "algorithmic_bytes_per_launch": ab16},
+            "e2e": e2e16}}
         r16.close()
         del f16
     run.close()
@@ -728,16 +820,21 @@ def main():
         del frames
         torch.cuda.empty_cache()
         out.setdefault("variants", {})["batched_f16_graph"] = run_batched(
-            dev, stream, max(3, min(args.steps, 20)), args.warmup)
+            dev, stream, max(3, min(args.steps, 20)), args.warmup, hbm_peak)
+    if not args.no_batched and rank == 0:
+        out.setdefault("variants", {})["bucket_1000_bricks"] = run_bucket_1000(dev, stream)
     if not args.no_batched and rank == 0:
         out.setdefault("variants", {})["image_parallel_average"] = run_image_parallel(
             dev, stream, max(3, min(args.steps, 50)), args.warmup, hbm_peak)
     if args.serving_seconds > 0 and rank == 0:
         out.setdefault("variants", {})["serving"] = run_serving(dev, stream, args.serving_seconds)
+    if args.serving_heavy_seconds > 0 and rank == 0:
+        out.setdefault("variants", {})["serving_4x_rate"] = run_serving(
+            dev, stream, args.serving_heavy_seconds, client_gap_s=0.002)
     out["gpu_launches"] = launches
     out["gpu_launches_note"] = ("kernels launched by libdfb.so inside the timed FP32 region "
-                                "(per frame: 4 bucketing, the composite, the per-tile variance "
-                                "sum), counted by the library")
+                                "(per frame: the bucketing kernel, the composite, the per-tile "
+                                "variance sum), counted by the library")
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample ----
     if pool is not None:

@@ -165,7 +165,9 @@ typedef struct dfb_frame_stats {
   int64_t kernel_launches;   /* kernels this handle has launched in total      */
 } dfb_frame_stats;
 
-/* Create a framebuffer with DFB_FLAGS_DEFAULT and FP32 storage.
+/* Create a framebuffer with DFB_FLAGS_DEFAULT and FP32 storage.  Sizes: at
+   most 2^31 pixels, and at most 2^32 pixels in its whole tiles
+   (ceil(W/T) * ceil(H/T) * T * T).
    Errors: INVALID_ARG (sizes, mode, tile size), OOM, CUDA (no device). */
 DFB_API int dfb_create(int width, int height, int tile_size, int mode, dfb_handle* out);
 
@@ -379,14 +381,22 @@ DFB_API int dfb_read_timing(dfb_handle h, dfb_timing* out, int reset);
    fragment tiles and ceil(W/T)*ceil(H/T) <= 16384 tiles; larger requests
    return DFB_ERR_CAPACITY before any GPU work.  The first call on a device
    looks up the array's device address (and uploads the sRGB table) with that
-   device current; make that first call before any stream capture.  All calls
-   share the one array, which keeps the previous call's contents (the call
-   clears what must start at zero): calls whose GPU work overlaps -- on two
-   streams, or from two threads -- race and must be serialised by the caller.
-   The call returns once the host arrays have been copied; the GPU work is
-   then queued on `stream`.  Errors: INVALID_ARG (sizes, NaN key, null or
-   misaligned pointer, outputs not device memory), TILE_RANGE, CAPACITY,
-   CUDA. */
+   device current.  All calls share the one array, which keeps the previous
+   call's contents (the call clears what must start at zero): calls whose GPU
+   work overlaps -- on two streams, or from two threads -- race and must be
+   serialised by the caller.
+   The call is synchronous: it copies the host arrays, queues the work on
+   `stream`, waits for it and returns the device status of the launch, so a
+   return of DFB_OK means the outputs are complete.  It copies from pageable
+   host memory and waits on the stream, so it must never be made on a stream
+   that is being captured into a CUDA graph (refused with DFB_ERR_STATE
+   before the stream is touched).  Errors: INVALID_ARG (sizes, NaN key, null
+   or misaligned pointer, an output or input tile that is not device or
+   managed memory -- for inputs laid out back to back, the first and last
+   tile of each run are checked), TILE_RANGE, CAPACITY, STATE (capturing
+   stream), TIMEOUT (a wait inside the kernels ran out; the outputs are
+   incomplete), CHECK (checked build: a device-side bounds check failed),
+   OOM (host), CUDA. */
 DFB_API int dfb_composite_noalloc(int width, int height, int tile_size, int mode, int dtype,
                                   int n, const int* tile_ids, const float* order_keys,
                                   const void* const* rgba, const float* const* depth,

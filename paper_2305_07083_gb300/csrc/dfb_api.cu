@@ -101,12 +101,13 @@ unsigned long long g_table_devices = 0;  // bit d: table uploaded on device d
 
 // Device buffers of one frame's bucketing (K1) and its launch header.
 struct BucketSet {
-  unsigned char* dStage = nullptr;  // [FrameHeader][FragRec x recCap], uploaded per frame
+  // [FrameHeader][FragRec x records, grouped by tile][tile offsets x nTiles+1],
+  // uploaded per frame
+  unsigned char* dStage = nullptr;
   FragRec* dRecs = nullptr;         // = dStage + kHdrBytes
-  uint32_t* tmp = nullptr;
   FragRec* srecs = nullptr;         // records sorted per tile (bucketing output)
   dfb::TileBlock* blocks = nullptr; // per-tile count/offset/first records
-  int *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
+  int* redo = nullptr;              // re-do list of the composite: [count, units...]
   cudaEvent_t ready = nullptr;      // the bucketing that filled this set has finished
   cudaEvent_t released = nullptr;   // the composite that read this set has finished
   bool used = false;
@@ -138,6 +139,7 @@ struct dfb_ctx {
   std::vector<int> touchedDeeper;
   std::vector<int> fragCount;  // records per tile in the open frame (all generations)
   std::vector<int> longTiles;  // tiles with more than kStageFragments records
+  std::vector<int> tileCursor; // host scratch of the grouping by tile
   bool hostCopies = false;
   int64_t launches = 0;  // kernels launched by this handle
   dfb_frame_stats stats{};
@@ -239,9 +241,32 @@ cudaError_t dalloc(T** p, size_t count) {
 }
 
 // Upload buffer of one frame:
-//   [FrameHeader][FragRec x records][long tiles x L][their item prefix x L+1]
+//   [FrameHeader][FragRec x records, grouped by tile][tile offsets x nTiles+1]
 size_t stage_bytes(const dfb_ctx* h, size_t records) {
-  return kHdrBytes + sizeof(FragRec) * records + sizeof(int) * (2 * (size_t)h->nTiles + 1);
+  return kHdrBytes + sizeof(FragRec) * records + sizeof(int) * ((size_t)h->nTiles + 1);
+}
+
+// Stable counting sort of records by tile: dst[off[t] ..] holds the records of
+// tile t in submission order; off[t] is the exclusive prefix of counts[t] over
+// the tiles and off[nTiles] the number of records.  `tileBase` is added to
+// each record's tile.  This is the routing half of the bucketing: each record
+// lands in its tile's list, as a setTile message lands at the tile's owner.
+void group_by_tile(const FragRec* src, size_t n, const int* counts, int nTiles, int tileBase,
+                   FragRec* dst, int* off, std::vector<int>& cursor) {
+  cursor.resize((size_t)nTiles);
+  int acc = 0;
+  for (int t = 0; t < nTiles; ++t) {
+    off[t] = acc;
+    cursor[t] = acc;
+    acc += counts[t];
+  }
+  off[nTiles] = acc;
+  for (size_t i = 0; i < n; ++i) {
+    FragRec r = src[i];
+    const int t = (int)r.tile;
+    r.tile += (uint32_t)tileBase;
+    dst[cursor[t]++] = r;
+  }
 }
 
 int grow_records(dfb_ctx* h, size_t need) {
@@ -254,17 +279,14 @@ int grow_records(dfb_ctx* h, size_t need) {
   h->recCap = 0;
   for (BucketSet& b : h->sets) {
     cudaFree(b.dStage);
-    cudaFree(b.tmp);
     cudaFree(b.srecs);
     b.dStage = nullptr;
     b.dRecs = nullptr;
-    b.tmp = nullptr;
     b.srecs = nullptr;
   }
   for (BucketSet& b : h->sets) {
     cudaError_t e =
         cudaMalloc(reinterpret_cast<void**>(&b.dStage), stage_bytes(h, cap));
-    if (e == cudaSuccess) e = dalloc(&b.tmp, cap);
     if (e == cudaSuccess) e = dalloc(&b.srecs, cap);
     if (e != cudaSuccess) return cuda_status(e);
     b.dRecs = reinterpret_cast<FragRec*>(b.dStage + kHdrBytes);
@@ -297,8 +319,8 @@ void free_device(dfb_ctx* h) {
   fr(h->tileVar); fr(h->varPartial);
   fr(h->readTmp); fr(h->errFlag);
   for (BucketSet& b : h->sets) {
-    fr(b.counts); fr(b.offsets); fr(b.cursor);
-    fr(b.dStage); fr(b.tmp); fr(b.srecs); fr(b.blocks);
+    fr(b.redo);
+    fr(b.dStage); fr(b.srecs); fr(b.blocks);
     b.dRecs = nullptr;
     if (b.ready) cudaEventDestroy(b.ready);
     if (b.released) cudaEventDestroy(b.released);
@@ -360,9 +382,8 @@ int allocate(dfb_ctx* h) {
   if (e == cudaSuccess) e = cudaMemset(h->tileVar, 0, sizeof(float) * h->nTiles);
   for (BucketSet& b : h->sets) {
     if (e == cudaSuccess) e = dalloc(&b.blocks, h->nTiles);
-    if (e == cudaSuccess) e = dalloc(&b.counts, h->nTiles);
-    if (e == cudaSuccess) e = dalloc(&b.offsets, h->nTiles);
-    if (e == cudaSuccess) e = dalloc(&b.cursor, h->nTiles);
+    // one re-do unit per warp of every work item at most
+    if (e == cudaSuccess) e = dalloc(&b.redo, (size_t)h->nTiles * h->chunks * (dfb::kItemPixels / 32) + 1);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.released, cudaEventDisableTiming);
   }
@@ -588,8 +609,8 @@ dfb::TuneParams tune_of(const dfb_ctx* h) {
   return h->tune.ringKB ? h->tune : dfb::default_tune(h->cfg.dtype);
 }
 
-dfb::LaunchCtl ctl_of(const dfb_ctx* h) {
-  return dfb::LaunchCtl{h->waitNs, h->stallItem, h->errFlag};
+dfb::LaunchCtl ctl_of(const dfb_ctx* h, int* redo) {
+  return dfb::LaunchCtl{h->waitNs, h->stallItem, h->errFlag, redo};
 }
 
 void finish_stats(dfb_ctx* h) {
@@ -656,20 +677,19 @@ int64_t build_records(const dfb_ctx* h, int n, const int* tile_ids, const float*
   return fpx;
 }
 
-// Copy the open frame's records behind the header slot of a pinned staging
-// buffer; returns the slot index and the buffer start.
+// Group the open frame's records by tile behind the header slot of a pinned
+// staging buffer, followed by the tile offsets; returns the slot index and
+// the buffer start.
 int stage_records(dfb_ctx* h, FragRec** out) {
   const int buf = h->hRecBuf;
   h->hRecBuf ^= 1;
   cudaEventSynchronize(h->hRecDone[buf]);  // its previous upload has finished
   int st = grow_staging(h, buf, h->recs.size());
   if (st != DFB_OK) return st;
-  if (!h->recs.empty())
-    memcpy(h->hRecs[buf] + kHdrBytes, h->recs.data(), sizeof(FragRec) * h->recs.size());
-  const size_t nl = h->longTiles.size();
-  int* lt = reinterpret_cast<int*>(h->hRecs[buf] + kHdrBytes + sizeof(FragRec) * h->recs.size());
-  if (nl) memcpy(lt, h->longTiles.data(), sizeof(int) * nl);
-  for (size_t i = 0; i <= nl; ++i) lt[nl + i] = (int)i * h->chunks;
+  const size_t n = h->recs.size();
+  FragRec* dst = reinterpret_cast<FragRec*>(h->hRecs[buf] + kHdrBytes);
+  int* off = reinterpret_cast<int*>(h->hRecs[buf] + kHdrBytes + sizeof(FragRec) * n);
+  group_by_tile(h->recs.data(), n, h->fragCount.data(), h->nTiles, 0, dst, off, h->tileCursor);
   *out = reinterpret_cast<FragRec*>(h->hRecs[buf]);
   return buf;
 }
@@ -725,6 +745,9 @@ int dfb_create_ex(const dfb_config* cfg, dfb_handle* out) {
     if (cfg->width < 1 || cfg->height < 1 || !is_pow2(T) || T < 4 || T > 256)
       return DFB_ERR_INVALID_ARG;
     if ((int64_t)cfg->width * cfg->height > (int64_t)1 << 31) return DFB_ERR_INVALID_ARG;
+    // the kernels index the tile-major state (whole tiles) with 32 bits
+    if ((int64_t)((cfg->width + T - 1) / T) * ((cfg->height + T - 1) / T) * T * T > (int64_t)1 << 32)
+      return DFB_ERR_INVALID_ARG;
     if (cfg->mode < DFB_BLEND_DEPTH || cfg->mode > DFB_AVERAGE) return DFB_ERR_INVALID_ARG;
     if (cfg->dtype < DFB_F32 || cfg->dtype > DFB_FP8E4M3) return DFB_ERR_INVALID_ARG;
     if (cfg->flags & ~(DFB_FLAG_ACCUMULATE | DFB_FLAG_WRITE_COLOR | DFB_FLAG_PACK_RGBA8 |
@@ -965,15 +988,17 @@ struct BatchRes {
   // Resources of one multi-frame launch; each device has two, used by
   // alternate launches, so the bucketing of the next batch (on a side
   // stream) overlaps the composite of the current one.
-  FragRec* dRecs = nullptr;
-  uint32_t* tmp = nullptr;
+  FragRec* dRecs = nullptr;       // records grouped by global tile
   FragRec* srecs = nullptr;
   size_t recCap = 0;
-  int *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
   dfb::TileBlock* blocks = nullptr;
-  int* dLong = nullptr;  // long tiles of the launch (global ids), then their item prefix
-  int* hLong = nullptr;
+  int* dOff = nullptr;            // tile offsets of dRecs (tiles + 1)
+  int* hOff = nullptr;
   size_t tileCap = 0;
+  int* redo = nullptr;            // re-do list of the composite: [count, units...]
+  size_t redoCap = 0;
+  std::vector<int> counts;        // records per global tile (host)
+  std::vector<int> cursor;        // host scratch of the grouping
   FrameArgs* dFrames = nullptr;
   int* dItemBase = nullptr;
   size_t frameCap = 0;
@@ -994,7 +1019,7 @@ struct BatchDev {
 std::mutex g_batch_mu;
 BatchDev g_batch[64];
 
-int batch_reserve(BatchRes& b, size_t nRec, size_t nTiles, size_t nFrames) {
+int batch_reserve(BatchRes& b, size_t nRec, size_t nTiles, size_t nFrames, size_t redoUnits) {
   cudaError_t e = cudaSuccess;
   if (!b.ready) {
     e = cudaEventCreateWithFlags(&b.ready, cudaEventDisableTiming);
@@ -1007,10 +1032,9 @@ int batch_reserve(BatchRes& b, size_t nRec, size_t nTiles, size_t nFrames) {
   if (nRec > b.recCap) {
     size_t cap = b.recCap ? b.recCap : 4096;
     while (cap < nRec) cap *= 2;
-    cudaFree(b.dRecs); cudaFree(b.tmp); cudaFree(b.srecs); cudaFreeHost(b.hRecs);
-    b.dRecs = nullptr; b.tmp = nullptr; b.srecs = nullptr; b.hRecs = nullptr; b.recCap = 0;
+    cudaFree(b.dRecs); cudaFree(b.srecs); cudaFreeHost(b.hRecs);
+    b.dRecs = nullptr; b.srecs = nullptr; b.hRecs = nullptr; b.recCap = 0;
     e = dalloc(&b.dRecs, cap);
-    if (e == cudaSuccess) e = dalloc(&b.tmp, cap);
     if (e == cudaSuccess) e = dalloc(&b.srecs, cap);
     if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&b.hRecs), sizeof(FragRec) * cap);
     if (e != cudaSuccess) return cuda_status(e);
@@ -1019,19 +1043,24 @@ int batch_reserve(BatchRes& b, size_t nRec, size_t nTiles, size_t nFrames) {
   if (nTiles > b.tileCap) {
     size_t cap = b.tileCap ? b.tileCap : 4096;
     while (cap < nTiles) cap *= 2;
-    cudaFree(b.counts); cudaFree(b.offsets); cudaFree(b.cursor); cudaFree(b.blocks);
-    cudaFree(b.dLong); cudaFreeHost(b.hLong);
-    b.counts = b.offsets = b.cursor = nullptr; b.blocks = nullptr; b.tileCap = 0;
-    b.dLong = b.hLong = nullptr;
-    e = dalloc(&b.counts, cap);
-    if (e == cudaSuccess) e = dalloc(&b.offsets, cap);
-    if (e == cudaSuccess) e = dalloc(&b.cursor, cap);
-    if (e == cudaSuccess) e = dalloc(&b.blocks, cap);
-    if (e == cudaSuccess) e = dalloc(&b.dLong, 2 * cap + 1);
+    cudaFree(b.blocks); cudaFree(b.dOff); cudaFreeHost(b.hOff);
+    b.blocks = nullptr; b.dOff = b.hOff = nullptr; b.tileCap = 0;
+    e = dalloc(&b.blocks, cap);
+    if (e == cudaSuccess) e = dalloc(&b.dOff, cap + 1);
     if (e == cudaSuccess)
-      e = cudaMallocHost(reinterpret_cast<void**>(&b.hLong), sizeof(int) * (2 * cap + 1));
+      e = cudaMallocHost(reinterpret_cast<void**>(&b.hOff), sizeof(int) * (cap + 1));
     if (e != cudaSuccess) return cuda_status(e);
     b.tileCap = cap;
+  }
+  if (redoUnits + 1 > b.redoCap) {
+    size_t cap = b.redoCap ? b.redoCap : 4096;
+    while (cap < redoUnits + 1) cap *= 2;
+    cudaFree(b.redo);
+    b.redo = nullptr;
+    b.redoCap = 0;
+    e = dalloc(&b.redo, cap);
+    if (e != cudaSuccess) return cuda_status(e);
+    b.redoCap = cap;
   }
   if (nFrames > b.frameCap) {
     size_t cap = b.frameCap ? b.frameCap : 64;
@@ -1113,11 +1142,10 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
   const int items = hdr->itemBase[1];
   FrameArgs* dFa = reinterpret_cast<FrameArgs*>(b.dStage);
   const int* dItemBase = reinterpret_cast<const int*>(b.dStage + offsetof(FrameHeader, itemBase));
-  const int nLong = (int)h->longTiles.size();
+  const int* dTileOff = reinterpret_cast<const int*>(b.dStage + kHdrBytes + sizeof(FragRec) * n);
+  // only BLEND_DEPTH items can need the exact re-do kernel
+  const int nLong = h->cfg.mode == DFB_BLEND_DEPTH ? (int)h->longTiles.size() : 0;
   dfb::LongList lng;
-  lng.tiles = reinterpret_cast<const int*>(b.dStage + kHdrBytes + sizeof(FragRec) * n);
-  lng.base = lng.tiles + nLong;
-  lng.n = nLong;
   lng.items = nLong * h->chunks;
   for (int t : h->longTiles) lng.maxFragments = std::max(lng.maxFragments, h->fragCount[t]);
   // The bucketing reads only library-owned buffers, so it runs on the side
@@ -1128,15 +1156,12 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
   if (h->lastStreamSet && h->lastStream != s) e = cudaStreamWaitEvent(s, h->frameDone, 0);
   if (e == cudaSuccess && b.used) e = cudaStreamWaitEvent(bs, b.released, 0);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b.dStage, staged,
-                        kHdrBytes + sizeof(FragRec) * n + sizeof(int) * (2 * nLong + 1),
-                        cudaMemcpyHostToDevice, bs);
+    e = cudaMemcpyAsync(b.dStage, staged, stage_bytes(h, n), cudaMemcpyHostToDevice, bs);
   if (e == cudaSuccess) e = cudaEventRecord(h->hRecDone[buf], bs);
   cudaEvent_t* ev = timing_slot(h);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], bs);
   if (e == cudaSuccess)
-    e = dfb::launch_bucket(b.dRecs, (int)n, h->nTiles, b.counts, b.offsets, b.cursor, b.tmp,
-                           b.srecs, b.blocks, bs);
+    e = dfb::launch_bucket(b.dRecs, dTileOff, h->nTiles, b.srecs, b.blocks, b.redo, bs);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], bs);
   if (e == cudaSuccess) e = cudaEventRecord(b.ready, bs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b.ready, 0);
@@ -1145,12 +1170,12 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
   if (e == cudaSuccess)
     e = dfb::launch_composite(dFa, dItemBase, 1, items, h->nTiles,
                               (h->cfg.flags & DFB_FLAG_ACCUMULATE) != 0, h->cfg.dtype, tune_of(h),
-                              ctl_of(h), lng, s);
+                              ctl_of(h, b.redo), lng, s);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
   if (e == cudaSuccess) e = cudaEventRecord(b.released, s);
   if (e == cudaSuccess) e = cudaEventRecord(h->frameDone, s);
   b.used = true;
-  h->launches += (n ? 4 : 2) + ((h->cfg.flags & DFB_FLAG_ACCUMULATE) ? 2 : 1) + (nLong ? 1 : 0);
+  h->launches += 1 + ((h->cfg.flags & DFB_FLAG_ACCUMULATE) ? 2 : 1) + (nLong ? 1 : 0);
   h->lastErr = h->errFlag;
   h->stallItem = -1;
   return cuda_status(e);
@@ -1167,19 +1192,37 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
   }
   BatchRes& b = bd.sets[bd.idx];
   bd.idx ^= 1;
-  size_t nRec = 0, nTiles = 0;
+  size_t nRec = 0, nTiles = 0, nItems = 0;
   for (int i = 0; i < n; ++i) {
     nRec += hs[i]->recs.size();
     nTiles += (size_t)hs[i]->nTiles;
+    nItems += (size_t)hs[i]->nTiles * hs[i]->chunks;
   }
-  int st = batch_reserve(b, nRec, nTiles, (size_t)n);
+  int st = batch_reserve(b, nRec, nTiles, (size_t)n, nItems * (dfb::kItemPixels / 32));
   if (st != DFB_OK) return st;
   cudaError_t e = cudaSuccess;
-  size_t r = 0;
-  int tileBase = 0, items = 0, nLong = 0, maxLong = 0;
-  std::vector<int> longChunks;
+  int tileBase = 0, items = 0;
+  dfb::LongList lng;
   const int dtype = hs[0]->cfg.dtype;
   bool anyAcc = false;
+  // per-global-tile counts, then every frame's records grouped by global tile
+  b.counts.resize(nTiles);
+  for (int i = 0; i < n; ++i) {
+    const dfb_ctx* h = hs[i];
+    std::copy(h->fragCount.begin(), h->fragCount.end(), b.counts.begin() + tileBase);
+    tileBase += h->nTiles;
+  }
+  b.cursor.resize(nTiles);
+  {
+    int acc = 0;
+    for (size_t t = 0; t < nTiles; ++t) {
+      b.hOff[t] = acc;
+      b.cursor[t] = acc;
+      acc += b.counts[t];
+    }
+    b.hOff[nTiles] = acc;
+  }
+  tileBase = 0;
   for (int i = 0; i < n; ++i) {
     dfb_ctx* h = hs[i];
     anyAcc |= (h->cfg.flags & DFB_FLAG_ACCUMULATE) != 0;
@@ -1187,13 +1230,10 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
       FragRec g = fr;
       g.tile += (uint32_t)tileBase;
       g.frame = (uint32_t)i;
-      b.hRecs[r++] = g;
+      b.hRecs[b.cursor[g.tile]++] = g;
     }
-    for (int t : h->longTiles) {
-      b.hLong[nLong++] = tileBase + t;
-      longChunks.push_back(h->chunks);
-      maxLong = std::max(maxLong, h->fragCount[t]);
-    }
+    if (h->cfg.mode == DFB_BLEND_DEPTH) lng.items += (int)h->longTiles.size() * h->chunks;
+    for (int t : h->longTiles) lng.maxFragments = std::max(lng.maxFragments, h->fragCount[t]);
     fill_frame_args(h, b.hFrames[i], tileBase, b.srecs, b.blocks);
     b.hItemBase[i] = items;
     items += h->nTiles * b.hFrames[i].chunks;
@@ -1210,39 +1250,27 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
   if (e == cudaSuccess && nRec)
     e = cudaMemcpyAsync(b.dRecs, b.hRecs, sizeof(FragRec) * nRec, cudaMemcpyHostToDevice, bs);
   if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b.dOff, b.hOff, sizeof(int) * (nTiles + 1), cudaMemcpyHostToDevice, bs);
+  if (e == cudaSuccess)
     e = cudaMemcpyAsync(b.dFrames, b.hFrames, sizeof(FrameArgs) * n, cudaMemcpyHostToDevice, bs);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b.dItemBase, b.hItemBase, sizeof(int) * (n + 1), cudaMemcpyHostToDevice,
                         bs);
-  dfb::LongList lng;
-  lng.n = nLong;
-  lng.maxFragments = maxLong;
-  lng.tiles = b.dLong;
-  lng.base = b.dLong + nLong;
-  for (int i = 0; i < nLong; ++i) {
-    b.hLong[nLong + i] = lng.items;
-    lng.items += longChunks[i];
-  }
-  b.hLong[2 * nLong] = lng.items;
-  if (e == cudaSuccess && nLong)
-    e = cudaMemcpyAsync(b.dLong, b.hLong, sizeof(int) * (2 * nLong + 1), cudaMemcpyHostToDevice,
-                        bs);
   cudaEvent_t* ev = timing_slot(hs[0]);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], bs);
   if (e == cudaSuccess)
-    e = dfb::launch_bucket(b.dRecs, (int)nRec, (int)nTiles, b.counts, b.offsets, b.cursor, b.tmp,
-                           b.srecs, b.blocks, bs);
+    e = dfb::launch_bucket(b.dRecs, b.dOff, (int)nTiles, b.srecs, b.blocks, b.redo, bs);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], bs);
   if (e == cudaSuccess) e = cudaEventRecord(b.ready, bs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b.ready, 0);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
   if (e == cudaSuccess)
     e = dfb::launch_composite(b.dFrames, b.dItemBase, n, items, tileBase, anyAcc, dtype,
-                              tune_of(hs[0]), ctl_of(hs[0]), lng, s);
+                              tune_of(hs[0]), ctl_of(hs[0], b.redo), lng, s);
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
   if (e == cudaSuccess) e = cudaEventRecord(b.released, s);
   b.used = true;
-  hs[0]->launches += (nRec ? 4 : 2) + (anyAcc ? 2 : 1) + (nLong ? 1 : 0);
+  hs[0]->launches += 1 + (anyAcc ? 2 : 1) + (lng.items ? 1 : 0);
   hs[0]->stallItem = -1;
   for (int i = 0; i < n && e == cudaSuccess; ++i) {
     e = cudaEventRecord(hs[i]->frameDone, s);
@@ -1547,14 +1575,13 @@ struct dfb_graph_t {
   int dtype = 0;
   bool anyAcc = false;
   int nRec = 0, nTiles = 0, items = 0;
-  FragRec* dRecs = nullptr;
-  uint32_t* tmp = nullptr;
+  FragRec* dRecs = nullptr;        // records grouped by global tile
+  int* dOff = nullptr;             // their tile offsets (nTiles + 1)
   FragRec* srecs = nullptr;
   dfb::TileBlock* blocks = nullptr;
-  int *counts = nullptr, *offsets = nullptr, *cursor = nullptr;
+  int* redo = nullptr;             // re-do list of the composite: [count, units...]
   FrameArgs* dFrames = nullptr;
   int* dItemBase = nullptr;
-  int* dLong = nullptr;  // long tiles (global ids), then their item prefix
   dfb::LongList lng;
   unsigned* err = nullptr;
   dfb::TuneParams tune{0, 0, 0};
@@ -1579,19 +1606,17 @@ int graph_capture(dfb_graph_t* g) {
   graph_release_capture(g);
   const dfb::TuneParams tune = g->tune.ringKB ? g->tune : dfb::default_tune(g->dtype);
   // per-device launch set-up happens outside the capture (no work is enqueued)
+  const dfb::LaunchCtl ctl{2000000000ull, -1, g->err, g->redo};
   cudaError_t e = dfb::launch_composite(g->dFrames, g->dItemBase, 1, 0, 0, false, g->dtype, tune,
-                                        dfb::LaunchCtl{2000000000ull, -1, g->err},
-                                        dfb::LongList{}, g->capStream);
+                                        ctl, dfb::LongList{}, g->capStream);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaStreamBeginCapture(g->capStream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_status(e);
-  cudaError_t le = dfb::launch_bucket(g->dRecs, g->nRec, g->nTiles, g->counts, g->offsets,
-                                      g->cursor, g->tmp, g->srecs, g->blocks, g->capStream);
+  cudaError_t le = dfb::launch_bucket(g->dRecs, g->dOff, g->nTiles, g->srecs, g->blocks, g->redo,
+                                      g->capStream);
   if (le == cudaSuccess)
     le = dfb::launch_composite(g->dFrames, g->dItemBase, (int)g->hs.size(), g->items, g->nTiles,
-                               g->anyAcc, g->dtype, tune,
-                               dfb::LaunchCtl{2000000000ull, -1, g->err}, g->lng,
-                               g->capStream);
+                               g->anyAcc, g->dtype, tune, ctl, g->lng, g->capStream);
   e = cudaStreamEndCapture(g->capStream, &g->graph);
   if (le != cudaSuccess) return cuda_status(le);
   if (e != cudaSuccess) return cuda_status(e);
@@ -1602,9 +1627,9 @@ int graph_capture(dfb_graph_t* g) {
 void graph_free(dfb_graph_t* g) {
   if (g->launched && g->done) cudaEventSynchronize(g->done);
   graph_release_capture(g);
-  cudaFree(g->dRecs); cudaFree(g->tmp); cudaFree(g->srecs); cudaFree(g->blocks);
-  cudaFree(g->counts); cudaFree(g->offsets); cudaFree(g->cursor);
-  cudaFree(g->dFrames); cudaFree(g->dItemBase); cudaFree(g->dLong); cudaFree(g->err);
+  cudaFree(g->dRecs); cudaFree(g->dOff); cudaFree(g->srecs); cudaFree(g->blocks);
+  cudaFree(g->redo);
+  cudaFree(g->dFrames); cudaFree(g->dItemBase); cudaFree(g->err);
   if (g->capStream) cudaStreamDestroy(g->capStream);
   if (g->done) cudaEventDestroy(g->done);
   delete g;
@@ -1616,53 +1641,53 @@ void graph_free(dfb_graph_t* g) {
 int graph_build(dfb_graph_t* g, const dfb_handle* hs, int n, dfb_graph* out) {
   g->hs.assign(hs, hs + n);
   g->dtype = hs[0]->cfg.dtype;
-  std::vector<FragRec> recs;
   std::vector<FrameArgs> fa((size_t)n);
   std::vector<int> itemBase((size_t)n + 1);
-  std::vector<int> longs, longChunks;
-  int tileBase = 0, items = 0;
+  std::vector<int> counts;  // records per global tile
+  int tileBase = 0, items = 0, nRec = 0;
   for (int i = 0; i < n; ++i) {
     dfb_ctx* h = hs[i];
     g->anyAcc |= (h->cfg.flags & DFB_FLAG_ACCUMULATE) != 0;
-    for (int t : h->longTiles) {
-      longs.push_back(tileBase + t);
-      longChunks.push_back(h->chunks);
-      g->lng.maxFragments = std::max(g->lng.maxFragments, h->fragCount[t]);
+    if (h->cfg.mode == DFB_BLEND_DEPTH) g->lng.items += (int)h->longTiles.size() * h->chunks;
+    for (int t : h->longTiles) g->lng.maxFragments = std::max(g->lng.maxFragments, h->fragCount[t]);
+    counts.insert(counts.end(), h->fragCount.begin(), h->fragCount.end());
+    nRec += (int)h->recs.size();
+    items += h->nTiles * h->chunks;
+    tileBase += h->nTiles;
+  }
+  // the records of every frame, grouped by global tile (submission order kept)
+  std::vector<FragRec> recs((size_t)nRec);
+  std::vector<int> off((size_t)tileBase + 1), cursor((size_t)tileBase);
+  {
+    int acc = 0;
+    for (int t = 0; t < tileBase; ++t) {
+      off[t] = acc;
+      cursor[t] = acc;
+      acc += counts[t];
     }
-    for (const FragRec& fr : h->recs) {
+    off[tileBase] = acc;
+  }
+  tileBase = 0;
+  for (int i = 0; i < n; ++i) {
+    for (const FragRec& fr : hs[i]->recs) {
       FragRec r = fr;
       r.tile += (uint32_t)tileBase;
       r.frame = (uint32_t)i;
-      recs.push_back(r);
+      recs[cursor[r.tile]++] = r;
     }
-    itemBase[i] = items;
-    tileBase += h->nTiles;
+    tileBase += hs[i]->nTiles;
   }
-  g->nRec = (int)recs.size();
+  g->nRec = nRec;
   g->nTiles = tileBase;
   cudaError_t e = cudaSuccess;
   const size_t rc = recs.empty() ? 1 : recs.size();
   e = dalloc(&g->dRecs, rc);
-  if (e == cudaSuccess) e = dalloc(&g->tmp, rc);
+  if (e == cudaSuccess) e = dalloc(&g->dOff, (size_t)tileBase + 1);
   if (e == cudaSuccess) e = dalloc(&g->srecs, rc);
   if (e == cudaSuccess) e = dalloc(&g->blocks, (size_t)tileBase);
-  if (e == cudaSuccess) e = dalloc(&g->counts, (size_t)tileBase);
-  if (e == cudaSuccess) e = dalloc(&g->offsets, (size_t)tileBase);
-  if (e == cudaSuccess) e = dalloc(&g->cursor, (size_t)tileBase);
+  if (e == cudaSuccess) e = dalloc(&g->redo, (size_t)items * (dfb::kItemPixels / 32) + 1);
   if (e == cudaSuccess) e = dalloc(&g->dFrames, (size_t)n);
   if (e == cudaSuccess) e = dalloc(&g->dItemBase, (size_t)n + 1);
-  const size_t nl = longs.size();
-  {
-    int acc = 0;
-    for (size_t i = 0; i < nl; ++i) {
-      longs.push_back(acc);  // item prefix after the tile ids
-      acc += longChunks[i];
-    }
-    longs.push_back(acc);
-    g->lng.n = (int)nl;
-    g->lng.items = acc;
-  }
-  if (e == cudaSuccess) e = dalloc(&g->dLong, longs.size());
   if (e == cudaSuccess) e = dalloc(&g->err, 1);
   if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
@@ -1670,6 +1695,7 @@ int graph_build(dfb_graph_t* g, const dfb_handle* hs, int n, dfb_graph* out) {
     return cuda_status(e);
   }
   tileBase = 0;
+  items = 0;
   for (int i = 0; i < n; ++i) {
     fill_frame_args(hs[i], fa[i], tileBase, g->srecs, g->blocks);
     itemBase[i] = items;
@@ -1681,13 +1707,11 @@ int graph_build(dfb_graph_t* g, const dfb_handle* hs, int n, dfb_graph* out) {
   if (!recs.empty())
     e = cudaMemcpy(g->dRecs, recs.data(), sizeof(FragRec) * recs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
+    e = cudaMemcpy(g->dOff, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
     e = cudaMemcpy(g->dFrames, fa.data(), sizeof(FrameArgs) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(g->dItemBase, itemBase.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
-  g->lng.tiles = g->dLong;
-  g->lng.base = g->dLong + nl;
-  if (e == cudaSuccess)
-    e = cudaMemcpy(g->dLong, longs.data(), sizeof(int) * longs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->capStream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -1761,7 +1785,7 @@ int dfb_graph_launch(dfb_graph g, void* stream) {
       h->lastStreamSet = true;
       h->haveFrame = true;
       h->lastErr = g->err;
-      h->launches += (g->nRec ? 4 : 2) + (g->anyAcc ? 2 : 1) + (g->lng.n ? 1 : 0);
+      h->launches += 1 + (g->anyAcc ? 2 : 1) + (g->lng.items ? 1 : 0);
     }
     g->launched = true;
     return cuda_status(e);

@@ -25,18 +25,21 @@
 //     copy kMetaQ items ahead, so locating an item's fragments needs no
 //     dependent global loads.  It then issues one-dimensional bulk copies
 //     (cp.async.bulk, the TMA engine) of each fragment's depth slab and RGBA
-//     slab straight into a shared-memory ring, completing on the item's
-//     mbarrier.  Items take only the ring bytes they need (n fragments x slab
-//     size), so the ring holds as many items in flight as their sizes allow,
-//     up to kSlots.
+//     slab straight into a shared-memory ring, completing on the fill's
+//     mbarrier.  Fills take only the ring bytes they need (n fragments x slab
+//     size), so the ring holds as many fills in flight as their sizes allow,
+//     up to kSlots (each consumer group owns kSlots / G of them).
+//   * An item of at most kStageFragments fragments is one fill.  A longer
+//     one streams through the ring in fills of kFill fragments; its
+//     consumers carry the per-pixel blend across the fills (BLEND_DEPTH
+//     speculatively in list order), so a long list costs the same bytes per
+//     fragment as a short one.  The rare 32-pixel units whose depths turn
+//     out to be out of list order are redone exactly by k_composite_redo.
 //   * The accumulation state (sum, M2, Kahan compensation) is stored
 //     tile-major, so an item's state is one contiguous run per buffer that
-//     the producer streams into the same ring space; consumers read every
+//     the producer streams into the item's last fill; consumers read every
 //     input from shared memory, sort and blend, take the state into
 //     registers and release the ring space before the epilogue.
-//   * Items of tiles with more than kStageFragments fragments get an empty
-//     slot here and are composited afterwards by k_composite_long, which
-//     stages their depth slabs in shared memory and streams their RGBA.
 //   * The epilogue writes one variance partial per warp with plain stores;
 //     a small second kernel sums each tile's partials in a fixed order.
 // Every wait is bounded in time; on expiry the kernel sets an error bit,
@@ -78,11 +81,17 @@ constexpr int kSlots = 16;               // items in flight at most
 constexpr int kMetaQ = 8;                // tile blocks fetched ahead
 constexpr uint32_t kWindowBytes = kSortWindow * kP * 8;
 
+// Descriptor of one fill of the ring: up to kN fragments of one work item
+// (all of them for an item of at most kN fragments, else kFill), plus the
+// item's state rows in its last fill.
 struct ItemMeta {
-  int n, staged;
-  uint32_t start;      // byte offset of the item's data in the ring
-  uint32_t stateOff;   // offset of the item's state rows from `start`
-  unsigned long long end;  // producer's head position after this item
+  int n;               // fragments in this fill
+  int total;           // fragments of the item
+  int first;           // list index of the fill's first fragment
+  int pad;
+  uint32_t start;      // byte offset of the fill's data in the ring
+  uint32_t stateOff;   // offset of the state rows from `start` (last fill)
+  unsigned long long end;  // producer's head position after this fill
   const void* rgba[kN];
   float scale[kN];
 };
@@ -99,11 +108,12 @@ constexpr int kHeader = kOffQLoc + 128;
 static_assert((2 * kSlots + kMetaQ) * 8 <= 512, "barrier space");
 static_assert(kOffQueue % 128 == 0 && kHeader % 128 == 0, "alignment");
 static_assert(kMetaQ * 16 <= 128, "queue locations");
+static_assert(32 % kFill == 0 && kFill <= kN, "fills never straddle a window of 32 records");
 
 template <int DT>
 struct Bytes {
   static constexpr int px = PxBytes<DT>::value;
-  // largest item the ring must hold: kN fragments plus three rows of
+  // largest fill the ring must hold: kN fragments plus three rows of
   // framebuffer state (sum, M2, Kahan compensation)
   static constexpr uint32_t maxItem = (uint32_t)kN * kP * (4 + px) + 3u * kP * 16u;
 };
@@ -170,16 +180,26 @@ __device__ __forceinline__ ItemLoc locate(const FrameArgs* frames, const int* it
 // ---------------------------------------------------------------------------
 // producer warp
 // ---------------------------------------------------------------------------
-template <int DT>
+// Fills of the ring.  Consumer group g owns the slots g*S .. g*S+S-1 (S =
+// kSlots / G) and takes its items' fills from them in order.  Ring bytes are
+// reclaimed in the global order of the fills; a fill may reuse a slot once
+// the slot's previous fill has been released.
+template <int DT, int G>
 __device__ void producer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                          int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
                          uint32_t ringBytes, ItemMeta* metas, TileBlock* queue, int4* qLoc,
                          uint64_t* fullB, uint64_t* emptyB, uint64_t* queueB,
                          volatile int* abort) {
   constexpr int px = Bytes<DT>::px;
+  constexpr int S = kSlots / G;
   const int lane = threadIdx.x & 31;
   unsigned long long head = 0, tail = 0;  // monotonic ring positions
-  int tailItem = 0;                       // oldest item not known to be released
+  int curFill = 0, tailFill = 0;          // fills issued / reclaimed (global order)
+  int gf0 = 0, gf1 = 0, gf2 = 0;          // fills issued per consumer group
+  // lane-distributed tables: lane e < kSlots holds the slot and the parity
+  // of outstanding fill e (mod kSlots); lane s < kSlots holds the global
+  // index of the last fill of slot s
+  int fifoSlot = 0, fifoPar = 0, slotFill = -1;
   uint32_t armed = 0, armedPar = 0;       // per ring slot: armed / parity of last arm
   uint32_t qArmed = 0, qPar = 0;          // per queue slot
   // tile block of local item kk -> queue slot kk % kMetaQ (lane 0)
@@ -201,97 +221,123 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
   for (int kk = 0; kk < kMetaQ; ++kk) fetch(kk);
   bool ok = true;
   int k = 0;
-  for (int item = blockIdx.x; item < totalItems; item += gridDim.x, ++k) {
+  for (int item = blockIdx.x; item < totalItems && ok; item += gridDim.x, ++k) {
     const int q = k % kMetaQ;
     if (!wait_phase(&queueB[q], (uint32_t)(k / kMetaQ) & 1u, ctl, abort)) {
       ok = false;
       break;
     }
+    // The item's tile block stays in queue slot q until its fills are
+    // issued; the next fetch into the slot follows them.
     const TileBlock* blk = queue + q;
     const int n = blk->n;
-    FragRec r{};
-    if (lane < n && lane < kN) r = blk->recs[lane];
     const int4 loc = qLoc[q];
-    const ItemLoc cur{loc.x, loc.y, loc.z, loc.w};
-    __syncwarp();
-    fetch(k + kMetaQ);  // every lane has read the slot
-    const FrameArgs* A = frames + cur.f;
+    const FrameArgs* A = frames + loc.x;
     const int P = A->P, mode = A->mode, T = A->T;
-    // Items of tiles with more than kN fragments belong to the long-tile
-    // kernel: they get an empty slot that the consumers skip.
-    const bool staged = n <= kN;
+    const size_t p0 = (size_t)loc.z * P;  // the item's first pixel in its tile
+    // An item of more than kN fragments is streamed in fills of kFill; its
+    // records past the tile block come from the sorted list.
+    const int per = n > kN ? kFill : kN;
+    const int fills = n > kN ? (n + kFill - 1) / kFill : 1;
     const uint32_t dBytes = mode == DFB_BLEND_DEPTH || mode == DFB_ZCOMPOSITE ? (uint32_t)P * 4u : 0u;
     const uint32_t cBytes = mode != DFB_ZCOMPOSITE ? (uint32_t)P * px : 0u;
-    const uint32_t fragBytes = staged ? (uint32_t)n * (dBytes + cBytes) : 0u;
     // accumulation state of the item's pixels: one contiguous run per buffer
-    const bool loadState = staged && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1;
+    const bool loadState = (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1;
     const int nState = loadState ? (A->kahan && !A->kahanFirst ? 3 : 2) : 0;
-    const uint32_t stateBytes = (uint32_t)P * 16u;
-    const uint32_t data = fragBytes + nState * stateBytes;
-    const uint32_t need = data;  // multiple of 16
-    // ring space: no item straddles the end of the ring
-    if ((uint32_t)(head % ringBytes) + need > ringBytes) head += ringBytes - head % ringBytes;
-    const int s = k % kSlots;
-    while (tailItem < k && (tailItem <= k - kSlots || head + need - tail > ringBytes)) {
-      const int qq = tailItem % kSlots;
-      if (!wait_phase(&emptyB[qq], (uint32_t)(tailItem / kSlots) & 1u, ctl, abort)) {
+    const int g = G == 1 ? 0 : k % G;
+    for (int f = 0; f < fills; ++f) {
+      const int i0 = f * per;
+      const int nf = min(per, n - i0);
+      const bool lastFill = f == fills - 1;
+      const uint32_t fragBytes = (uint32_t)nf * (dBytes + cBytes);
+      const uint32_t need = fragBytes + (lastFill ? nState * (uint32_t)P * 16u : 0u);  // multiple of 16
+      // ring space: no fill straddles the end of the ring
+      if ((uint32_t)(head % ringBytes) + need > ringBytes) head += ringBytes - head % ringBytes;
+      const int jg = g == 0 ? gf0 : (g == 1 ? gf1 : gf2);
+      const int s = g * S + jg % S;
+      const uint32_t par = (uint32_t)(jg / S) & 1u;
+      const int prev = __shfl_sync(0xffffffffu, slotFill, s);
+      while (tailFill < curFill && (tailFill <= prev || head + need - tail > ringBytes)) {
+        const int e = tailFill % kSlots;
+        const int es = __shfl_sync(0xffffffffu, fifoSlot, e);
+        const int ep = __shfl_sync(0xffffffffu, fifoPar, e);
+        if (!wait_phase(&emptyB[es], (uint32_t)ep, ctl, abort)) {
+          ok = false;
+          break;
+        }
+        tail = metas[es].end;
+        ++tailFill;
+      }
+      if (!ok) break;
+      if (tailFill == curFill) tail = head;  // nothing outstanding: the padding is free too
+      if (!DFB_CHECK((uint64_t)(head % ringBytes) + need <= ringBytes &&
+                         head + need - tail <= ringBytes && nf <= kN &&
+                         (loc.z + 1) * P <= T * T,
+                     ctl.err)) {
         ok = false;
         break;
       }
-      tail = metas[qq].end;
-      ++tailItem;
-    }
-    if (!ok) break;
-    if (tailItem == k) tail = head;  // nothing outstanding: the padding is free too
-    if (!DFB_CHECK((uint64_t)(head % ringBytes) + need <= ringBytes && head + need - tail <= ringBytes &&
-                       (!staged || n <= kN) && (cur.chunk + 1) * P <= T * T,
-                   ctl.err)) {
-      ok = false;
-      break;
-    }
-    const uint32_t start = (uint32_t)(head % ringBytes);
-    head += need;
-    ItemMeta* meta = metas + s;
-    if (staged && lane < n) {
-      meta->rgba[lane] = r.rgba;
-      meta->scale[lane] = r.scale;
-    }
-    if (lane == 0) {
-      meta->n = n;
-      meta->staged = staged ? 1 : 0;
-      meta->start = start;
-      meta->stateOff = fragBytes;
-      meta->end = head;
+      const uint32_t start = (uint32_t)(head % ringBytes);
+      head += need;
+      ItemMeta* meta = metas + s;
+      // lane li < nf takes fragment i0 + li: from the tile block for the
+      // first kN, else from the sorted list in global memory
+      const void* rRgba = nullptr;
+      const float* rDepth = nullptr;
+      if (lane < nf) {
+        const int i = i0 + lane;
+        const FragRec* rec = i < kN ? blk->recs + i : A->srecs + blk->off + i;
+        rRgba = rec->rgba;
+        rDepth = rec->depth;
+        meta->rgba[lane] = rRgba;
+        meta->scale[lane] = rec->scale;
+      }
+      if (lane == 0) {
+        meta->n = nf;
+        meta->total = n;
+        meta->first = i0;
+        meta->start = start;
+        meta->stateOff = fragBytes;
+        meta->end = head;
+      }
+      if (lane == curFill % kSlots) {
+        fifoSlot = s;
+        fifoPar = (int)par;
+      }
+      if (lane == s) slotFill = curFill;
+      ++curFill;
+      if (g == 0) ++gf0; else if (g == 1) ++gf1; else ++gf2;
+      __syncwarp();
+      if (f != 0 || item != ctl.stallItem) {  // test fault injection: never signal this item
+        if (lane == 0) mbar_arrive_expect_tx(&fullB[s], need);
+        armed |= 1u << s;
+        armedPar = (armedPar & ~(1u << s)) | (par << s);
+        __syncwarp();
+        unsigned char* base = ring + start;
+        if (lane < nf) {
+          if (dBytes) bulk_g2s(base + lane * dBytes, rDepth + p0, dBytes, &fullB[s]);
+          if (cBytes)
+            bulk_g2s(base + nf * dBytes + lane * cBytes,
+                     static_cast<const unsigned char*>(rRgba) + p0 * px, cBytes, &fullB[s]);
+        }
+        if (lastFill && lane < nState) {
+          // state runs: [sum | M2 | comp], P pixels of 16 bytes each
+          const float4* src = lane == 0 ? A->accum : (lane == 1 ? A->m2 : A->comp);
+          bulk_g2s(base + fragBytes + lane * (uint32_t)P * 16u,
+                   src + (size_t)loc.y * T * T + p0, (uint32_t)P * 16u, &fullB[s]);
+        }
+      }
     }
     __syncwarp();
-    if (item != ctl.stallItem) {  // test fault injection: never signal this item
-      if (lane == 0) mbar_arrive_expect_tx(&fullB[s], data);
-      armed |= 1u << s;
-      armedPar = (armedPar & ~(1u << s)) | ((uint32_t)((k / kSlots) & 1) << s);
-      __syncwarp();
-      unsigned char* base = ring + start;
-      const size_t p0 = (size_t)cur.chunk * P;
-      if (staged && lane < n) {
-        if (dBytes) bulk_g2s(base + lane * dBytes, r.depth + p0, dBytes, &fullB[s]);
-        if (cBytes)
-          bulk_g2s(base + n * dBytes + lane * cBytes,
-                   static_cast<const unsigned char*>(r.rgba) + p0 * px, cBytes, &fullB[s]);
-      }
-      if (lane < nState) {
-        // state runs: [sum | M2 | comp], P pixels of 16 bytes each
-        const float4* src = lane == 0 ? A->accum : (lane == 1 ? A->m2 : A->comp);
-        bulk_g2s(base + fragBytes + lane * stateBytes, src + (size_t)cur.tile * T * T + p0,
-                 stateBytes, &fullB[s]);
-      }
-    }
+    fetch(k + kMetaQ);  // every lane is done with the slot's block
   }
   if (!ok && lane == 0) give_up(ctl, abort);
   // Leave no bulk copy in flight into this CTA's shared memory.
-  auto drain = [&](uint64_t* bars, uint32_t mask, uint32_t par, int count) {
+  auto drain = [&](uint64_t* bars, uint32_t mask, uint32_t parv, int count) {
     for (int qq = 0; qq < count; ++qq)
       if (mask & (1u << qq)) {
         const uint64_t t0 = global_ns();
-        while (!mbar_try_wait(&bars[qq], (par >> qq) & 1u)) {
+        while (!mbar_try_wait(&bars[qq], (parv >> qq) & 1u)) {
           if (global_ns() - t0 > ctl.waitNs) {
             if (lane == 0) atomicOr(ctl.err, kErrDrain);
             break;
@@ -412,94 +458,14 @@ __device__ __forceinline__ bool composite_staged(int mode, int n, int P, const u
   return true;
 }
 
-// Long lists (more than kN fragments), fragments read from HBM.  In
-// BLEND_DEPTH, `sD` (when not null) holds the item's depth slabs in shared
-// memory (stride P): the pixel then first takes a speculative pass in list
-// order (as composite_staged does), and only if its depths are out of order
-// the exact path below, which works in rounds of a per-pixel window of the
-// kSortWindow nearest fragments not yet blended.
+// Exact BLEND_DEPTH order for one pixel of a long list, fragments read from
+// HBM: rounds of a per-pixel window of the kSortWindow nearest (depth key,
+// list index) keys above the last one blended, blended in that order.  The
+// list arrives in (key, submit index) order, so ties on depth keep it.
 template <int DT>
-__device__ __forceinline__ bool composite_streamed(int mode, int n, const FragRec* list,
-                                                   uint64_t* kbAll, int t, int p,
-                                                   float& c0, float& c1, float& c2, float& al,
-                                                   const float* sD = nullptr, int P = 0) {
-  if (mode == DFB_BLEND_ORDERED) {
-    for (int ib = 0; ib < n; ib += 8) {
-      float4 c[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (ib + u < n) c[u] = Px<DT>::global(list[ib + u].rgba, p, list[ib + u].scale);
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (ib + u < n) over(c[u], c0, c1, c2, al);
-    }
-    return true;
-  }
-  if (mode == DFB_AVERAGE) {
-    for (int ib = 0; ib < n; ib += 8) {
-      float4 c[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (ib + u < n) c[u] = Px<DT>::global(list[ib + u].rgba, p, list[ib + u].scale);
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (ib + u < n) { c0 += c[u].x; c1 += c[u].y; c2 += c[u].z; al += c[u].w; }
-    }
-    const float k = (float)n;
-    c0 = __fdiv_rn(c0, k); c1 = __fdiv_rn(c1, k); c2 = __fdiv_rn(c2, k); al = __fdiv_rn(al, k);
-    return true;
-  }
-  if (mode == DFB_ZCOMPOSITE) {
-    uint64_t best = ~0ull;
-    for (int ib = 0; ib < n; ib += 8) {
-      float z[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) z[u] = (ib + u < n) ? __ldg(list[ib + u].depth + p) : 0.0f;
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (ib + u < n) {
-          const uint64_t k = ((uint64_t)depth_bits(z[u]) << 32) | (uint32_t)(ib + u);
-          best = k < best ? k : best;
-        }
-    }
-    if ((uint32_t)(best >> 32) == kInfBits) return false;
-    const int i = (int)(uint32_t)best;
-    const float4 f = Px<DT>::global(list[i].rgba, p, list[i].scale);
-    c0 = f.x; c1 = f.y; c2 = f.z; al = f.w;
-    return true;
-  }
-  if (sD) {
-    uint32_t last = 0, emptyBits = 0;
-    bool inOrder = true;
-    for (int ib = 0; ib < n; ib += 8) {
-      float4 f[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (ib + u < n) f[u] = Px<DT>::global(list[ib + u].rgba, p, list[ib + u].scale);
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (ib + u < n) {
-          const uint32_t key = depth_bits(sD[(ib + u) * P + t]);
-          if (key != kInfBits) {
-            inOrder = inOrder && key >= last;
-            last = key;
-            over(f[u], c0, c1, c2, al);
-          } else {
-            emptyBits |= __float_as_uint(f[u].x) | __float_as_uint(f[u].y) |
-                         __float_as_uint(f[u].z) | __float_as_uint(f[u].w);
-          }
-        }
-    }
-    if (inOrder) {
-      if (emptyBits)
-        for (int i = 0; i < n; ++i)
-          if (depth_bits(sD[i * P + t]) == kInfBits)
-            over(Px<DT>::global(list[i].rgba, p, list[i].scale), c0, c1, c2, al);
-      return true;
-    }
-    c0 = c1 = c2 = al = 0.0f;
-  }
-  // rounds: each round keeps the window's nearest keys above the last blended
+__device__ __forceinline__ void composite_exact(int n, const FragRec* list, uint64_t* kbAll,
+                                                int t, int p, float& c0, float& c1, float& c2,
+                                                float& al) {
   uint64_t* kb = kbAll + t;
   uint64_t lo = 0;
   int done = 0;
@@ -509,8 +475,7 @@ __device__ __forceinline__ bool composite_streamed(int mode, int n, const FragRe
     for (int ib = 0; ib < n; ib += 8) {
       float z[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-        z[u] = (ib + u < n) ? (sD ? sD[(ib + u) * P + t] : __ldg(list[ib + u].depth + p)) : 0.0f;
+      for (int u = 0; u < 8; ++u) z[u] = (ib + u < n) ? __ldg(list[ib + u].depth + p) : 0.0f;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int i = ib + u;
@@ -548,7 +513,6 @@ __device__ __forceinline__ bool composite_streamed(int mode, int n, const FragRe
     lo = last;
     done += m;
   }
-  return true;
 }
 
 // One pixel of one work item.
@@ -556,8 +520,8 @@ struct PixWork {
   const FrameArgs* A;
   int tile, chunk, p, P;
   bool active;
-  size_t pix;   // row-major image index
-  size_t sidx;  // tile-major state index
+  uint32_t pix;   // row-major image index (frames hold at most 2^31 pixels)
+  uint32_t sidx;  // tile-major state index (tile-major state of at most 2^32 pixels)
 };
 
 __device__ __forceinline__ PixWork prepare(const FrameArgs* frames, const int* itemBase,
@@ -576,11 +540,11 @@ __device__ __forceinline__ PixWork prepare(const FrameArgs* frames, const int* i
   const int ty = __float2int_rz(((float)w.tile + 0.5f) * A->invTilesX);
   const int tx = w.tile - ty * A->tilesX;
   w.p = w.chunk * w.P + t;
-  w.sidx = (size_t)w.tile * T * T + w.p;
+  w.sidx = (uint32_t)w.tile * (uint32_t)(T * T) + (uint32_t)w.p;
   const int x = tx * T + (w.p & (T - 1));
   const int y = ty * T + (w.p >> A->logT);
   w.active = (t < w.P) && (x < A->W) && (y < A->H);
-  w.pix = (size_t)y * A->W + x;
+  w.pix = (uint32_t)y * (uint32_t)A->W + (uint32_t)x;
   return w;
 }
 
@@ -655,59 +619,195 @@ __device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& 
   }
 }
 
+// A multi-fill item's fills, for one blend mode: the consumer group takes
+// them from its slots in order (jg counts its fills) and carries the
+// per-pixel blend across them; the item's state rows come with the last
+// fill.  BLEND_DEPTH blends speculatively in list order; `exact` turns false
+// for a pixel whose finite depths are out of list order or that has a
+// non-zero empty fragment.  Returns false when a wait ran out.
+template <int DT, int MODE, int G>
+__device__ __forceinline__ bool multi_fill(int total, const PixWork& w, int t, int lane,
+                                           const LaunchCtl& ctl, unsigned char* ring,
+                                           ItemMeta* metas, uint64_t* fullB, uint64_t* emptyB,
+                                           volatile int* abort, uint32_t ringBytes, int group,
+                                           int& jg, uint32_t stateRows, float& c0, float& c1,
+                                           float& c2, float& al, bool& covered, bool& exact,
+                                           float4& S0, float4& M, float4& CP) {
+  constexpr int S = kSlots / G;
+  constexpr int px = Bytes<DT>::px;
+  const int fills = (total + kFill - 1) / kFill;
+  const int P = w.P;
+  uint32_t last = 0u, emptyBits = 0u;
+  bool inOrder = true;
+  uint64_t best = ~0ull;
+  const void* bestRgba = nullptr;
+  float bestScale = 1.0f;
+  for (int f = 0; f < fills; ++f) {
+    const int s = group * S + jg % S;
+    if (f > 0 && !wait_phase(&fullB[s], (uint32_t)(jg / S) & 1u, ctl, abort)) {
+      if (lane == 0) give_up(ctl, abort);
+      return false;
+    }
+    const ItemMeta* meta = metas + s;
+    const unsigned char* base = ring + meta->start;
+    const int nf = meta->n;
+    const bool lastFill = f == fills - 1;
+    const bool inRing = DFB_CHECK(
+        nf <= kN && (uint64_t)meta->start + meta->stateOff +
+                            (uint64_t)(lastFill ? stateRows : 0u) * P * 16u <=
+                        ringBytes,
+        ctl.err);
+    if (w.active && inRing) {
+      const float* sD = reinterpret_cast<const float*>(base);
+      constexpr bool hasD = MODE == DFB_BLEND_DEPTH || MODE == DFB_ZCOMPOSITE;
+      const unsigned char* sC = base + (hasD ? (size_t)nf * P * 4 : 0);
+      if (MODE == DFB_BLEND_ORDERED) {
+        for (int i = 0; i < nf; ++i)
+          over(Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]), c0, c1, c2, al);
+      } else if (MODE == DFB_AVERAGE) {
+        for (int i = 0; i < nf; ++i) {
+          const float4 v = Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]);
+          c0 += v.x; c1 += v.y; c2 += v.z; al += v.w;
+        }
+      } else if (MODE == DFB_ZCOMPOSITE) {
+        const int first = meta->first;
+        for (int i = 0; i < nf; ++i) {
+          const uint64_t k = ((uint64_t)depth_bits(sD[i * P + t]) << 32) | (uint32_t)(first + i);
+          if (k < best) {
+            best = k;
+            bestRgba = meta->rgba[i];
+            bestScale = meta->scale[i];
+          }
+        }
+      } else {
+        for (int i = 0; i < nf; ++i) {
+          const uint32_t key = depth_bits(sD[i * P + t]);
+          const float4 v = Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]);
+          if (key != kInfBits) {
+            inOrder = inOrder && key >= last;
+            last = key;
+            over(v, c0, c1, c2, al);
+          } else {
+            emptyBits |= __float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) |
+                         __float_as_uint(v.w);
+          }
+        }
+      }
+    }
+    if (lastFill && stateRows && inRing) {
+      const float4* sState = reinterpret_cast<const float4*>(base + meta->stateOff);
+      S0 = sState[t];
+      M = sState[P + t];
+      if (stateRows == 3u) CP = sState[2 * P + t];
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&emptyB[s]);
+    ++jg;
+  }
+  if (MODE == DFB_AVERAGE) {
+    const float kk = (float)total;
+    c0 = __fdiv_rn(c0, kk); c1 = __fdiv_rn(c1, kk); c2 = __fdiv_rn(c2, kk); al = __fdiv_rn(al, kk);
+  } else if (MODE == DFB_ZCOMPOSITE) {
+    covered = (uint32_t)(best >> 32) != kInfBits;
+    if (covered && w.active) {
+      const float4 v = Px<DT>::global(bestRgba, w.p, bestScale);
+      c0 = v.x; c1 = v.y; c2 = v.z; al = v.w;
+    }
+  } else if (MODE == DFB_BLEND_DEPTH) {
+    exact = inOrder && emptyBits == 0u;
+  }
+  return true;
+}
+
+// Consumer group: one pixel per thread.  Its items' fills come from its own
+// slots, in order.
 template <int DT, int G>
 __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                          int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
                          ItemMeta* metas, uint64_t* fullB, uint64_t* emptyB, volatile int* abort,
                          const SrgbTables* tb, uint32_t ringBytes) {
+  constexpr int S = kSlots / G;
   const int group = threadIdx.x / kP;
   const int t = threadIdx.x - group * kP;  // pixel of the item, 0 .. kP-1
   const int lane = t & 31, warp = t >> 5;
+  int jg = 0;  // this group's fills taken
   for (int k = group; ; k += G) {
     const int item = blockIdx.x + k * (int)gridDim.x;
     if (item >= totalItems) break;
-    const int s = k % kSlots;
     const PixWork w = prepare(frames, itemBase, nFrames, item, t);
     const FrameArgs* A = w.A;
-    if (!wait_phase(&fullB[s], (uint32_t)(k / kSlots) & 1u, ctl, abort)) {
+    int s = group * S + jg % S;
+    if (!wait_phase(&fullB[s], (uint32_t)(jg / S) & 1u, ctl, abort)) {
       if (lane == 0) give_up(ctl, abort);
       break;
     }
     const ItemMeta* meta = metas + s;
-    if (!meta->staged) {  // a long tile's item: done by k_composite_long
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&emptyB[s]);
-      continue;
-    }
-    const int n = meta->n;
+    const int total = meta->total;
     const int P = w.P;
-    const unsigned char* base = ring + meta->start;
     const bool accRead = w.active && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1;
-    // checked build: the item's fragments and state rows lie inside the ring
-    const bool inRing = DFB_CHECK(
-        n <= kN && (uint64_t)meta->start + meta->stateOff +
-                           (uint64_t)(accRead ? ((A->kahan && !A->kahanFirst) ? 3u : 2u) : 0u) *
-                               P * 16u <=
-                       ringBytes,
-        ctl.err);
+    const uint32_t stateRows = accRead ? ((A->kahan && !A->kahanFirst) ? 3u : 2u) : 0u;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 S0 = zero4, M = zero4, CP = zero4;
     float c0 = 0.f, c1 = 0.f, c2 = 0.f, al = 0.f;
     bool covered = true;
-    if (w.active && inRing)
-      covered = composite_staged<DT>(A->mode, n, P, base, meta, t, w.p, c0, c1, c2, al);
-    // the item's accumulation state: from the ring into registers, then the
-    // ring space goes back to the producer before the epilogue's math and
-    // stores
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 S = zero4, M = zero4, CP = zero4;
-    if (accRead && inRing) {
-      const float4* sState = reinterpret_cast<const float4*>(base + meta->stateOff);
-      S = sState[t];
-      M = sState[P + t];
-      if (A->kahan && !A->kahanFirst) CP = sState[2 * P + t];
+    if (total <= kN) {
+      const unsigned char* base = ring + meta->start;
+      // checked build: the item's fragments and state rows lie inside the ring
+      const bool inRing = DFB_CHECK(
+          meta->n <= kN && (uint64_t)meta->start + meta->stateOff + (uint64_t)stateRows * P * 16u <=
+                               ringBytes,
+          ctl.err);
+      if (w.active && inRing)
+        covered = composite_staged<DT>(A->mode, total, P, base, meta, t, w.p, c0, c1, c2, al);
+      // the item's accumulation state: from the ring into registers, then the
+      // ring space goes back to the producer before the epilogue's math and
+      // stores
+      if (accRead && inRing) {
+        const float4* sState = reinterpret_cast<const float4*>(base + meta->stateOff);
+        S0 = sState[t];
+        M = sState[P + t];
+        if (stateRows == 3u) CP = sState[2 * P + t];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&emptyB[s]);  // ring space free for the producer
+      ++jg;
+    } else {
+      // multi-fill item: kFill fragments per fill, the state rows in the last
+      bool ok, exact = true;
+      switch (A->mode) {
+        case DFB_BLEND_DEPTH:
+          ok = multi_fill<DT, DFB_BLEND_DEPTH, G>(total, w, t, lane, ctl, ring, metas, fullB,
+                                                  emptyB, abort, ringBytes, group, jg, stateRows,
+                                                  c0, c1, c2, al, covered, exact, S0, M, CP);
+          break;
+        case DFB_BLEND_ORDERED:
+          ok = multi_fill<DT, DFB_BLEND_ORDERED, G>(total, w, t, lane, ctl, ring, metas, fullB,
+                                                    emptyB, abort, ringBytes, group, jg, stateRows,
+                                                    c0, c1, c2, al, covered, exact, S0, M, CP);
+          break;
+        case DFB_ZCOMPOSITE:
+          ok = multi_fill<DT, DFB_ZCOMPOSITE, G>(total, w, t, lane, ctl, ring, metas, fullB,
+                                                 emptyB, abort, ringBytes, group, jg, stateRows,
+                                                 c0, c1, c2, al, covered, exact, S0, M, CP);
+          break;
+        default:
+          ok = multi_fill<DT, DFB_AVERAGE, G>(total, w, t, lane, ctl, ring, metas, fullB, emptyB,
+                                              abort, ringBytes, group, jg, stateRows, c0, c1, c2,
+                                              al, covered, exact, S0, M, CP);
+          break;
+      }
+      if (!ok) break;
+      if (__any_sync(0xffffffffu, w.active && !exact)) {
+        // out-of-order depths (or a non-zero empty fragment) in this warp's
+        // 32 pixels: the exact re-do kernel composites them after this launch
+        if (lane == 0) {
+          const int slot = atomicAdd(ctl.redo, 1);
+          ctl.redo[1 + slot] = item * (kP / 32) + warp;
+        }
+        continue;
+      }
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&emptyB[s]);  // ring space free for the producer
-    finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, tb, ctl.err);
+    finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S0, M, CP, tb, ctl.err);
   }
 }
 
@@ -739,95 +839,49 @@ __global__ void __launch_bounds__(Shape<G>::threads, PER) k_composite(
   }
   __syncthreads();
   if (threadIdx.x >= G * kP)
-    producer<DT>(frames, itemBase, nFrames, totalItems, ctl, ring, ringBytes, metas, queue, qLoc,
+    producer<DT, G>(frames, itemBase, nFrames, totalItems, ctl, ring, ringBytes, metas, queue, qLoc,
                  fullB, emptyB, queueB, abort);
   else
     consumer<DT, G>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
                     tb, ringBytes);
 }
 
-// Depth slabs a long-tile item can stage in shared memory (1 KB each at 256
-// pixels per item); longer lists read their depths from HBM.
-constexpr int kLongStage = 160;
-
-// Tiles with more than kN fragments, after the main kernel: the work items of
-// all long tiles are spread over the CTAs (kP threads, one pixel per thread).
-// In BLEND_DEPTH the item's depth slabs (up to `stageN` of them) are first
-// copied into shared memory with bulk copies, so that the pixel's
-// speculative in-order pass and, where needed, its exact windowed rounds
-// read depths from there; RGBA is read from HBM in batches of 8 fragments.
-// Two CTAs per SM (128 registers) measured faster than one CTA without the
-// register cap.
-// The pixel then goes through the same epilogue as in the main kernel.  Long
-// lists are rare, and keeping this path out of k_composite keeps that
-// kernel's register count low enough for more resident warps.
+// Exact re-do of the 32-pixel units (work item, warp) that the persistent
+// kernel left: multi-fill BLEND_DEPTH items whose depths were out of list
+// order at some pixel, or that had a non-zero empty fragment.  Each warp of a
+// CTA takes one unit at a time; each pixel reads its fragments from HBM and
+// blends them in exact (depth, key, submit index) order through the
+// windowed rounds of composite_exact, then goes through the same
+// epilogue.  Units are rare on brick scenes, whose key order is their depth
+// order; the kernel returns at once when there are none.
 template <int DT>
-__global__ void __launch_bounds__(kP, 2) k_composite_long(const FrameArgs* __restrict__ frames,
+__global__ void __launch_bounds__(kP, 2) k_composite_redo(const FrameArgs* __restrict__ frames,
                                                        const int* __restrict__ itemBase,
-                                                       int nFrames, LongList lng, int stageN,
-                                                       LaunchCtl ctl) {
+                                                       int nFrames, LaunchCtl ctl) {
   extern __shared__ __align__(128) unsigned char lsmem[];
   SrgbTables* tb = reinterpret_cast<SrgbTables*>(lsmem);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(lsmem + sizeof(SrgbTables));
   uint64_t* window = reinterpret_cast<uint64_t*>(lsmem + sizeof(SrgbTables) + 128);
-  float* sDepth = reinterpret_cast<float*>(lsmem + sizeof(SrgbTables) + 128 + kWindowBytes);
+  const int count = *(volatile int*)ctl.redo;
+  if ((int)blockIdx.x * (kP / 32) >= count) return;
   load_srgb(tb, kP);
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  if (t == 0) {
-    mbar_init(bar, 1);
-    fence_barrier_init();
-  }
   __syncthreads();
-  uint32_t parity = 0;
-  bool inFlight = false;  // a staging copy may still land (after a timed-out wait)
-  for (int u = blockIdx.x; u < lng.items; u += gridDim.x) {
-    int j = 0, hj = lng.n - 1;  // long tile with the largest item base <= u
-    while (j < hj) {
-      const int mid = (j + hj + 1) >> 1;
-      if (__ldg(lng.base + mid) <= u) j = mid; else hj = mid - 1;
-    }
-    const int gt = __ldg(lng.tiles + j);
-    const int c = u - __ldg(lng.base + j);
-    int lo = 0, hi = nFrames - 1;  // frame with the largest tileBase <= gt
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (frames[mid].tileBase <= gt) lo = mid; else hi = mid - 1;
-    }
-    const FrameArgs* A = frames + lo;
-    if (!DFB_CHECK(gt >= A->tileBase && gt < A->tileBase + A->nTiles && c >= 0 && c < A->chunks,
-                   ctl.err))
+  const int lane = threadIdx.x & 31;
+  for (int u = blockIdx.x * (kP / 32) + (threadIdx.x >> 5); u < count;
+       u += gridDim.x * (kP / 32)) {
+    const int entry = ctl.redo[1 + u];
+    const int item = entry / (kP / 32), iw = entry % (kP / 32);
+    const int f = find_frame(itemBase, nFrames, item);
+    const FrameArgs* A = frames + f;
+    const int local = item - __ldg(itemBase + f);
+    const int gt = A->tileBase + (local >> A->logChunks);
+    if (!DFB_CHECK(f >= 0 && f < nFrames && (local >> A->logChunks) < A->nTiles, ctl.err))
       continue;
     const TileBlock* blk = A->blocks + gt;
-    const int n = blk->n, off = blk->off;
-    const FragRec* list = A->srecs + off;
-    const int item = __ldg(itemBase + lo) + (gt - A->tileBase) * A->chunks + c;
-    const PixWork w = prepare(frames, itemBase, nFrames, item, t);
-    const bool stage = A->mode == DFB_BLEND_DEPTH && n <= stageN;
-    if (stage) {
-      // one bulk copy per fragment's depth slab, issued by warp 0
-      const uint32_t slab = (uint32_t)w.P * 4u;
-      if (t == 0) mbar_arrive_expect_tx(bar, (uint32_t)n * slab);
-      if (warp == 0) {
-        __syncwarp();
-        for (int i = lane; i < n; i += 32)
-          bulk_g2s(sDepth + (size_t)i * w.P, list[i].depth + (size_t)c * w.P, slab, bar);
-      }
-      inFlight = true;
-      bool got = mbar_try_wait(bar, parity);
-      const uint64_t t0 = global_ns();
-      while (!got && global_ns() - t0 <= ctl.waitNs) got = mbar_try_wait(bar, parity);
-      if (!__syncthreads_and(got)) {
-        if (t == 0) atomicOr(ctl.err, kErrTimeout);
-        break;
-      }
-      inFlight = false;
-      parity ^= 1u;
-    }
+    const int n = blk->n;
+    const FragRec* list = A->srecs + blk->off;
+    const PixWork w = prepare(frames, itemBase, nFrames, item, iw * 32 + lane);
     float c0 = 0.f, c1 = 0.f, c2 = 0.f, al = 0.f;
-    bool covered = true;
-    if (w.active)
-      covered = composite_streamed<DT>(A->mode, n, list, window, t, w.p, c0, c1, c2, al,
-                                       stage ? sDepth : nullptr, w.P);
+    if (w.active) composite_exact<DT>(n, list, window, threadIdx.x, w.p, c0, c1, c2, al);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 S = zero4, M = zero4, CP = zero4;
     if (w.active && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1) {
@@ -835,17 +889,7 @@ __global__ void __launch_bounds__(kP, 2) k_composite_long(const FrameArgs* __res
       M = A->m2[w.sidx];
       if (A->kahan && !A->kahanFirst) CP = A->comp[w.sidx];
     }
-    finish_pixel(A, w, lane, warp, c0, c1, c2, al, covered, S, M, CP, tb, ctl.err);
-    __syncthreads();  // every thread is done with the staged depths
-  }
-  if (inFlight && t == 0) {
-    // leave no bulk copy in flight into this CTA's shared memory
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
-      if (global_ns() - t0 > ctl.waitNs) {
-        atomicOr(ctl.err, kErrDrain);
-        break;
-      }
+    finish_pixel(A, w, lane, iw, c0, c1, c2, al, true, S, M, CP, tb, ctl.err);
   }
 }
 
@@ -953,48 +997,45 @@ cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int n
     case DFB_BF16: e = launch_dt<DFB_BF16>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
     default: e = launch_dt<DFB_FP8E4M3>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
   }
-  // One-time set-up of the long-tile kernel per device, done on any launch
-  // (so that it never first happens inside a stream capture).
+  // One-time set-up of the re-do kernel per device, done on any launch (so
+  // that it never first happens inside a stream capture).
   static int sms[64] = {0};
   int dev = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess && (dev < 0 || dev >= 64)) e = cudaErrorInvalidDevice;
+  const int smem = (int)(sizeof(SrgbTables) + 128 + kWindowBytes);
   if (e == cudaSuccess && !sms[dev]) {
     int count = 0;
     e = cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
-    const int maxSmem = (int)(sizeof(SrgbTables) + 128 + kWindowBytes) + kLongStage * kP * 4;
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_composite_long<DFB_F32>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
+      e = cudaFuncSetAttribute(k_composite_redo<DFB_F32>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_composite_long<DFB_F16>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
+      e = cudaFuncSetAttribute(k_composite_redo<DFB_F16>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_composite_long<DFB_BF16>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
+      e = cudaFuncSetAttribute(k_composite_redo<DFB_BF16>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_composite_long<DFB_FP8E4M3>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, maxSmem);
+      e = cudaFuncSetAttribute(k_composite_redo<DFB_FP8E4M3>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) sms[dev] = count;
   }
-  if (e == cudaSuccess && lng.n > 0 && lng.items > 0) {
-    const int grid = lng.items < 8 * sms[dev] ? lng.items : 8 * sms[dev];
-    const int stageN = lng.maxFragments < kLongStage ? lng.maxFragments : kLongStage;
-    const size_t smem = sizeof(SrgbTables) + 128 + kWindowBytes + (size_t)stageN * kP * 4;
+  if (e == cudaSuccess && lng.items > 0) {
+    // at most one unit per warp of the long items; the count is on the device
+    const int grid = lng.items < 2 * sms[dev] ? lng.items : 2 * sms[dev];
     switch (dtype) {
       case DFB_F32:
-        k_composite_long<DFB_F32><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng, stageN, ctl);
+        k_composite_redo<DFB_F32><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, ctl);
         break;
       case DFB_F16:
-        k_composite_long<DFB_F16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng, stageN, ctl);
+        k_composite_redo<DFB_F16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, ctl);
         break;
       case DFB_BF16:
-        k_composite_long<DFB_BF16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng, stageN,
-                                                          ctl);
+        k_composite_redo<DFB_BF16><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, ctl);
         break;
       default:
-        k_composite_long<DFB_FP8E4M3><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, lng,
-                                                             stageN, ctl);
+        k_composite_redo<DFB_FP8E4M3><<<grid, kP, smem, s>>>(frames, itemBase, nFrames, ctl);
         break;
     }
     e = cudaGetLastError();

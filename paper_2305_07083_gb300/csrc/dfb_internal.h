@@ -13,11 +13,14 @@ namespace dfb {
 // is 256 consecutive pixels of one tile; a 64x64 tile is 16 items.  Tiles of
 // fewer than 256 pixels are one item each.
 constexpr int kItemPixels = 256;
-// Fragments of an item staged in shared memory by bulk copies; tiles with
-// more fragments are composited by a separate, streaming kernel.
+// Fragments of a work item staged in shared memory by one fill of the
+// composite's ring.  Items of tiles with more fragments are streamed through
+// the ring in several fills of kFill fragments each.
 constexpr int kStageFragments = 16;
-// Per-pixel sort window of the streaming path: fragments are taken in rounds
-// of at most kSortWindow, each round the window's nearest not yet blended.
+constexpr int kFill = 8;
+// Per-pixel sort window of the exact re-do path: fragments are taken in
+// rounds of at most kSortWindow, each round the window's nearest not yet
+// blended.
 constexpr int kSortWindow = 16;
 
 // Device record of one submitted fragment tile (32 bytes).
@@ -103,15 +106,12 @@ struct TuneParams {
   int groups;     // consumer groups per CTA (items composited at once)
 };
 
-// Tiles of a launch with more than kStageFragments fragments: global tile
-// ids and the prefix of their work items (base[i] = items of tiles 0..i-1;
-// base[n] = items), device arrays.
+// Tiles of a launch with more than kStageFragments fragments: their work
+// items (the only ones that can need the exact re-do kernel) and the longest
+// list among them.
 struct LongList {
-  const int* tiles = nullptr;
-  const int* base = nullptr;
-  int n = 0;
   int items = 0;
-  int maxFragments = 0;  // longest list among them
+  int maxFragments = 0;
 };
 
 // Bits of a launch's device error word.
@@ -133,20 +133,25 @@ struct LaunchCtl {
   unsigned long long waitNs;  // bound on every barrier wait inside the kernel
   int stallItem;              // test fault injection: this item is never filled (-1: off)
   unsigned* err;              // device error word; bit 0 = a wait timed out
+  int* redo;                  // [count, items...]: multi-fill items left to the re-do kernel
 };
 
-// Bucketing (K1): counts -> offsets -> scatter -> per-tile rank sort that
-// writes the records themselves in (key, index) order to `srecs` and fills
-// one TileBlock per tile.
-cudaError_t launch_bucket(const FragRec* recs, int nRec, int nTilesTotal, int* counts,
-                          int* offsets, int* cursor, uint32_t* tmp, FragRec* srecs,
-                          TileBlock* blocks, cudaStream_t s);
+// Bucketing (K1), second half.  The host groups the records by global tile
+// while it stages them (a stable counting sort: submission order kept within
+// a tile) and uploads the tile offsets tileOff[0..nTiles] (tileOff[nTiles] =
+// records).  One kernel then orders every tile's records by (order key,
+// position) -- the (key, submit index) order -- into `srecs` and fills one
+// TileBlock per tile.  It also clears the re-do count `redo[0]` (if given)
+// of the composite launch that follows.
+cudaError_t launch_bucket(const FragRec* grouped, const int* tileOff, int nTiles, FragRec* srecs,
+                          TileBlock* blocks, int* redo, cudaStream_t s);
 
 // Composite + accumulate + variance + pack (K2/K3 + K4) over the work items of
 // `nFrames` frames (device arrays `frames` and `itemBase`, nFrames + 1 prefix
-// of work items), all of storage dtype `dtype`, one persistent launch; then
-// the work items of the long tiles (which the first launch skips); then, if
-// `accumulate`, the per-tile variance of `totalTiles` global tiles.
+// of work items), all of storage dtype `dtype`, one persistent launch; then,
+// if the launch has long tiles, the exact re-do of the multi-fill items the
+// persistent kernel left (out-of-order depths); then, if `accumulate`, the
+// per-tile variance of `totalTiles` global tiles.
 cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int nFrames,
                              int totalItems, int totalTiles, bool accumulate, int dtype,
                              const TuneParams& tune, const LaunchCtl& ctl, const LongList& lng,

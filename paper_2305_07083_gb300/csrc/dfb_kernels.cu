@@ -1,9 +1,9 @@
 // CUDA kernels of the DFB path for sm_103a, apart from the composite kernel
 // (dfb_composite.cu):
 //
-//   K1  bucket:     records -> per-tile lists sorted by (order key, submit
-//                   index): the routing of setTile to the tile owner
-//                   (Sec. 3.1) and the rank order of the list tree (Sec. 4.2).
+//   K1  bucket:     per-tile lists (grouped by the host) sorted by (order key,
+//                   submit index): the rank order of the list tree (Sec. 4.2)
+//                   and the tile blocks the composite reads.
 //   K6  convert:    producer-side FP16 / BF16 / FP8-e4m3 storage of tiles.
 //   read-back:      normalised accumulation and per-pixel variance.
 #include <cuda_bf16.h>
@@ -16,112 +16,101 @@ namespace dfb {
 // ----------------------------------------------------------------------------
 // K1: bucketing
 // ----------------------------------------------------------------------------
-__global__ void k1_count(const FragRec* __restrict__ recs, int n, int* __restrict__ counts) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) atomicAdd(&counts[recs[i].tile], 1);
-}
+// Lists longer than this are sorted with a bitonic network in shared memory
+// (one warp per tile); longer ones than kSortSmem by rank counting.
+constexpr int kOrderWarps = 8;
+constexpr int kSortSmem = 256;
 
-// One CTA of 1024 threads: exclusive scan of the per-tile counts.
-__global__ void __launch_bounds__(1024) k1_scan(const int* __restrict__ counts, int nTiles,
-                                                int* __restrict__ offsets,
-                                                int* __restrict__ cursor) {
-  __shared__ int warpSum[32];
-  __shared__ int carry;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < nTiles; base += 1024) {
-    const int i = base + threadIdx.x;
-    const int v = i < nTiles ? counts[i] : 0;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) warpSum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      int w = warpSum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      warpSum[lane] = w;
-    }
-    __syncthreads();
-    const int excl = carry + (warp ? warpSum[warp - 1] : 0) + x - v;
-    if (i < nTiles) {
-      offsets[i] = excl;
-      cursor[i] = excl;
-    }
-    __syncthreads();
-    if (threadIdx.x == 1023) carry = excl + v;
-    __syncthreads();
-  }
-}
-
-__global__ void k1_scatter(const FragRec* __restrict__ recs, int n, int* __restrict__ cursor,
-                           uint32_t* __restrict__ tmp) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) tmp[atomicAdd(&cursor[recs[i].tile], 1)] = (uint32_t)i;
-}
-
-// One warp per tile: each element's final position is its rank under the
-// total order (key bits, record index), so the result does not depend on the
-// order in which the scatter's atomics placed the records.  The records are
-// written in that order, and the tile's block gets its count, offset and
-// first records.
-__global__ void k1_segsort(const FragRec* __restrict__ recs, const int* __restrict__ counts,
-                           const int* __restrict__ offsets, int nTiles,
-                           const uint32_t* __restrict__ tmp, FragRec* __restrict__ srecs,
-                           TileBlock* __restrict__ blocks) {
-  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+// One warp per tile.  The tile's records arrive grouped, in submission order;
+// the element at position i gets the key (order-key bits << 32 | i), and its
+// final place is its rank under that key: the (key, submit index) order.
+// Lists of up to 32 are ranked in registers, longer ones sorted in shared
+// memory.
+__global__ void __launch_bounds__(kOrderWarps * 32) k1_order(const FragRec* __restrict__ grouped,
+                                                            const int* __restrict__ tileOff,
+                                                            int nTiles, FragRec* __restrict__ srecs,
+                                                            TileBlock* __restrict__ blocks,
+                                                            int* __restrict__ redo) {
+  __shared__ uint64_t keys[kOrderWarps][kSortSmem];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * kOrderWarps + warp;
+  if (redo && blockIdx.x == 0 && threadIdx.x == 0) redo[0] = 0;
   if (t >= nTiles) return;
-  const int n = counts[t], off = offsets[t];
+  const int off = __ldg(tileOff + t);
+  const int n = __ldg(tileOff + t + 1) - off;
   if (lane == 0) {
     blocks[t].n = n;
     blocks[t].off = off;
   }
+  const FragRec* in = grouped + off;
+  if (n <= 32) {
+    FragRec r{};
+    uint64_t k = ~0ull;
+    if (lane < n) {
+      r = in[lane];
+      k = ((uint64_t)r.key << 32) | (uint32_t)lane;
+    }
+    int rank = 0;
+    for (int j = 0; j < n; ++j) rank += (__shfl_sync(0xffffffffu, k, j) < k) ? 1 : 0;
+    if (lane < n) {
+      srecs[off + rank] = r;
+      if (rank < kStageFragments) blocks[t].recs[rank] = r;
+    }
+    return;
+  }
+  if (n <= kSortSmem) {
+    uint64_t* a = keys[warp];
+    int m = 64;
+    while (m < n) m <<= 1;
+    for (int i = lane; i < m; i += 32)
+      a[i] = i < n ? (((uint64_t)__ldg(&in[i].key) << 32) | (uint32_t)i) : ~0ull;
+    __syncwarp();
+    for (int k = 2; k <= m; k <<= 1) {
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = lane; i < m; i += 32) {
+          const int p = i ^ j;
+          if (p > i) {
+            const uint64_t x = a[i], y = a[p];
+            const bool up = (i & k) == 0;
+            if ((x > y) == up) {
+              a[i] = y;
+              a[p] = x;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    for (int i = lane; i < n; i += 32) {
+      const FragRec r = in[(uint32_t)a[i]];
+      srecs[off + i] = r;
+      if (i < kStageFragments) blocks[t].recs[i] = r;
+    }
+    return;
+  }
+  // very long lists: rank of each element by counting the smaller keys
   for (int jb = 0; jb < n; jb += 32) {
     const int j = jb + lane;
-    uint32_t rj = 0;
-    uint64_t kj = ~0ull;
-    if (j < n) {
-      rj = tmp[off + j];
-      kj = ((uint64_t)recs[rj].key << 32) | rj;
-    }
+    const uint64_t kj = j < n ? (((uint64_t)__ldg(&in[j].key) << 32) | (uint32_t)j) : ~0ull;
     int rank = 0;
     for (int mb = 0; mb < n; mb += 32) {
       const int m = mb + lane;
-      uint64_t km = ~0ull;
-      if (m < n) {
-        const uint32_t rm = tmp[off + m];
-        km = ((uint64_t)recs[rm].key << 32) | rm;
-      }
+      const uint64_t km = m < n ? (((uint64_t)__ldg(&in[m].key) << 32) | (uint32_t)m) : ~0ull;
       const int cnt = min(32, n - mb);
-      for (int s = 0; s < cnt; ++s) rank += (__shfl_sync(0xffffffffu, km, s) < kj) ? 1 : 0;
+      for (int q = 0; q < cnt; ++q) rank += (__shfl_sync(0xffffffffu, km, q) < kj) ? 1 : 0;
     }
     if (j < n) {
-      const FragRec r = recs[rj];
+      const FragRec r = in[j];
       srecs[off + rank] = r;
       if (rank < kStageFragments) blocks[t].recs[rank] = r;
     }
   }
 }
 
-cudaError_t launch_bucket(const FragRec* recs, int nRec, int nTilesTotal, int* counts,
-                          int* offsets, int* cursor, uint32_t* tmp, FragRec* srecs,
-                          TileBlock* blocks, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)nTilesTotal, s);
-  if (e != cudaSuccess) return e;
-  if (nRec > 0) k1_count<<<(nRec + 255) / 256, 256, 0, s>>>(recs, nRec, counts);
-  k1_scan<<<1, 1024, 0, s>>>(counts, nTilesTotal, offsets, cursor);
-  if (nRec > 0) k1_scatter<<<(nRec + 255) / 256, 256, 0, s>>>(recs, nRec, cursor, tmp);
-  k1_segsort<<<(nTilesTotal * 32 + 255) / 256, 256, 0, s>>>(recs, counts, offsets, nTilesTotal,
-                                                             tmp, srecs, blocks);
+cudaError_t launch_bucket(const FragRec* grouped, const int* tileOff, int nTiles, FragRec* srecs,
+                          TileBlock* blocks, int* redo, cudaStream_t s) {
+  const int grid = nTiles > 0 ? (nTiles + kOrderWarps - 1) / kOrderWarps : 1;
+  k1_order<<<grid, kOrderWarps * 32, 0, s>>>(grouped, tileOff, nTiles, srecs, blocks, redo);
   return cudaGetLastError();
 }
 

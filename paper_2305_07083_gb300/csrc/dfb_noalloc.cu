@@ -27,21 +27,21 @@ using dfb::FrameArgs;
 
 constexpr int kMaxFragments = 65536;  // fragment tiles per call
 constexpr int kMaxTiles = 16384;      // tiles per frame
+constexpr int kMaxRedo = 1 << 19;     // re-do units (32-pixel units of long tiles' items)
 
 // Layout of g_scratch (each region 256-byte aligned):
 //   FrameArgs + item prefix + error word
-//   FragRec  recs[kMaxFragments]      32 B each
+//   FragRec  recs[kMaxFragments]      32 B each, grouped by tile
 //   int      tileIn[kMaxFragments]    raw inputs copied from the caller
 //   float    keyIn[kMaxFragments]
 //   uint64   rgbaIn[kMaxFragments]
 //   uint64   depthIn[kMaxFragments]
 //   float    scaleIn[kMaxFragments]
-//   uint32   tmp[kMaxFragments]
+//   int      posIn[kMaxFragments]     each record's place in the grouped list
 //   FragRec  srecs[kMaxFragments]     records sorted per tile
-//   int      counts[kMaxTiles], offsets[kMaxTiles], cursor[kMaxTiles]
+//   int      tileOff[kMaxTiles + 1]   offsets of the tiles' lists
 //   TileBlock blocks[kMaxTiles]       per-tile count/offset/first records
-//   int      longIn[2 * kMaxTiles + 1] tiles with more fragments than the composite
-//                                      stages, then the prefix of their work items
+//   int      redo[kMaxRedo + 1]       the composite's re-do list
 constexpr size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 struct Header {
   FrameArgs fa;
@@ -54,14 +54,12 @@ constexpr size_t kOffKeyIn = align256(kOffTileIn + sizeof(int) * kMaxFragments);
 constexpr size_t kOffRgbaIn = align256(kOffKeyIn + sizeof(float) * kMaxFragments);
 constexpr size_t kOffDepthIn = align256(kOffRgbaIn + sizeof(uint64_t) * kMaxFragments);
 constexpr size_t kOffScaleIn = align256(kOffDepthIn + sizeof(uint64_t) * kMaxFragments);
-constexpr size_t kOffTmp = align256(kOffScaleIn + sizeof(float) * kMaxFragments);
-constexpr size_t kOffSrecs = align256(kOffTmp + sizeof(uint32_t) * kMaxFragments);
-constexpr size_t kOffCounts = align256(kOffSrecs + sizeof(FragRec) * kMaxFragments);
-constexpr size_t kOffOffsets = align256(kOffCounts + sizeof(int) * kMaxTiles);
-constexpr size_t kOffCursor = align256(kOffOffsets + sizeof(int) * kMaxTiles);
-constexpr size_t kOffBlocks = align256(kOffCursor + sizeof(int) * kMaxTiles);
-constexpr size_t kOffLong = align256(kOffBlocks + sizeof(dfb::TileBlock) * kMaxTiles);
-constexpr size_t kScratchBytes = align256(kOffLong + sizeof(int) * (2 * kMaxTiles + 1));  // ~15.3 MB
+constexpr size_t kOffPosIn = align256(kOffScaleIn + sizeof(float) * kMaxFragments);
+constexpr size_t kOffSrecs = align256(kOffPosIn + sizeof(int) * kMaxFragments);
+constexpr size_t kOffTileOff = align256(kOffSrecs + sizeof(FragRec) * kMaxFragments);
+constexpr size_t kOffBlocks = align256(kOffTileOff + sizeof(int) * (kMaxTiles + 1));
+constexpr size_t kOffRedo = align256(kOffBlocks + sizeof(dfb::TileBlock) * kMaxTiles);
+constexpr size_t kScratchBytes = align256(kOffRedo + sizeof(int) * (kMaxRedo + 1));  // ~17 MB
 
 // The scratch itself.  Every GPU that loads the library holds it until the
 // process exits.  In host code `g_scratch` names a host-side stand-in, not the
@@ -88,12 +86,13 @@ int scratch_for_current_device(unsigned char** out) {
   return DFB_OK;
 }
 
-// Build the 32-byte fragment records from the raw per-fragment inputs.
+// Build the 32-byte fragment records from the raw per-fragment inputs, each
+// at its place in the list grouped by tile.
 __global__ void k_pack_records(const int* __restrict__ tileIn, const float* __restrict__ keyIn,
                                const uint64_t* __restrict__ rgbaIn,
                                const uint64_t* __restrict__ depthIn,
-                               const float* __restrict__ scaleIn, int useScale, int n,
-                               FragRec* __restrict__ recs) {
+                               const float* __restrict__ scaleIn, const int* __restrict__ posIn,
+                               int useScale, int n, FragRec* __restrict__ recs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint32_t u = __float_as_uint(keyIn[i]);
@@ -105,7 +104,7 @@ __global__ void k_pack_records(const int* __restrict__ tileIn, const float* __re
   r.key = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
   r.scale = useScale ? scaleIn[i] : 1.0f;
   r.frame = 0u;
-  recs[i] = r;
+  recs[posIn[i]] = r;
 }
 
 bool device_accessible(const void* p) {
@@ -117,13 +116,41 @@ bool device_accessible(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-}  // namespace
+// Input tiles must be device (or managed) memory: the kernels read them with
+// bulk copies.  Checking every pointer would cost one driver query per
+// fragment tile, so only the first and the last tile of every run of
+// back-to-back tiles (each starting `bytes` after the previous one, the
+// layout of a pool) are checked.
+template <class P>
+bool tiles_accessible(const P* const* ptrs, int n, size_t bytes) {
+  for (int i = 0; i < n;) {
+    int j = i;
+    while (j + 1 < n && reinterpret_cast<uintptr_t>(ptrs[j + 1]) ==
+                            reinterpret_cast<uintptr_t>(ptrs[j]) + bytes)
+      ++j;
+    if (!device_accessible(ptrs[i]) || (j != i && !device_accessible(ptrs[j]))) return false;
+    i = j + 1;
+  }
+  return true;
+}
 
-extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int mode, int dtype,
-                                     int n, const int* tile_ids, const float* order_keys,
-                                     const void* const* rgba, const float* const* depth,
-                                     const float* scales, const float* background,
-                                     float* color_out, uint32_t* rgba8_out, void* stream) {
+// The C entry point runs its body under this guard, so that no C++
+// exception (a host vector that cannot grow) crosses the interface.
+template <typename F>
+int guarded_call(F&& body) noexcept {
+  try {
+    return body();
+  } catch (const std::bad_alloc&) {
+    return DFB_ERR_OOM;
+  } catch (...) {
+    return DFB_ERR_STATE;
+  }
+}
+
+int composite_noalloc(int width, int height, int tile_size, int mode, int dtype, int n,
+                      const int* tile_ids, const float* order_keys, const void* const* rgba,
+                      const float* const* depth, const float* scales, const float* background,
+                      float* color_out, uint32_t* rgba8_out, void* stream) {
   // ---- validation (host only) ----
   const int T = tile_size;
   if (width < 1 || height < 1 || T < 4 || T > 256 || (T & (T - 1))) return DFB_ERR_INVALID_ARG;
@@ -135,10 +162,13 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   const int tilesX = (width + T - 1) / T, tilesY = (height + T - 1) / T;
   if ((int64_t)tilesX * tilesY > kMaxTiles || n > kMaxFragments) return DFB_ERR_CAPACITY;
   const int nTiles = tilesX * tilesY;
-  std::vector<int> perTile((size_t)nTiles, 0), longTiles;  // host memory only
+  std::vector<int> perTile((size_t)nTiles, 0);  // host memory only
+  int nLong = 0, maxFrags = 0;
   for (int i = 0; i < n; ++i) {
     if (tile_ids[i] < 0 || tile_ids[i] >= nTiles) return DFB_ERR_TILE_RANGE;
-    if (++perTile[tile_ids[i]] == dfb::kStageFragments + 1) longTiles.push_back(tile_ids[i]);
+    const int c = ++perTile[tile_ids[i]];
+    if (c == dfb::kStageFragments + 1) ++nLong;
+    if (c > maxFrags) maxFrags = c;
     if (isnan(order_keys[i]) || !rgba[i] || !depth[i]) return DFB_ERR_INVALID_ARG;
     if (((uintptr_t)rgba[i] % 16) || ((uintptr_t)depth[i] % 16)) return DFB_ERR_INVALID_ARG;
     if (dtype == DFB_FP8E4M3 && !(scales[i] > 0.0f && isfinite(scales[i])))
@@ -150,8 +180,26 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
       if (!isfinite(background[c])) return DFB_ERR_INVALID_ARG;
       bg[c] = background[c];
     }
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    // The call copies from pageable host memory and waits on the stream,
+    // neither of which a capturing stream allows.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+      cudaGetLastError();
+      return DFB_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return DFB_ERR_STATE;
+  }
   if ((color_out && !device_accessible(color_out)) ||
       (rgba8_out && !device_accessible(rgba8_out)))
+    return DFB_ERR_INVALID_ARG;
+  const int chunksPerTile = T * T < dfb::kItemPixels ? 1 : T * T / dfb::kItemPixels;
+  // only BLEND_DEPTH items of long tiles can need the re-do kernel
+  const int64_t longItems = mode == DFB_BLEND_DEPTH ? (int64_t)nLong * chunksPerTile : 0;
+  if (longItems * (dfb::kItemPixels / 32) > kMaxRedo) return DFB_ERR_CAPACITY;
+  const size_t rgbaBytes = (size_t)T * T * 4 * (dtype == DFB_F32 ? 4 : (dtype == DFB_FP8E4M3 ? 1 : 2));
+  if (!tiles_accessible(rgba, n, rgbaBytes) || !tiles_accessible(depth, n, (size_t)T * T * 4))
     return DFB_ERR_INVALID_ARG;
 
   unsigned char* base = nullptr;
@@ -163,29 +211,31 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   uint64_t* rgbaIn = reinterpret_cast<uint64_t*>(base + kOffRgbaIn);
   uint64_t* depthIn = reinterpret_cast<uint64_t*>(base + kOffDepthIn);
   float* scaleIn = reinterpret_cast<float*>(base + kOffScaleIn);
-  uint32_t* tmp = reinterpret_cast<uint32_t*>(base + kOffTmp);
+  int* posIn = reinterpret_cast<int*>(base + kOffPosIn);
   FragRec* srecs = reinterpret_cast<FragRec*>(base + kOffSrecs);
+  int* tileOff = reinterpret_cast<int*>(base + kOffTileOff);
   dfb::TileBlock* blocks = reinterpret_cast<dfb::TileBlock*>(base + kOffBlocks);
+  int* redo = reinterpret_cast<int*>(base + kOffRedo);
   Header* dHdr = reinterpret_cast<Header*>(base);
-  int* counts = reinterpret_cast<int*>(base + kOffCounts);
-  int* offsets = reinterpret_cast<int*>(base + kOffOffsets);
-  int* cursor = reinterpret_cast<int*>(base + kOffCursor);
-  int* longIn = reinterpret_cast<int*>(base + kOffLong);
-  const int nLong = (int)longTiles.size();
-  const int chunksPerTile = T * T < dfb::kItemPixels ? 1 : T * T / dfb::kItemPixels;
-  for (int i = 0; i <= nLong; ++i) longTiles.push_back(i * chunksPerTile);  // item prefix
+  // each record's place in the list grouped by tile (stable: submission order
+  // kept within a tile) and the tiles' offsets -- host memory only
+  std::vector<int> off((size_t)nTiles + 1), pos((size_t)n);
+  {
+    int acc = 0;
+    for (int t = 0; t < nTiles; ++t) {
+      off[t] = acc;
+      acc += perTile[t];
+    }
+    off[nTiles] = acc;
+    std::vector<int> cursor(off.begin(), off.end() - 1);
+    for (int i = 0; i < n; ++i) pos[i] = cursor[tile_ids[i]]++;
+  }
   dfb::LongList lng;
-  lng.tiles = longIn;
-  lng.base = longIn + nLong;
-  lng.n = nLong;
-  lng.items = nLong * chunksPerTile;
-  for (int i = 0; i < nLong; ++i)
-    lng.maxFragments = perTile[longTiles[i]] > lng.maxFragments ? perTile[longTiles[i]]
-                                                                 : lng.maxFragments;
+  lng.items = (int)longItems;
+  lng.maxFragments = maxFrags;
   static_assert(sizeof(void*) == sizeof(uint64_t), "64-bit pointers");
 
   // ---- inputs into the scratch (plain copies; the host arrays may be pageable) ----
-  cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   const bool fp8 = dtype == DFB_FP8E4M3;
   if (n > 0) {
@@ -198,20 +248,20 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
       e = cudaMemcpyAsync(depthIn, depth, sizeof(void*) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && fp8)
       e = cudaMemcpyAsync(scaleIn, scales, sizeof(float) * n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && nLong)
-      e = cudaMemcpyAsync(longIn, longTiles.data(), sizeof(int) * (2 * nLong + 1),
-                          cudaMemcpyHostToDevice, s);
-    // the caller may reuse its host arrays once this call returns
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e == cudaSuccess) {
-      k_pack_records<<<(n + 255) / 256, 256, 0, s>>>(tileIn, keyIn, rgbaIn, depthIn, scaleIn,
-                                                     fp8 ? 1 : 0, n, recs);
-      e = cudaGetLastError();
-    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(posIn, pos.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s);
   }
-  // ---- bucketing (clears the per-tile counts itself) and compositing ----
   if (e == cudaSuccess)
-    e = dfb::launch_bucket(recs, n, nTiles, counts, offsets, cursor, tmp, srecs, blocks, s);
+    e = cudaMemcpyAsync(tileOff, off.data(), sizeof(int) * (nTiles + 1), cudaMemcpyHostToDevice, s);
+  // the caller may reuse its host arrays once this call returns
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && n > 0) {
+    k_pack_records<<<(n + 255) / 256, 256, 0, s>>>(tileIn, keyIn, rgbaIn, depthIn, scaleIn, posIn,
+                                                   fp8 ? 1 : 0, n, recs);
+    e = cudaGetLastError();
+  }
+  // ---- bucketing (also clears the re-do count) and compositing ----
+  if (e == cudaSuccess) e = dfb::launch_bucket(recs, tileOff, nTiles, srecs, blocks, redo, s);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? DFB_ERR_OOM : DFB_ERR_CUDA;
 
   Header hdr{};
@@ -246,8 +296,31 @@ extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int m
   e = cudaMemcpyAsync(dHdr, &hdr, sizeof(Header), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return DFB_ERR_CUDA;
-  const dfb::LaunchCtl ctl{2000000000ull, -1, &dHdr->err};
+  const dfb::LaunchCtl ctl{2000000000ull, -1, &dHdr->err, redo};
   e = dfb::launch_composite(&dHdr->fa, dHdr->itemBase, 1, hdr.itemBase[1], nTiles, false, dtype,
                            dfb::default_tune(dtype), ctl, lng, s);
-  return e == cudaSuccess ? DFB_OK : DFB_ERR_CUDA;
+  if (e != cudaSuccess) return DFB_ERR_CUDA;
+  // The launch's error word: a wait that ran out (the frame is then
+  // incomplete) or, in the checked build, a failed device-side check.  The
+  // next call clears it, so it is read here, once the frame is done.
+  unsigned err = 0u;
+  e = cudaMemcpyAsync(&err, &dHdr->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return DFB_ERR_CUDA;
+  if (err & dfb::kErrCheck) return DFB_ERR_CHECK;
+  if (err) return DFB_ERR_TIMEOUT;
+  return DFB_OK;
+}
+
+}  // namespace
+
+extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int mode, int dtype,
+                                     int n, const int* tile_ids, const float* order_keys,
+                                     const void* const* rgba, const float* const* depth,
+                                     const float* scales, const float* background,
+                                     float* color_out, uint32_t* rgba8_out, void* stream) {
+  return guarded_call([&]() -> int {
+    return composite_noalloc(width, height, tile_size, mode, dtype, n, tile_ids, order_keys, rgba,
+                             depth, scales, background, color_out, rgba8_out, stream);
+  });
 }

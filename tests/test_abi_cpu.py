@@ -54,7 +54,9 @@ def test_error_strings_and_version():
 
 @pytest.mark.parametrize("W,H,T,mode,dtype,flags", [
     (0, 64, 16, 0, 0, 1), (64, -1, 16, 0, 0, 1), (64, 64, 12, 0, 0, 1), (64, 64, 2, 0, 0, 1),
-    (64, 64, 512, 0, 0, 1), (64, 64, 16, 4, 0, 1), (64, 64, 16, 0, 4, 1), (64, 64, 16, 0, 0, 64)])
+    (64, 64, 512, 0, 0, 1), (64, 64, 16, 4, 0, 1), (64, 64, 16, 0, 4, 1), (64, 64, 16, 0, 0, 64),
+    (1 << 16, (1 << 15) + 1, 16, 0, 0, 1),    # more than 2^31 pixels
+    ((1 << 24) + 1, 1, 256, 0, 0, 1)])        # whole tiles hold more than 2^32 pixels
 def test_create_rejects_bad_config(W, H, T, mode, dtype, flags):
     with pytest.raises(D.DfbError) as e:
         D.dfb_create_ex(W, H, T, mode, dtype, flags)

@@ -291,14 +291,15 @@ def test_save_and_resume_accumulation():
 
 # --- storage precision ---------------------------------------------------------------
 # Storage error bounds.  FP16 meets the 2e-3 max-abs target.  BF16 keeps an
-# 8-bit significand: a stored value in [0.5, 1) is off by up to 2^-9, and the
-# errors of a pixel's colour and coverage over several layers add, so its
-# max-abs bound is 2^-7 and the 2e-3 target holds for the RMS error.  FP8
-# e4m3 keeps 3 mantissa bits, so a value near the tile's amax carries up to
-# 2^-4 relative error; colour and coverage errors of several layers add, so
-# its max-abs bound is 2^-3 and the 2e-2 target holds for the RMS error, not
-# the max.
-STORAGE = [(D.DFB_F16, 2e-3, 2e-3), (D.DFB_BF16, 2.0 ** -7, 2e-3), (D.DFB_FP8E4M3, 2.0 ** -3, 2e-2)]
+# 8-bit significand (a stored value in [0.5, 1) is off by up to 2^-9) and
+# FP8 e4m3 3 mantissa bits (up to 2^-4 relative near the tile's amax); the
+# colour and coverage errors of a pixel's layers add, so the format-derived
+# bounds would be 2^-7 and 2^-3.  The asserted max-abs bounds sit just above
+# the errors these scenes actually reach (the oracle on the stored values
+# against the oracle on the FP32 values: BF16 3.0e-3 here and 4.0e-3 at
+# 4096x1024, FP8 4.8e-2 and 6.6e-2), so that a regression fails; the 2e-3
+# and 2e-2 targets hold for the RMS error.
+STORAGE = [(D.DFB_F16, 2e-3, 2e-3), (D.DFB_BF16, 5e-3, 2e-3), (D.DFB_FP8E4M3, 8e-2, 2e-2)]
 
 
 @pytest.mark.parametrize("dtype,max_tol,rms_tol", STORAGE)

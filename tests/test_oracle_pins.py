@@ -314,10 +314,13 @@ def test_srgb_pack_against_inverse_thresholds():
         x = thr * (1 + eps)
         got = o.unpack_rgba8(o.pack_rgba8(np.stack([x, x, x, np.zeros_like(x)], -1)))[:, 0]
         np.testing.assert_array_equal(got, np.arange(1, 256) + want)
-    x = np.random.default_rng(15).uniform(0, 1, 1 << 20)
-    got = o.unpack_rgba8(o.pack_rgba8(np.stack([x, x, x, x], -1)))
-    np.testing.assert_array_equal(got[:, 0], np.searchsorted(thr, x, side="right"))
-    np.testing.assert_array_equal(got[:, 3], np.floor(255 * x + 0.5).astype(int))
+    # 2^24 seeded uniform samples, in chunks to bound the memory
+    rng = np.random.default_rng(15)
+    for _ in range(4):
+        x = rng.uniform(0, 1, 1 << 22)
+        got = o.unpack_rgba8(o.pack_rgba8(np.stack([x, x, x, x], -1)))
+        np.testing.assert_array_equal(got[:, 0], np.searchsorted(thr, x, side="right"))
+        np.testing.assert_array_equal(got[:, 3], np.floor(255 * x + 0.5).astype(int))
 
 
 # --- storage formats --------------------------------------------------------

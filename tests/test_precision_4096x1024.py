@@ -24,8 +24,8 @@ pytestmark = pytest.mark.gpu
 
 FORMS = [("f32", D.DFB_F32), ("f16", D.DFB_F16), ("bf16", D.DFB_BF16), ("fp8e4m3", D.DFB_FP8E4M3)]
 # (kernel max-abs, storage max-abs, storage RMS) bounds; see test_gpu_parity
-BOUNDS = {"f32": (1e-5, 1e-5, 1e-5), "f16": (1e-5, 2e-3, 2e-3), "bf16": (1e-5, 2.0 ** -7, 2e-3),
-          "fp8e4m3": (1e-5, 2.0 ** -3, 2e-2)}
+BOUNDS = {"f32": (1e-5, 1e-5, 1e-5), "f16": (1e-5, 2e-3, 2e-3), "bf16": (1e-5, 5e-3, 2e-3),
+          "fp8e4m3": (1e-5, 8e-2, 2e-2)}
 
 
 def _chan(err):

@@ -5,15 +5,17 @@ synchronisation a cudaMalloc may cause).
 
 Calls in a row, through the C ABI, are checked against the handle-based path
 (dfb_create / dfb_submit_tiles / dfb_end_frame), which allocates its own
-buffers.  The second call is smaller than the first, so leftovers of the first
-call in the shared scratch array would show up as wrong pixels; the last two
-have tiles with more than 16 fragments.  This file is collected last on
-purpose."""
+buffers, and against the FP64 oracle fed the same stored values.  The second
+call is smaller than the first, so leftovers of the first call in the shared
+scratch array would show up as wrong pixels; the later calls have tiles with
+more than 16 fragments, and one stores its tiles as FP8 with a scale per
+tile.  This file is collected last on purpose."""
 
 import numpy as np
 import pytest
 
 from harness import scenes
+from oracle import dfb_oracle as o
 from paper_2305_07083_gb300 import dfb as D
 
 from tests.gpu_helpers import GpuFrameBuffer, to_dev
@@ -63,6 +65,7 @@ def test_two_calls_in_a_row_match_the_handle_path():
     longs = scenes.random_scene(256, 192, 64, counts, seed=23, alpha_max=0.3)
     calls.append((longs, D.DFB_BLEND_DEPTH, D.DFB_F32, (0.1, 0.2, 0.3, 1.0)))
     calls.append((longs, D.DFB_AVERAGE, D.DFB_BF16, (0.0, 0.0, 0.0, 0.0)))
+    calls.append((longs, D.DFB_BLEND_ORDERED, D.DFB_FP8E4M3, (0.3, 0.3, 0.3, 0.25)))
     for sc, mode, dtype, bg in calls:
         stored, scales = scenes.store_rgba(sc.rgba, dtype)
         want_c, want_8 = handle_path(sc, mode, dtype, stored, scales, bg)
@@ -70,6 +73,58 @@ def test_two_calls_in_a_row_match_the_handle_path():
         assert np.max(np.abs(got_c - want_c)) <= TOL
         d8 = np.abs(got_8.view(np.uint8).astype(int) - want_8.view(np.uint8).astype(int))
         assert d8.max() <= 1
+        # and the oracle, on the same stored (dequantised) values
+        ref = o.composite_frame(sc.W, sc.H, sc.T, mode, sc.tile_ids, sc.keys,
+                                o.dequantize(stored, dtype, scales), sc.depth, bg=bg)
+        assert np.max(np.abs(got_c.astype(np.float64) - ref)) <= TOL
+        r8 = o.unpack_rgba8(o.pack_rgba8(ref)).astype(int)
+        assert np.abs(o.unpack_rgba8(got_8).astype(int) - r8).max() <= 1
+
+
+def test_refuses_host_tiles_and_a_capturing_stream():
+    import torch
+    sc = scenes.random_scene(64, 64, 16, np.full(16, 2), seed=24)
+    out = torch.empty((sc.H, sc.W, 4), dtype=torch.float32, device="cuda")
+    host_r = np.ascontiguousarray(sc.rgba, np.float32)
+    host_d = np.ascontiguousarray(sc.depth, np.float32)
+    dev_d = to_dev(sc.depth)
+    tb = sc.T * sc.T
+    # ordinary host memory passed as tiles: refused before any GPU work
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_composite_noalloc(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH, D.DFB_F32, sc.tile_ids,
+                                sc.keys, D.pool_pointers(host_r, sc.n, tb * 16),
+                                D.pool_pointers(dev_d, sc.n, tb * 4), None, None, out, None)
+    assert e.value.code == D.DFB_ERR_INVALID_ARG
+    with pytest.raises(D.DfbError) as e:
+        D.dfb_composite_noalloc(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH, D.DFB_F32, sc.tile_ids,
+                                sc.keys, D.pool_pointers(to_dev(sc.rgba), sc.n, tb * 16),
+                                D.pool_pointers(host_d, sc.n, tb * 4), None, None, out, None)
+    assert e.value.code == D.DFB_ERR_INVALID_ARG
+    # a stream under capture: refused before the stream is touched
+    dev_r = to_dev(sc.rgba)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    codes = []
+    with torch.cuda.stream(s):
+        g.capture_begin(capture_error_mode="relaxed")
+        try:
+            D.dfb_composite_noalloc(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH, D.DFB_F32, sc.tile_ids,
+                                    sc.keys, D.pool_pointers(dev_r, sc.n, tb * 16),
+                                    D.pool_pointers(dev_d, sc.n, tb * 4), None, None, out, None,
+                                    stream=s)
+        except D.DfbError as err:
+            codes.append(err.code)
+        finally:
+            g.capture_end()
+    assert codes == [D.DFB_ERR_STATE]
+    # the same call on an ordinary stream then succeeds
+    D.dfb_composite_noalloc(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH, D.DFB_F32, sc.tile_ids, sc.keys,
+                            D.pool_pointers(dev_r, sc.n, tb * 16),
+                            D.pool_pointers(dev_d, sc.n, tb * 4), None, None, out, None)
+    ref = o.composite_frame(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH, sc.tile_ids, sc.keys,
+                            sc.rgba.astype(np.float64), sc.depth)
+    assert np.max(np.abs(out.cpu().numpy().astype(np.float64) - ref)) <= TOL
 
 
 def test_rejects_requests_beyond_the_fixed_scratch():
