@@ -165,12 +165,15 @@ struct ItemLoc {
   int f, tile, chunk, gt;
 };
 
+// ONE: a launch of a single frame, whose arguments `frames` points to in the
+// kernel's parameter space (read through the constant cache, no loads).
+template <bool ONE>
 __device__ __forceinline__ ItemLoc locate(const FrameArgs* frames, const int* itemBase,
                                           int nFrames, int item) {
   ItemLoc L;
-  L.f = find_frame(itemBase, nFrames, item);
+  L.f = ONE ? 0 : find_frame(itemBase, nFrames, item);
   const FrameArgs* A = frames + L.f;
-  const int local = item - __ldg(itemBase + L.f);
+  const int local = ONE ? item : item - __ldg(itemBase + L.f);
   L.tile = local >> A->logChunks;
   L.chunk = local & (A->chunks - 1);
   L.gt = A->tileBase + L.tile;
@@ -184,7 +187,7 @@ __device__ __forceinline__ ItemLoc locate(const FrameArgs* frames, const int* it
 // kSlots / G) and takes its items' fills from them in order.  Ring bytes are
 // reclaimed in the global order of the fills; a fill may reuse a slot once
 // the slot's previous fill has been released.
-template <int DT, int G>
+template <int DT, int G, bool ONE>
 __device__ void producer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                          int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
                          uint32_t ringBytes, ItemMeta* metas, TileBlock* queue, int4* qLoc,
@@ -206,7 +209,7 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
   auto fetch = [&](int kk) {
     const int it = blockIdx.x + kk * (int)gridDim.x;
     if (it >= totalItems || lane != 0) return;
-    const ItemLoc L = locate(frames, itemBase, nFrames, it);
+    const ItemLoc L = locate<ONE>(frames, itemBase, nFrames, it);
     if (!DFB_CHECK(L.f >= 0 && L.f < nFrames && L.tile >= 0 && L.tile < frames[L.f].nTiles,
                    ctl.err))
       return;
@@ -354,6 +357,12 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
 // ---------------------------------------------------------------------------
 // consumer warps: one pixel per thread
 // ---------------------------------------------------------------------------
+// A depth that takes part in the blend: not +inf and not NaN (both read as an
+// empty fragment; NaN maps to +inf).  The speculative in-order passes compare
+// such depths as floats, which orders them exactly as their canonical keys
+// (depth_bits) do: -0 equals +0 and -inf comes first.
+__device__ __forceinline__ bool covers(float z) { return z <= 3.402823466e38f; }
+
 // Returns false only in DFB_ZCOMPOSITE for a pixel no fragment covers.
 template <int DT>
 __device__ __forceinline__ bool composite_staged(int mode, int n, int P, const unsigned char* base,
@@ -396,14 +405,15 @@ __device__ __forceinline__ bool composite_staged(int mode, int n, int P, const u
     // the second pass, in list order, after the finite ones.  If the check
     // fails the pixel starts over on the sorting path below.
     {
-      uint32_t last = 0, emptyBits = 0;
+      float last = -INFINITY;
+      uint32_t emptyBits = 0;
       bool inOrder = true;
       for (int i = 0; i < n; ++i) {
-        const uint32_t key = depth_bits(sD[i * P + t]);
+        const float z = sD[i * P + t];
         const float4 f = Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]);
-        if (key != kInfBits) {
-          inOrder = inOrder && key >= last;
-          last = key;
+        if (covers(z)) {
+          inOrder = inOrder && z >= last;
+          last = z;
           over(f, c0, c1, c2, al);
         } else {
           emptyBits |= __float_as_uint(f.x) | __float_as_uint(f.y) | __float_as_uint(f.z) |
@@ -413,7 +423,7 @@ __device__ __forceinline__ bool composite_staged(int mode, int n, int P, const u
       if (inOrder) {
         if (emptyBits) {
           for (int i = 0; i < n; ++i)
-            if (depth_bits(sD[i * P + t]) == kInfBits)
+            if (!covers(sD[i * P + t]))
               over(Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]), c0, c1, c2, al);
         }
         return true;
@@ -524,13 +534,14 @@ struct PixWork {
   uint32_t sidx;  // tile-major state index (tile-major state of at most 2^32 pixels)
 };
 
+template <bool ONE>
 __device__ __forceinline__ PixWork prepare(const FrameArgs* frames, const int* itemBase,
                                            int nFrames, int item, int t) {
   PixWork w;
-  const int f = find_frame(itemBase, nFrames, item);
+  const int f = ONE ? 0 : find_frame(itemBase, nFrames, item);
   const FrameArgs* A = frames + f;
   w.A = A;
-  const int local = item - __ldg(itemBase + f);
+  const int local = ONE ? item : item - __ldg(itemBase + f);
   const int T = A->T;
   w.P = A->P;
   w.tile = local >> A->logChunks;
@@ -637,7 +648,8 @@ __device__ __forceinline__ bool multi_fill(int total, const PixWork& w, int t, i
   constexpr int px = Bytes<DT>::px;
   const int fills = (total + kFill - 1) / kFill;
   const int P = w.P;
-  uint32_t last = 0u, emptyBits = 0u;
+  float last = -INFINITY;
+  uint32_t emptyBits = 0u;
   bool inOrder = true;
   uint64_t best = ~0ull;
   const void* bestRgba = nullptr;
@@ -681,11 +693,11 @@ __device__ __forceinline__ bool multi_fill(int total, const PixWork& w, int t, i
         }
       } else {
         for (int i = 0; i < nf; ++i) {
-          const uint32_t key = depth_bits(sD[i * P + t]);
+          const float z = sD[i * P + t];
           const float4 v = Px<DT>::shared(sC + (size_t)i * P * px, t, meta->scale[i]);
-          if (key != kInfBits) {
-            inOrder = inOrder && key >= last;
-            last = key;
+          if (covers(z)) {
+            inOrder = inOrder && z >= last;
+            last = z;
             over(v, c0, c1, c2, al);
           } else {
             emptyBits |= __float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) |
@@ -721,7 +733,7 @@ __device__ __forceinline__ bool multi_fill(int total, const PixWork& w, int t, i
 
 // Consumer group: one pixel per thread.  Its items' fills come from its own
 // slots, in order.
-template <int DT, int G>
+template <int DT, int G, bool ONE>
 __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                          int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
                          ItemMeta* metas, uint64_t* fullB, uint64_t* emptyB, volatile int* abort,
@@ -734,7 +746,7 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
   for (int k = group; ; k += G) {
     const int item = blockIdx.x + k * (int)gridDim.x;
     if (item >= totalItems) break;
-    const PixWork w = prepare(frames, itemBase, nFrames, item, t);
+    const PixWork w = prepare<ONE>(frames, itemBase, nFrames, item, t);
     const FrameArgs* A = w.A;
     int s = group * S + jg % S;
     if (!wait_phase(&fullB[s], (uint32_t)(jg / S) & 1u, ctl, abort)) {
@@ -811,12 +823,15 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
   }
 }
 
-template <int DT, int G, int PER>
-__global__ void __launch_bounds__(Shape<G>::threads, PER) k_composite(
-    const FrameArgs* __restrict__ frames,
-                                                        const int* __restrict__ itemBase,
-                                                        int nFrames, int totalItems,
-                                                        uint32_t ringBytes, LaunchCtl ctl) {
+// ONE: a single-frame launch; its arguments come as the kernel parameter
+// `one` and are read from the parameter space.  Otherwise `frames` is the
+// launch's frame table in global memory.
+template <int DT, int G, int PER, bool ONE>
+__global__ void __launch_bounds__(Shape<G>::threads, PER)
+    k_composite(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
+                int nFrames, int totalItems, uint32_t ringBytes, LaunchCtl ctl,
+                const __grid_constant__ FrameArgs one) {
+  if (ONE) frames = &one;
   extern __shared__ __align__(128) unsigned char smem[];
   SrgbTables* tb = reinterpret_cast<SrgbTables*>(smem);
   uint64_t* fullB = reinterpret_cast<uint64_t*>(smem + kOffBars);
@@ -839,10 +854,10 @@ __global__ void __launch_bounds__(Shape<G>::threads, PER) k_composite(
   }
   __syncthreads();
   if (threadIdx.x >= G * kP)
-    producer<DT, G>(frames, itemBase, nFrames, totalItems, ctl, ring, ringBytes, metas, queue, qLoc,
+    producer<DT, G, ONE>(frames, itemBase, nFrames, totalItems, ctl, ring, ringBytes, metas, queue, qLoc,
                  fullB, emptyB, queueB, abort);
   else
-    consumer<DT, G>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
+    consumer<DT, G, ONE>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
                     tb, ringBytes);
 }
 
@@ -879,7 +894,7 @@ __global__ void __launch_bounds__(kP, 2) k_composite_redo(const FrameArgs* __res
     const TileBlock* blk = A->blocks + gt;
     const int n = blk->n;
     const FragRec* list = A->srecs + blk->off;
-    const PixWork w = prepare(frames, itemBase, nFrames, item, iw * 32 + lane);
+    const PixWork w = prepare<false>(frames, itemBase, nFrames, item, iw * 32 + lane);
     float c0 = 0.f, c1 = 0.f, c2 = 0.f, al = 0.f;
     if (w.active) composite_exact<DT>(n, list, window, threadIdx.x, w.p, c0, c1, c2, al);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -923,8 +938,10 @@ __global__ void k_tile_variance(const FrameArgs* __restrict__ frames, int nFrame
 
 template <int DT, int G, int PER>
 cudaError_t launch_shape(const FrameArgs* frames, const int* itemBase, int nFrames,
-                         int totalItems, int ringKB, const LaunchCtl& ctl, cudaStream_t s) {
-  auto kern = k_composite<DT, G, PER>;
+                         int totalItems, int ringKB, const LaunchCtl& ctl, const FrameArgs* one,
+                         cudaStream_t s) {
+  auto kTable = k_composite<DT, G, PER, false>;
+  auto kOne = k_composite<DT, G, PER, true>;
   constexpr int per = PER;  // CTAs per SM
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -939,7 +956,10 @@ cudaError_t launch_shape(const FrameArgs* frames, const int* itemBase, int nFram
       e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess)
       e = cudaDeviceGetAttribute(&perSm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kTable, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kOne, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) {
       sms[dev] = 0;
       return e;
@@ -955,18 +975,24 @@ cudaError_t launch_shape(const FrameArgs* frames, const int* itemBase, int nFram
   int grid = sms[dev] * per;
   if (grid > totalItems) grid = totalItems;
   if (grid < 1) return cudaSuccess;
-  kern<<<grid, Shape<G>::threads, kHeader + ring, s>>>(frames, itemBase, nFrames, totalItems, ring,
-                                                       ctl);
+  if (one)
+    kOne<<<grid, Shape<G>::threads, kHeader + ring, s>>>(frames, itemBase, nFrames, totalItems,
+                                                         ring, ctl, *one);
+  else
+    kTable<<<grid, Shape<G>::threads, kHeader + ring, s>>>(frames, itemBase, nFrames, totalItems,
+                                                           ring, ctl, FrameArgs{});
   return cudaGetLastError();
 }
 
 template <int DT>
 cudaError_t launch_dt(const FrameArgs* frames, const int* itemBase, int nFrames, int totalItems,
-                      const TuneParams& tune, const LaunchCtl& ctl, cudaStream_t s) {
+                      const TuneParams& tune, const LaunchCtl& ctl, const FrameArgs* one,
+                      cudaStream_t s) {
   const int per = tune.ctasPerSm, g = tune.groups;
 #define DFB_SHAPE(G_, PER_)                                                                   \
   if (g == G_ && per == PER_)                                                                 \
-    return launch_shape<DT, G_, PER_>(frames, itemBase, nFrames, totalItems, tune.ringKB, ctl, s);
+    return launch_shape<DT, G_, PER_>(frames, itemBase, nFrames, totalItems, tune.ringKB, ctl,  \
+                                      one, s);
   DFB_SHAPE(1, 2)
   DFB_SHAPE(2, 2)
   DFB_SHAPE(1, 3)
@@ -989,13 +1015,22 @@ TuneParams default_tune(int dtype) {
 cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int nFrames,
                              int totalItems, int totalTiles, bool accumulate, int dtype,
                              const TuneParams& tune, const LaunchCtl& ctl, const LongList& lng,
-                             cudaStream_t s) {
+                             const FrameArgs* hostOne, cudaStream_t s) {
+  const FrameArgs* one = nFrames == 1 ? hostOne : nullptr;
   cudaError_t e;
   switch (dtype) {
-    case DFB_F32: e = launch_dt<DFB_F32>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
-    case DFB_F16: e = launch_dt<DFB_F16>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
-    case DFB_BF16: e = launch_dt<DFB_BF16>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
-    default: e = launch_dt<DFB_FP8E4M3>(frames, itemBase, nFrames, totalItems, tune, ctl, s); break;
+    case DFB_F32:
+      e = launch_dt<DFB_F32>(frames, itemBase, nFrames, totalItems, tune, ctl, one, s);
+      break;
+    case DFB_F16:
+      e = launch_dt<DFB_F16>(frames, itemBase, nFrames, totalItems, tune, ctl, one, s);
+      break;
+    case DFB_BF16:
+      e = launch_dt<DFB_BF16>(frames, itemBase, nFrames, totalItems, tune, ctl, one, s);
+      break;
+    default:
+      e = launch_dt<DFB_FP8E4M3>(frames, itemBase, nFrames, totalItems, tune, ctl, one, s);
+      break;
   }
   // One-time set-up of the re-do kernel per device, done on any launch (so
   // that it never first happens inside a stream capture).
