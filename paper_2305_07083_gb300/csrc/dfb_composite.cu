@@ -44,6 +44,8 @@
 //     a small second kernel sums each tile's partials in a fixed order.
 // Every wait is bounded in time; on expiry the kernel sets an error bit,
 // drains its own bulk copies and returns.
+#include <string.h>
+
 #include "dfb_device.cuh"
 #include "dfb_internal.h"
 
@@ -118,11 +120,34 @@ struct Bytes {
   static constexpr uint32_t maxItem = (uint32_t)kN * kP * (4 + px) + 3u * kP * 16u;
 };
 
+// Where a launch's frame arguments are read from.
+constexpr int kGlobalTable = 0;  // the frame table and item prefix in global memory
+constexpr int kOneFrame = 1;     // one frame, its arguments a kernel parameter
+constexpr int kParamTable = 2;   // up to kParamFrames frames, the tables a kernel parameter
+constexpr int kParamFrames = 48;
+struct FrameTable {
+  int itemBase[kParamFrames + 1];
+  FrameArgs f[kParamFrames];
+};
+static_assert(sizeof(FrameTable) <= 16384, "kernel parameter size");
+template <int FR>
+struct FrameParams {
+  using type = int;  // unused
+};
+template <>
+struct FrameParams<kOneFrame> {
+  using type = FrameArgs;
+};
+template <>
+struct FrameParams<kParamTable> {
+  using type = FrameTable;
+};
+
 __device__ __forceinline__ int find_frame(const int* itemBase, int nFrames, int item) {
   int lo = 0, hi = nFrames - 1;  // last frame whose first item <= item
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(itemBase + mid) <= item) lo = mid; else hi = mid - 1;
+    if (itemBase[mid] <= item) lo = mid; else hi = mid - 1;
   }
   return lo;
 }
@@ -165,15 +190,16 @@ struct ItemLoc {
   int f, tile, chunk, gt;
 };
 
-// ONE: a launch of a single frame, whose arguments `frames` points to in the
-// kernel's parameter space (read through the constant cache, no loads).
-template <bool ONE>
+// FR: where the launch's frame arguments are (FrameSource); with kOneFrame
+// `frames` points to a single frame's arguments in the kernel's parameter
+// space (read through the constant cache, no loads).
+template <int FR>
 __device__ __forceinline__ ItemLoc locate(const FrameArgs* frames, const int* itemBase,
                                           int nFrames, int item) {
   ItemLoc L;
-  L.f = ONE ? 0 : find_frame(itemBase, nFrames, item);
+  L.f = FR == kOneFrame ? 0 : find_frame(itemBase, nFrames, item);
   const FrameArgs* A = frames + L.f;
-  const int local = ONE ? item : item - __ldg(itemBase + L.f);
+  const int local = FR == kOneFrame ? item : item - itemBase[L.f];
   L.tile = local >> A->logChunks;
   L.chunk = local & (A->chunks - 1);
   L.gt = A->tileBase + L.tile;
@@ -187,7 +213,7 @@ __device__ __forceinline__ ItemLoc locate(const FrameArgs* frames, const int* it
 // kSlots / G) and takes its items' fills from them in order.  Ring bytes are
 // reclaimed in the global order of the fills; a fill may reuse a slot once
 // the slot's previous fill has been released.
-template <int DT, int G, bool ONE>
+template <int DT, int G, int FR>
 __device__ void producer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                          int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
                          uint32_t ringBytes, ItemMeta* metas, TileBlock* queue, int4* qLoc,
@@ -209,7 +235,7 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
   auto fetch = [&](int kk) {
     const int it = blockIdx.x + kk * (int)gridDim.x;
     if (it >= totalItems || lane != 0) return;
-    const ItemLoc L = locate<ONE>(frames, itemBase, nFrames, it);
+    const ItemLoc L = locate<FR>(frames, itemBase, nFrames, it);
     if (!DFB_CHECK(L.f >= 0 && L.f < nFrames && L.tile >= 0 && L.tile < frames[L.f].nTiles,
                    ctl.err))
       return;
@@ -534,14 +560,14 @@ struct PixWork {
   uint32_t sidx;  // tile-major state index (tile-major state of at most 2^32 pixels)
 };
 
-template <bool ONE>
+template <int FR>
 __device__ __forceinline__ PixWork prepare(const FrameArgs* frames, const int* itemBase,
                                            int nFrames, int item, int t) {
   PixWork w;
-  const int f = ONE ? 0 : find_frame(itemBase, nFrames, item);
+  const int f = FR == kOneFrame ? 0 : find_frame(itemBase, nFrames, item);
   const FrameArgs* A = frames + f;
   w.A = A;
-  const int local = ONE ? item : item - __ldg(itemBase + f);
+  const int local = FR == kOneFrame ? item : item - itemBase[f];
   const int T = A->T;
   w.P = A->P;
   w.tile = local >> A->logChunks;
@@ -733,7 +759,7 @@ __device__ __forceinline__ bool multi_fill(int total, const PixWork& w, int t, i
 
 // Consumer group: one pixel per thread.  Its items' fills come from its own
 // slots, in order.
-template <int DT, int G, bool ONE>
+template <int DT, int G, int FR>
 __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                          int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
                          ItemMeta* metas, uint64_t* fullB, uint64_t* emptyB, volatile int* abort,
@@ -746,7 +772,7 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
   for (int k = group; ; k += G) {
     const int item = blockIdx.x + k * (int)gridDim.x;
     if (item >= totalItems) break;
-    const PixWork w = prepare<ONE>(frames, itemBase, nFrames, item, t);
+    const PixWork w = prepare<FR>(frames, itemBase, nFrames, item, t);
     const FrameArgs* A = w.A;
     int s = group * S + jg % S;
     if (!wait_phase(&fullB[s], (uint32_t)(jg / S) & 1u, ctl, abort)) {
@@ -823,15 +849,21 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
   }
 }
 
-// ONE: a single-frame launch; its arguments come as the kernel parameter
-// `one` and are read from the parameter space.  Otherwise `frames` is the
-// launch's frame table in global memory.
-template <int DT, int G, int PER, bool ONE>
+// FR = kOneFrame: a single-frame launch, whose arguments come as the kernel
+// parameter `prm`; kParamTable: the frame table (and work-item prefix) of a
+// launch of at most kParamFrames frames comes as `prm`; both are read from
+// the parameter space.  kGlobalTable: `frames` and `itemBase` are the
+// launch's tables in global memory.
+template <int DT, int G, int PER, int FR>
 __global__ void __launch_bounds__(Shape<G>::threads, PER)
     k_composite(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                 int nFrames, int totalItems, uint32_t ringBytes, LaunchCtl ctl,
-                const __grid_constant__ FrameArgs one) {
-  if (ONE) frames = &one;
+                const __grid_constant__ typename FrameParams<FR>::type prm) {
+  if constexpr (FR == kOneFrame) frames = &prm;
+  if constexpr (FR == kParamTable) {
+    frames = prm.f;
+    itemBase = prm.itemBase;
+  }
   extern __shared__ __align__(128) unsigned char smem[];
   SrgbTables* tb = reinterpret_cast<SrgbTables*>(smem);
   uint64_t* fullB = reinterpret_cast<uint64_t*>(smem + kOffBars);
@@ -854,10 +886,10 @@ __global__ void __launch_bounds__(Shape<G>::threads, PER)
   }
   __syncthreads();
   if (threadIdx.x >= G * kP)
-    producer<DT, G, ONE>(frames, itemBase, nFrames, totalItems, ctl, ring, ringBytes, metas, queue, qLoc,
+    producer<DT, G, FR>(frames, itemBase, nFrames, totalItems, ctl, ring, ringBytes, metas, queue, qLoc,
                  fullB, emptyB, queueB, abort);
   else
-    consumer<DT, G, ONE>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
+    consumer<DT, G, FR>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
                     tb, ringBytes);
 }
 
@@ -894,7 +926,7 @@ __global__ void __launch_bounds__(kP, 2) k_composite_redo(const FrameArgs* __res
     const TileBlock* blk = A->blocks + gt;
     const int n = blk->n;
     const FragRec* list = A->srecs + blk->off;
-    const PixWork w = prepare<false>(frames, itemBase, nFrames, item, iw * 32 + lane);
+    const PixWork w = prepare<kGlobalTable>(frames, itemBase, nFrames, item, iw * 32 + lane);
     float c0 = 0.f, c1 = 0.f, c2 = 0.f, al = 0.f;
     if (w.active) composite_exact<DT>(n, list, window, threadIdx.x, w.p, c0, c1, c2, al);
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -938,10 +970,11 @@ __global__ void k_tile_variance(const FrameArgs* __restrict__ frames, int nFrame
 
 template <int DT, int G, int PER>
 cudaError_t launch_shape(const FrameArgs* frames, const int* itemBase, int nFrames,
-                         int totalItems, int ringKB, const LaunchCtl& ctl, const FrameArgs* one,
-                         cudaStream_t s) {
-  auto kTable = k_composite<DT, G, PER, false>;
-  auto kOne = k_composite<DT, G, PER, true>;
+                         int totalItems, int ringKB, const LaunchCtl& ctl,
+                         const FrameArgs* hostFrames, const int* hostItemBase, cudaStream_t s) {
+  auto kTable = k_composite<DT, G, PER, kGlobalTable>;
+  auto kOne = k_composite<DT, G, PER, kOneFrame>;
+  auto kParam = k_composite<DT, G, PER, kParamTable>;
   constexpr int per = PER;  // CTAs per SM
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -960,6 +993,8 @@ cudaError_t launch_shape(const FrameArgs* frames, const int* itemBase, int nFram
       e = cudaFuncSetAttribute(kTable, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(kOne, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kParam, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) {
       sms[dev] = 0;
       return e;
@@ -975,24 +1010,32 @@ cudaError_t launch_shape(const FrameArgs* frames, const int* itemBase, int nFram
   int grid = sms[dev] * per;
   if (grid > totalItems) grid = totalItems;
   if (grid < 1) return cudaSuccess;
-  if (one)
-    kOne<<<grid, Shape<G>::threads, kHeader + ring, s>>>(frames, itemBase, nFrames, totalItems,
-                                                         ring, ctl, *one);
-  else
-    kTable<<<grid, Shape<G>::threads, kHeader + ring, s>>>(frames, itemBase, nFrames, totalItems,
-                                                           ring, ctl, FrameArgs{});
+  const size_t smem = kHeader + ring;
+  if (hostFrames && nFrames == 1) {
+    kOne<<<grid, Shape<G>::threads, smem, s>>>(frames, itemBase, nFrames, totalItems, ring, ctl,
+                                               hostFrames[0]);
+  } else if (hostFrames && hostItemBase && nFrames <= kParamFrames) {
+    FrameTable tab;
+    memcpy(tab.itemBase, hostItemBase, sizeof(int) * (nFrames + 1));
+    memcpy(tab.f, hostFrames, sizeof(FrameArgs) * nFrames);
+    kParam<<<grid, Shape<G>::threads, smem, s>>>(frames, itemBase, nFrames, totalItems, ring, ctl,
+                                                 tab);
+  } else {
+    kTable<<<grid, Shape<G>::threads, smem, s>>>(frames, itemBase, nFrames, totalItems, ring, ctl,
+                                                 0);
+  }
   return cudaGetLastError();
 }
 
 template <int DT>
 cudaError_t launch_dt(const FrameArgs* frames, const int* itemBase, int nFrames, int totalItems,
-                      const TuneParams& tune, const LaunchCtl& ctl, const FrameArgs* one,
-                      cudaStream_t s) {
+                      const TuneParams& tune, const LaunchCtl& ctl, const FrameArgs* hostFrames,
+                      const int* hostItemBase, cudaStream_t s) {
   const int per = tune.ctasPerSm, g = tune.groups;
 #define DFB_SHAPE(G_, PER_)                                                                   \
   if (g == G_ && per == PER_)                                                                 \
     return launch_shape<DT, G_, PER_>(frames, itemBase, nFrames, totalItems, tune.ringKB, ctl,  \
-                                      one, s);
+                                      hostFrames, hostItemBase, s);
   DFB_SHAPE(1, 2)
   DFB_SHAPE(2, 2)
   DFB_SHAPE(1, 3)
@@ -1015,21 +1058,25 @@ TuneParams default_tune(int dtype) {
 cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int nFrames,
                              int totalItems, int totalTiles, bool accumulate, int dtype,
                              const TuneParams& tune, const LaunchCtl& ctl, const LongList& lng,
-                             const FrameArgs* hostOne, cudaStream_t s) {
-  const FrameArgs* one = nFrames == 1 ? hostOne : nullptr;
+                             const FrameArgs* hostFrames, const int* hostItemBase,
+                             cudaStream_t s) {
   cudaError_t e;
   switch (dtype) {
     case DFB_F32:
-      e = launch_dt<DFB_F32>(frames, itemBase, nFrames, totalItems, tune, ctl, one, s);
+      e = launch_dt<DFB_F32>(frames, itemBase, nFrames, totalItems, tune, ctl, hostFrames,
+                                 hostItemBase, s);
       break;
     case DFB_F16:
-      e = launch_dt<DFB_F16>(frames, itemBase, nFrames, totalItems, tune, ctl, one, s);
+      e = launch_dt<DFB_F16>(frames, itemBase, nFrames, totalItems, tune, ctl, hostFrames,
+                                 hostItemBase, s);
       break;
     case DFB_BF16:
-      e = launch_dt<DFB_BF16>(frames, itemBase, nFrames, totalItems, tune, ctl, one, s);
+      e = launch_dt<DFB_BF16>(frames, itemBase, nFrames, totalItems, tune, ctl, hostFrames,
+                                 hostItemBase, s);
       break;
     default:
-      e = launch_dt<DFB_FP8E4M3>(frames, itemBase, nFrames, totalItems, tune, ctl, one, s);
+      e = launch_dt<DFB_FP8E4M3>(frames, itemBase, nFrames, totalItems, tune, ctl, hostFrames,
+                                 hostItemBase, s);
       break;
   }
   // One-time set-up of the re-do kernel per device, done on any launch (so

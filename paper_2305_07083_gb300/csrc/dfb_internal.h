@@ -151,13 +151,15 @@ cudaError_t launch_bucket(const FragRec* grouped, const int* tileOff, int nTiles
 // of work items), all of storage dtype `dtype`, one persistent launch; then,
 // if the launch has long tiles, the exact re-do of the multi-fill items the
 // persistent kernel left (out-of-order depths); then, if `accumulate`, the
-// per-tile variance of `totalTiles` global tiles.  `hostOne`, for a launch
-// of one frame, is a host copy of frames[0]: the persistent kernel then
-// takes it by value as a kernel parameter (null: it reads `frames`).
+// per-tile variance of `totalTiles` global tiles.  `hostFrames` and
+// `hostItemBase` are host copies of `frames` and `itemBase` (or null): for a
+// launch of one frame, or of a few, the persistent kernel then takes them by
+// value as a kernel parameter instead of reading the global tables.
 cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int nFrames,
                              int totalItems, int totalTiles, bool accumulate, int dtype,
                              const TuneParams& tune, const LaunchCtl& ctl, const LongList& lng,
-                             const FrameArgs* hostOne, cudaStream_t s);
+                             const FrameArgs* hostFrames, const int* hostItemBase,
+                             cudaStream_t s);
 
 // Default launch shape for a dtype.
 TuneParams default_tune(int dtype);
