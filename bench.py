@@ -631,6 +631,8 @@ def main():
                          "(0 skips it)")
     ap.add_argument("--tune", default=None,
                     help="composite launch shape 'ringKB,ctasPerSm,groups' (default: the library's)")
+    ap.add_argument("--tune-f16", default=None,
+                    help="launch shape of the FP16 leg (default: --tune, else the library's)")
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="distinct resident frames (the 16-frame step cycles through them); "
                          "fewer frames only to keep profiler captures small")
@@ -772,7 +774,8 @@ def main():
             dst = torch.empty(fr.numel(), dtype=torch.float16, device=dev)
             D.dfb_convert_tiles(fr, dst, None, sc.n, sc.T * sc.T, D.DFB_F16, stream)
             f16.append(dst)
-        r16 = Runner(sc, f16, depth, D.DFB_F16, tune=tune)
+        tune16 = tuple(int(v) for v in args.tune_f16.split(",")) if args.tune_f16 else tune
+        r16 = Runner(sc, f16, depth, D.DFB_F16, tune=tune16)
         ms16, tm16, _, _ = timed(r16, args.steps, args.warmup, stream, dist, None)
         e2e16 = None
         if not args.no_e2e:

@@ -1047,11 +1047,11 @@ cudaError_t launch_dt(const FrameArgs* frames, const int* itemBase, int nFrames,
 
 }  // namespace
 
-// Measured on the 2048x2048 brick workload: FP32 items need the larger ring
-// of 2 CTAs per SM (two consumer groups each); the narrower formats fit a
-// full item into the ring of 3 CTAs per SM.
+// Measured on the 2048x2048 brick workload: FP32 fills need the larger ring
+// of 2 CTAs per SM (one consumer group each measured faster than two); the
+// narrower formats fit a full fill into the ring of 3 CTAs per SM.
 TuneParams default_tune(int dtype) {
-  if (dtype == DFB_F32) return TuneParams{110, 2, 2};
+  if (dtype == DFB_F32) return TuneParams{110, 2, 1};
   return TuneParams{72, 3, 1};
 }
 
