@@ -372,11 +372,14 @@ def peaks():
 # ----------------------------------------------------------------------------
 # batched form: 32 mixed frames, FP16, one persistent launch in a CUDA graph
 # ----------------------------------------------------------------------------
-def run_batched(dev, stream, steps, warmup, hbm_peak):
+def run_batched(dev, stream, steps, warmup, hbm_peak, n_frames=32, scene_device=None):
     import torch
     from harness import scenes
     from paper_2305_07083_gb300 import dfb as D
-    frames = scenes.batch_frames_torch(32, seed=0, device=dev)
+    frames = scenes.batch_frames_torch(n_frames, seed=0, device=scene_device or dev)
+    for f in frames:
+        f["rgba"] = f["rgba"].to(dev)
+        f["depth"] = f["depth"].to(dev)
     fpx = sum(len(f["tile_ids"]) * f["T"] * f["T"] for f in frames)
     flags = D.DFB_FLAG_WRITE_COLOR | D.DFB_FLAG_PACK_RGBA8
     keep, h16, h32 = [], [], []
@@ -442,8 +445,9 @@ def run_batched(dev, stream, steps, warmup, hbm_peak):
         D.dfb_destroy(h)
     del keep, frames
     torch.cuda.empty_cache()
-    return {"workload": "32 frames of 512x512 / 1024x1024 / 2048x2048 / 4096x1024 (8 each), "
-                        "64x64 tiles, 8 to 512 bricks per frame, BLEND_DEPTH, no accumulation",
+    return {"workload": "%d frames of 512x512 / 1024x1024 / 2048x2048 / 4096x1024 (in turn), "
+                        "64x64 tiles, 8 to 512 bricks per frame, BLEND_DEPTH, no accumulation"
+                        % n_frames,
             "fragment_pixels_per_step": fpx, "max_fragments_per_tile": int(counts.max()),
             "value": fpx / (batch_ms / 1e3), "unit": UNIT, "ms_per_step": batch_ms,
             "dtype": "f16 storage, f32 math",
@@ -633,6 +637,11 @@ def main():
                     help="composite launch shape 'ringKB,ctasPerSm,groups' (default: the library's)")
     ap.add_argument("--tune-f16", default=None,
                     help="launch shape of the FP16 leg (default: --tune, else the library's)")
+    ap.add_argument("--batch-frames", type=int, default=32,
+                    help="frames of the batched form (fewer only to keep profiler captures small)")
+    ap.add_argument("--scene-device", default=None,
+                    help="device that draws the batched form's scenes (default: the GPU; 'cpu' "
+                         "keeps profiler captures free of the generator's many small kernels)")
     ap.add_argument("--frames", type=int, default=N_FRAMES,
                     help="distinct resident frames (the 16-frame step cycles through them); "
                          "fewer frames only to keep profiler captures small")
@@ -823,7 +832,8 @@ def main():
         del frames
         torch.cuda.empty_cache()
         out.setdefault("variants", {})["batched_f16_graph"] = run_batched(
-            dev, stream, max(3, min(args.steps, 20)), args.warmup, hbm_peak)
+            dev, stream, max(3, min(args.steps, 20)), args.warmup, hbm_peak, args.batch_frames,
+            args.scene_device)
     if not args.no_batched and rank == 0:
         out.setdefault("variants", {})["bucket_1000_bricks"] = run_bucket_1000(dev, stream)
     if not args.no_batched and rank == 0:
