@@ -88,8 +88,10 @@ def test_long_fragment_lists(mode, n):
 @pytest.mark.parametrize("mode", MODES)
 def test_long_tiles_of_many_items_with_accumulation(mode):
     """Long tiles (more than 16 fragments) of 64x64 pixels are 16 work items
-    each, composited by the long-tile kernel next to ordinary tiles; two
-    accumulated frames exercise its reads of the running state."""
+    each, streamed through the composite in several fills next to ordinary
+    tiles (their random depths send them to the exact re-do kernel in
+    BLEND_DEPTH); two accumulated frames exercise both kernels' reads of the
+    running state."""
     counts = np.array([20, 3, 33, 0, 17, 16, 1, 25])
     fb = GpuFrameBuffer(256, 128, 64, mode)
     imgs = []

@@ -58,8 +58,8 @@ def test_two_calls_in_a_row_match_the_handle_path():
     small = scenes.random_scene(200, 136, 16, counts, seed=22, special_depths=True)
     calls.append((small, D.DFB_BLEND_ORDERED, D.DFB_F16, (0.2, 0.4, 0.6, 0.5)))
     assert small.n < big.n
-    # long tiles (more than 16 fragments) go through the long-tile kernel,
-    # whose list also lives in the fixed scratch
+    # long tiles (more than 16 fragments) stream in several fills; their
+    # re-do list also lives in the fixed scratch
     counts = np.random.default_rng(23).integers(0, 4, 4 * 3)
     counts[[1, 6, 10]] = [20, 37, 17]
     longs = scenes.random_scene(256, 192, 64, counts, seed=23, alpha_max=0.3)
