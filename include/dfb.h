@@ -350,14 +350,15 @@ DFB_API int dfb_convert_tiles(const float* src, void* dst, float* scales, int n_
                       int tile_pixels, int dtype, void* stream);
 
 /* Per-stage device timing (tracing).  While enabled, every dfb_end_frame /
-   dfb_end_frames call records CUDA events around its bucketing kernels and its
-   composite kernel on the launch stream.  dfb_read_timing waits for the
+   dfb_end_frames call records CUDA events around its bucketing kernel and its
+   persistent composite kernel on their streams (the re-do and per-tile
+   variance kernels that follow the composite are not included).  dfb_read_timing waits for the
    recorded events, adds them up since the last reset and, if reset != 0,
    starts a new sum.  For dfb_end_frames the batch is timed on its first
    handle.  Errors: INVALID_ARG, CUDA. */
 typedef struct dfb_timing {
   int32_t launches;     /* end-of-frame launches timed                        */
-  float bucket_ms;      /* total time of the bucketing kernels (K1)           */
+  float bucket_ms;      /* total time of the bucketing kernel (K1)            */
   float composite_ms;   /* total time of the composite kernel (K2/K3 + K4)    */
 } dfb_timing;
 DFB_API int dfb_set_timing(dfb_handle h, int enable);
@@ -405,9 +406,10 @@ DFB_API int dfb_composite_noalloc(int width, int height, int tile_size, int mode
 
 /* ---- Batched frames replayed from a CUDA graph ------------------------------
    A dfb_graph holds the device work of compositing the open frames of several
-   handles -- record upload done once, then per launch: the bucketing kernels
+   handles -- record upload done once, then per launch: the bucketing kernel
    and ONE persistent composite launch over every work item of every frame
-   (plus the per-tile variance sum) -- captured in a CUDA graph.  Each launch
+   (plus the re-do and per-tile variance kernels) -- captured in a CUDA
+   graph.  Each launch
    re-reads the fragment tiles through the same device pointers, so producers
    may rewrite their tiles in place between launches.  Frame arguments are
    frozen at creation: an accumulating handle keeps the frame count it had

@@ -1170,8 +1170,8 @@ int end_one(dfb_ctx* h, cudaStream_t s) {
   if (e == cudaSuccess)
     e = dfb::launch_composite(dFa, dItemBase, 1, items, h->nTiles,
                               (h->cfg.flags & DFB_FLAG_ACCUMULATE) != 0, h->cfg.dtype, tune_of(h),
-                              ctl_of(h, b.redo), lng, &hdr->fa, hdr->itemBase, s);
-  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
+                              ctl_of(h, b.redo), lng, &hdr->fa, hdr->itemBase,
+                              ev ? ev[3] : nullptr, s);
   if (e == cudaSuccess) e = cudaEventRecord(b.released, s);
   if (e == cudaSuccess) e = cudaEventRecord(h->frameDone, s);
   b.used = true;
@@ -1267,8 +1267,7 @@ int end_batch(dfb_ctx* const* hs, int n, cudaStream_t s) {
   if (e == cudaSuccess)
     e = dfb::launch_composite(b.dFrames, b.dItemBase, n, items, tileBase, anyAcc, dtype,
                               tune_of(hs[0]), ctl_of(hs[0], b.redo), lng, b.hFrames, b.hItemBase,
-                              s);
-  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], s);
+                              ev ? ev[3] : nullptr, s);
   if (e == cudaSuccess) e = cudaEventRecord(b.released, s);
   b.used = true;
   hs[0]->launches += 1 + (anyAcc ? 2 : 1) + (lng.items ? 1 : 0);
@@ -1611,7 +1610,8 @@ int graph_capture(dfb_graph_t* g) {
   // per-device launch set-up happens outside the capture (no work is enqueued)
   const dfb::LaunchCtl ctl{2000000000ull, -1, g->err, g->redo};
   cudaError_t e = dfb::launch_composite(g->dFrames, g->dItemBase, 1, 0, 0, false, g->dtype, tune,
-                                        ctl, dfb::LongList{}, nullptr, nullptr, g->capStream);
+                                        ctl, dfb::LongList{}, nullptr, nullptr, nullptr,
+                                        g->capStream);
   if (e != cudaSuccess) return cuda_status(e);
   e = cudaStreamBeginCapture(g->capStream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_status(e);
@@ -1620,7 +1620,7 @@ int graph_capture(dfb_graph_t* g) {
   if (le == cudaSuccess)
     le = dfb::launch_composite(g->dFrames, g->dItemBase, (int)g->hs.size(), g->items, g->nTiles,
                                g->anyAcc, g->dtype, tune, ctl, g->lng, g->hostFrames.data(),
-                               g->hostItemBase.data(), g->capStream);
+                               g->hostItemBase.data(), nullptr, g->capStream);
   e = cudaStreamEndCapture(g->capStream, &g->graph);
   if (le != cudaSuccess) return cuda_status(le);
   if (e != cudaSuccess) return cuda_status(e);

@@ -1059,7 +1059,7 @@ cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int n
                              int totalItems, int totalTiles, bool accumulate, int dtype,
                              const TuneParams& tune, const LaunchCtl& ctl, const LongList& lng,
                              const FrameArgs* hostFrames, const int* hostItemBase,
-                             cudaStream_t s) {
+                             cudaEvent_t afterMain, cudaStream_t s) {
   cudaError_t e;
   switch (dtype) {
     case DFB_F32:
@@ -1079,6 +1079,7 @@ cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int n
                                  hostItemBase, s);
       break;
   }
+  if (e == cudaSuccess && afterMain) e = cudaEventRecord(afterMain, s);
   // One-time set-up of the re-do kernel per device, done on any launch (so
   // that it never first happens inside a stream capture).
   static int sms[64] = {0};

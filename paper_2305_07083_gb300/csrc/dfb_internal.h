@@ -155,11 +155,13 @@ cudaError_t launch_bucket(const FragRec* grouped, const int* tileOff, int nTiles
 // `hostItemBase` are host copies of `frames` and `itemBase` (or null): for a
 // launch of one frame, or of a few, the persistent kernel then takes them by
 // value as a kernel parameter instead of reading the global tables.
+// `afterMain`, if given, is recorded on `s` right after the persistent
+// kernel (before the re-do and variance kernels), for tracing.
 cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int nFrames,
                              int totalItems, int totalTiles, bool accumulate, int dtype,
                              const TuneParams& tune, const LaunchCtl& ctl, const LongList& lng,
                              const FrameArgs* hostFrames, const int* hostItemBase,
-                             cudaStream_t s);
+                             cudaEvent_t afterMain, cudaStream_t s);
 
 // Default launch shape for a dtype.
 TuneParams default_tune(int dtype);

@@ -298,7 +298,7 @@ int composite_noalloc(int width, int height, int tile_size, int mode, int dtype,
   if (e != cudaSuccess) return DFB_ERR_CUDA;
   const dfb::LaunchCtl ctl{2000000000ull, -1, &dHdr->err, redo};
   e = dfb::launch_composite(&dHdr->fa, dHdr->itemBase, 1, hdr.itemBase[1], nTiles, false, dtype,
-                           dfb::default_tune(dtype), ctl, lng, &hdr.fa, hdr.itemBase, s);
+                           dfb::default_tune(dtype), ctl, lng, &hdr.fa, hdr.itemBase, nullptr, s);
   if (e != cudaSuccess) return DFB_ERR_CUDA;
   // The launch's error word: a wait that ran out (the frame is then
   // incomplete) or, in the checked build, a failed device-side check.  The
