@@ -256,13 +256,14 @@ class Runner:
         self.keys = np.ascontiguousarray(sc.keys, np.float32)
         self.rptr = [D.pool_pointers(fr, sc.n, rb) for fr in frames]
         self.dptr = D.pool_pointers(depth, sc.n, P * 4)
+        self.scales = None  # FP8: one scale per fragment tile
 
     def step(self, stream):
         D = self.D
         for f in range(N_FRAMES):
             D.dfb_begin_frame(self.h, f > 0)
             D.dfb_submit_tiles(self.h, self.tile_ids, self.keys, self.rptr[f % len(self.rptr)],
-                               self.dptr, None, self.where)
+                               self.dptr, self.scales, self.where)
             D.dfb_end_frame(self.h, stream)
 
     def serial_bucket_ms(self, stream, frames=16):
@@ -275,7 +276,7 @@ class Runner:
         for f in range(frames):
             D.dfb_begin_frame(self.h, 0)
             D.dfb_submit_tiles(self.h, self.tile_ids, self.keys, self.rptr[f % len(self.rptr)],
-                               self.dptr, None, self.where)
+                               self.dptr, self.scales, self.where)
             D.dfb_end_frame(self.h, stream)
             D.dfb_sync(self.h)
         D.dfb_set_timing(self.h, False)
@@ -461,6 +462,77 @@ def run_batched(dev, stream, steps, warmup, hbm_peak, n_frames=32, scene_device=
                                   "composite + re-do kernel), CUDA events on the stream",
                          "bytes": "12 B per fragment-pixel (FP16 RGBA + FP32 depth) + 20 B "
                                   "per frame pixel (FP32 colour + RGBA8)"}}
+
+
+# ----------------------------------------------------------------------------
+# precision form: 4096x1024, 128 bricks, FP32 / FP16 / BF16 / FP8 storage
+# ----------------------------------------------------------------------------
+def run_precision_forms(dev, stream, steps, warmup, hbm_peak):
+    """The 4096x1024 / 128-brick frame in every storage dtype, each a 16-frame
+    accumulation step like the headline: composite launch time, algorithmic
+    bytes and roofline per dtype, and the colour's max-abs / RMS difference
+    from the FP32 path (which is within 3e-7 of the FP64 oracle)."""
+    import torch
+    from harness import scenes
+    from paper_2305_07083_gb300 import dfb as D
+    W, H, T = 4096, 1024, 64
+    hi = (2.0, 1.0, 1.0)
+    cam = scenes.orbit_camera(W, H, 0, radius=1.2, hi=hi)
+    tid, key, rgba, depth = scenes.brick_scene_torch(W, H, T, scenes.brick_grid((8, 4, 4), hi=hi),
+                                                     cam, 0, dev)
+    sc = _TileSet(W, H, T, tid, key)
+    n, P = sc.n, T * T
+    out, ref = {}, None
+    for name, dt in (("f32", D.DFB_F32), ("f16", D.DFB_F16), ("bf16", D.DFB_BF16),
+                     ("fp8e4m3", D.DFB_FP8E4M3)):
+        scales = None
+        if dt == D.DFB_F32:
+            stored = rgba
+        else:
+            tdt = {D.DFB_F16: torch.float16, D.DFB_BF16: torch.bfloat16,
+                   D.DFB_FP8E4M3: torch.uint8}[dt]
+            stored = torch.empty((n, P, 4), dtype=tdt, device=dev)
+            sc_dev = torch.empty(n, dtype=torch.float32, device=dev) if dt == D.DFB_FP8E4M3 else None
+            D.dfb_convert_tiles(rgba, stored, sc_dev, n, P, dt, stream)
+            if sc_dev is not None:
+                scales = sc_dev.cpu().numpy()
+        run = Runner(sc, [stored], depth, dt)
+        run.scales = scales
+        ms, tm, _, _ = timed(run, steps, warmup, stream)
+        st = D.dfb_get_stats(run.h)
+        comp = tm["composite_ms"] / max(tm["launches"], 1)
+        px = W * H
+        state_avg = ((16 + 32 + 4) * px + (N_FRAMES - 1) * (16 + 64 + 4) * px) / N_FRAMES
+        algo = st["fragment_bytes"] + state_avg
+        # one frame's colour for the comparison with the FP32 path
+        D.dfb_begin_frame(run.h, 0)
+        D.dfb_submit_tiles(run.h, run.tile_ids, run.keys, run.rptr[0], run.dptr, scales,
+                           D.DFB_PTR_DEVICE)
+        D.dfb_end_frame(run.h, stream)
+        col = np.empty((H, W, 4), np.float32)
+        D.dfb_read_color(run.h, col)
+        run.close()
+        e = {}
+        if ref is None:
+            ref = col.astype(np.float64)
+        else:
+            d = (col.astype(np.float64) - ref).reshape(-1, 4)
+            e = {"max_abs_vs_f32_rgba": [float(v) for v in np.abs(d).max(axis=0)],
+                 "rms_vs_f32_rgba": [float(v) for v in np.sqrt((d * d).mean(axis=0))]}
+        out[name] = dict({"bytes_per_fragment_pixel": 4 * D.ELEMENT_BYTES[dt] + 4,
+                          "value": n * P * N_FRAMES * steps / (ms / 1e3),
+                          "ms_per_step": ms / steps, "avg_launch_ms": comp,
+                          "algorithmic_bytes_per_launch": algo,
+                          "achieved_gbs": algo / (comp / 1e3) / 1e9,
+                          "frac": algo / (comp / 1e3) / 1e9 / hbm_peak}, **e)
+        del stored
+    for name in out:
+        out[name]["speedup_vs_f32"] = out["f32"]["ms_per_step"] / out[name]["ms_per_step"]
+    del rgba, depth
+    torch.cuda.empty_cache()
+    return {"workload": "4096x1024, 64x64 tiles, 128 bricks (8x4x4 of a 2x1x1 box), seeded orbit "
+                        "camera, BLEND_DEPTH, 16-frame accumulation with variance and RGBA8",
+            "fragments": int(n), "unit": UNIT, "forms": out}
 
 
 # ----------------------------------------------------------------------------
@@ -836,6 +908,9 @@ def main():
             args.scene_device)
     if not args.no_batched and rank == 0:
         out.setdefault("variants", {})["bucket_1000_bricks"] = run_bucket_1000(dev, stream)
+    if not args.no_batched and rank == 0:
+        out.setdefault("variants", {})["precision_4096x1024"] = run_precision_forms(
+            dev, stream, max(3, min(args.steps, 20)), args.warmup, hbm_peak)
     if not args.no_batched and rank == 0:
         out.setdefault("variants", {})["image_parallel_average"] = run_image_parallel(
             dev, stream, max(3, min(args.steps, 50)), args.warmup, hbm_peak)
