@@ -193,11 +193,13 @@ def gather_tiles(local, own: TileOwnership, group=None, dst=0):
         parts = [tiles]
     else:
         t = torch.from_numpy(tiles.view(np.uint8).reshape(-1)).clone()
+        if not _staged(group):  # NCCL gathers device buffers
+            t = t.to(torch.device("cuda", torch.cuda.current_device()))
         parts_t = [torch.empty_like(t) for _ in range(world)] if rank == dst else None
         dist.gather(t, parts_t, dst=dst, group=group)
         if rank != dst:
             return None
-        parts = [p.numpy().view(loc.dtype).reshape(maxn, T, T, C) for p in parts_t]
+        parts = [p.cpu().numpy().view(loc.dtype).reshape(maxn, T, T, C) for p in parts_t]
     frame = np.zeros((own.tiles_y * T, own.tiles_x * T, C), loc.dtype)
     for r in range(world):
         for i, g in enumerate(own.owned[r]):
