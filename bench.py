@@ -465,6 +465,62 @@ def run_batched(dev, stream, steps, warmup, hbm_peak, n_frames=32, scene_device=
 
 
 # ----------------------------------------------------------------------------
+# tile ownership across ranks: one frame rendered by all ranks
+# ----------------------------------------------------------------------------
+def run_tile_ownership(dev, stream, sc, frame, depth, steps, warmup, dist, world, rank):
+    """The 2048x2048 frame 0 composited through the paper's distribution:
+    rank r holds every world-th fragment tile (any rank renders for any
+    tile), sends each to its tile's owner (round-robin ownership) in one
+    all-to-all, the owners composite their tiles, and the RGBA8 frame is
+    gathered to rank 0.  Strong scaling: the whole job is one frame per
+    step.  Timed per step with CUDA events (exchange + composite) and on the
+    host (gather), the slowest rank's times."""
+    import torch
+    from paper_2305_07083_gb300 import dfb as D, distributed as DD
+    mine = np.arange(sc.n)[rank::world]
+    idx = torch.as_tensor(mine, dtype=torch.long, device=dev)
+    r = frame.index_select(0, idx).contiguous()
+    d = depth.index_select(0, idx).contiguous()
+    tid = np.ascontiguousarray(sc.tile_ids[mine], np.int32)
+    key = np.ascontiguousarray(sc.keys[mine], np.float32)
+    fb = DD.DistributedFrameBuffer(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH, D.DFB_F32,
+                                   D.DFB_FLAG_WRITE_COLOR | D.DFB_FLAG_PACK_RGBA8)
+
+    def step():
+        fb.composite(tid, key, r, d, stream=stream)
+
+    for _ in range(warmup):
+        step()
+        fb.gather("rgba8")
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    comp_ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist, dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        fb.gather("rgba8")
+    gather_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / steps, dist, dev)
+    fb.close()
+    fpx = sc.fragment_pixels()
+    rec = 16 + sc.T * sc.T * 20
+    return {"workload": "frame 0 of the 2048x2048 / 64-brick workload, rank r holding every "
+                        "%d-th fragment tile, round-robin tile ownership, FP32, BLEND_DEPTH, "
+                        "colour + RGBA8 (no accumulation)" % world,
+            "ranks": world, "scaling": "strong", "unit": UNIT,
+            "value": fpx / ((comp_ms + gather_ms) / 1e3),
+            "exchange_and_composite_ms": comp_ms, "gather_rgba8_ms": gather_ms,
+            "exchange_bytes_per_rank": int(len(mine) * rec * (world - 1) / world),
+            "note": "with one rank nothing is exchanged; the gather reorders the tiles on the "
+                    "device and reads the RGBA8 frame back to host memory once per step"}
+
+
+# ----------------------------------------------------------------------------
 # precision form: 4096x1024, 128 bricks, FP32 / FP16 / BF16 / FP8 storage
 # ----------------------------------------------------------------------------
 def run_precision_forms(dev, stream, steps, warmup, hbm_peak):
@@ -888,16 +944,19 @@ def main():
         c16 = tm16["composite_ms"] / max(tm16["launches"], 1)
         ab16 = st16["fragment_bytes"] + state_avg
         a16 = ab16 / (c16 / 1e3) / 1e9
-        out["variants"] = {"f16": {
+        out.setdefault("variants", {})["f16"] = {
             "value": world * fpx_frame * N_FRAMES * args.steps / (ms16 / 1e3),
             "ms_per_step": ms16 / args.steps, "speedup_vs_f32": ms / ms16,
             "roofline": {"achieved": a16, "frac": a16 / hbm_peak, "avg_launch_ms": c16,
                          "traffic": ncu_traffic("composite_f16_2048.md"),
                          "kernel": "k_composite<BLEND_DEPTH,F16>",
                          "algorithmic_bytes_per_launch": ab16},
-            "e2e": e2e16}}
+            "e2e": e2e16}
         r16.close()
         del f16
+    out.setdefault("variants", {})["tile_ownership"] = run_tile_ownership(
+        dev, stream, sc, frames[0], depth, max(3, min(args.steps, 20)), args.warmup, dist, world,
+        rank)
     run.close()
     frame0 = frames[0].cpu().numpy() if pool is not None else None
     if not args.no_batched and rank == 0:

@@ -151,62 +151,67 @@ def exchange(tile_ids, keys, rgba, depth, own: TileOwnership, scales=None, group
     rank, world = _rank_world(group)
     if world != own.world:
         raise ValueError("ownership is for %d ranks, the group has %d" % (own.world, world))
+    if world == 1:  # every tile is this rank's: nothing moves
+        sc = np.ones(len(tile_ids), np.float32) if scales is None else np.asarray(scales, np.float32)
+        return (np.asarray(tile_ids, np.int32), np.asarray(keys, np.float32), sc, rgba, depth)
     order, counts = route(tile_ids, own)
     packed, rec = pack_records(tile_ids, keys, rgba, depth, scales, order)
-    if world == 1:
-        buf = packed
-    else:
-        staged = _staged(group)
-        dev = torch.device("cpu") if staged else packed.device
-        send_counts = torch.as_tensor(counts, dtype=torch.int64, device=dev)
-        recv_counts = torch.empty(world, dtype=torch.int64, device=dev)
-        dist.all_to_all_single(recv_counts, send_counts, group=group)
-        rc = recv_counts.cpu().numpy()
-        src = packed.cpu() if staged else packed
-        buf = torch.empty((int(rc.sum()), rec), dtype=torch.uint8, device=src.device)
-        dist.all_to_all_single(buf, src, [int(v) for v in rc], [int(v) for v in counts],
-                               group=group)
-        buf = buf.to(rgba.device)
+    staged = _staged(group)
+    dev = torch.device("cpu") if staged else packed.device
+    send_counts = torch.as_tensor(counts, dtype=torch.int64, device=dev)
+    recv_counts = torch.empty(world, dtype=torch.int64, device=dev)
+    dist.all_to_all_single(recv_counts, send_counts, group=group)
+    rc = recv_counts.cpu().numpy()
+    src = packed.cpu() if staged else packed
+    buf = torch.empty((int(rc.sum()), rec), dtype=torch.uint8, device=src.device)
+    dist.all_to_all_single(buf, src, [int(v) for v in rc], [int(v) for v in counts],
+                           group=group)
+    buf = buf.to(rgba.device)
     return unpack_records(buf, tuple(rgba.shape[1:]), rgba.dtype, tuple(depth.shape[1:]))
 
 
 def gather_tiles(local, own: TileOwnership, group=None, dst=0):
     """Assemble a frame from the tiles every rank owns.  `local` is this
-    rank's framebuffer image (H_r x W_r x C, numpy or tensor, laid out as
-    TileOwnership.local_grid); returns the H x W x C frame on `dst` (None on
-    the other ranks)."""
+    rank's framebuffer image (H_r x W_r x C or H_r x W_r; numpy array or
+    tensor on any device, laid out as TileOwnership.local_grid); returns the
+    H x W (x C) frame as a numpy array on `dst` (None on the other ranks).
+    The tiles are reordered on the device that holds `local`."""
     import torch
     import torch.distributed as dist
     rank, world = _rank_world(group)
     T = own.T
-    loc = local.cpu().numpy() if hasattr(local, "cpu") else np.asarray(local)
-    C = loc.shape[2] if loc.ndim == 3 else 1
-    loc = loc.reshape(loc.shape[0], loc.shape[1], C)
-    cols, _ = own.local_grid(rank)
-    mine = own.owned[rank]
+    loc = local if torch.is_tensor(local) else torch.from_numpy(np.ascontiguousarray(local))
+    flat = loc.dim() == 2
+    if flat:
+        loc = loc.unsqueeze(-1)
+    C = loc.shape[2]
+    cols, rows = own.local_grid(rank)
+    mine = len(own.owned[rank])
     maxn = max(1, max(len(o) for o in own.owned))
-    tiles = np.zeros((maxn, T, T, C), loc.dtype)
-    for i in range(len(mine)):
-        r, c = divmod(i, cols)
-        tiles[i] = loc[r * T:(r + 1) * T, c * T:(c + 1) * T]
+    grid = loc[:rows * T, :cols * T].reshape(rows, T, cols, T, C).permute(0, 2, 1, 3, 4)
+    tiles = torch.zeros((maxn, T, T, C), dtype=loc.dtype, device=loc.device)
+    tiles[:mine] = grid.reshape(rows * cols, T, T, C)[:mine]
     if world == 1:
         parts = [tiles]
     else:
-        t = torch.from_numpy(tiles.view(np.uint8).reshape(-1)).clone()
-        if not _staged(group):  # NCCL gathers device buffers
+        t = tiles.reshape(-1).view(torch.uint8)
+        if _staged(group):
+            t = t.cpu()
+        elif not t.is_cuda:  # NCCL gathers device buffers
             t = t.to(torch.device("cuda", torch.cuda.current_device()))
         parts_t = [torch.empty_like(t) for _ in range(world)] if rank == dst else None
         dist.gather(t, parts_t, dst=dst, group=group)
         if rank != dst:
             return None
-        parts = [p.cpu().numpy().view(loc.dtype).reshape(maxn, T, T, C) for p in parts_t]
-    frame = np.zeros((own.tiles_y * T, own.tiles_x * T, C), loc.dtype)
+        parts = [p.to(loc.device).view(loc.dtype).reshape(maxn, T, T, C) for p in parts_t]
+    by_tile = torch.zeros((own.n_tiles, T, T, C), dtype=loc.dtype, device=loc.device)
     for r in range(world):
-        for i, g in enumerate(own.owned[r]):
-            ty, tx = divmod(int(g), own.tiles_x)
-            frame[ty * T:(ty + 1) * T, tx * T:(tx + 1) * T] = parts[r][i]
-    frame = frame[:own.H, :own.W]
-    return frame if C > 1 else frame[..., 0]
+        idx = torch.as_tensor(own.owned[r], dtype=torch.long, device=loc.device)
+        by_tile.index_copy_(0, idx, parts[r][:len(own.owned[r])])
+    frame = by_tile.reshape(own.tiles_y, own.tiles_x, T, T, C).permute(0, 2, 1, 3, 4)
+    frame = frame.reshape(own.tiles_y * T, own.tiles_x * T, C)[:own.H, :own.W]
+    out = frame.contiguous().cpu().numpy()
+    return out[..., 0] if flat else out
 
 
 class DistributedFrameBuffer:
@@ -234,9 +239,9 @@ class DistributedFrameBuffer:
         """One frame: this rank's fragment tiles (global tile ids; rgba and
         depth device tensors of shape (n, T*T, 4) and (n, T*T)) go to their
         owners; this rank composites the fragments it owns."""
-        if self.keep:
-            D.dfb_sync(self.h)  # the previous frame's tiles are released below
         tid, key, scl, r, d = exchange(tile_ids, keys, rgba, depth, self.own, scales, self.group)
+        if self.keep and (self.keep[0] is not r or self.keep[1] is not d):
+            D.dfb_sync(self.h)  # the previous frame's tiles are released below
         self.keep = [r, d]  # the library borrows the device tiles until the frame is done
         n = len(tid)
         P = self.T * self.T
@@ -250,15 +255,22 @@ class DistributedFrameBuffer:
         return n
 
     def _local(self, what):
+        """This rank's framebuffer image as a device tensor (RGBA8 as int32)."""
+        import torch
         lw, lh = self.own.local_size(self.rank)
+        dev = torch.device("cuda", torch.cuda.current_device())
         if what == "rgba8":
-            out = np.empty((lh, lw), np.uint32)
+            out = torch.empty((lh, lw), dtype=torch.int32, device=dev)
             D.dfb_read_rgba8(self.h, out)
-            return out
-        out = np.empty((lh, lw, 4), np.float32)
-        (D.dfb_read_color if what == "color" else D.dfb_read_accum)(self.h, out)
+        else:
+            out = torch.empty((lh, lw, 4), dtype=torch.float32, device=dev)
+            (D.dfb_read_color if what == "color" else D.dfb_read_accum)(self.h, out)
+        # the read is queued on the frame's stream; torch works on its own
+        torch.cuda.synchronize()
         return out
 
     def gather(self, what="rgba8", dst=0):
-        """The finished frame ("rgba8", "color" or "accum") on rank `dst`."""
-        return gather_tiles(self._local(what), self.own, self.group, dst)
+        """The finished frame ("rgba8" as uint32, "color" or "accum" as
+        float32 RGBA) as a numpy array on rank `dst` (None elsewhere)."""
+        frame = gather_tiles(self._local(what), self.own, self.group, dst)
+        return frame.view(np.uint32) if (frame is not None and what == "rgba8") else frame
