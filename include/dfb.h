@@ -352,10 +352,13 @@ DFB_API int dfb_convert_tiles(const float* src, void* dst, float* scales, int n_
 /* Per-stage device timing (tracing).  While enabled, every dfb_end_frame /
    dfb_end_frames call records CUDA events around its bucketing kernel and its
    persistent composite kernel on their streams (the re-do and per-tile
-   variance kernels that follow the composite are not included).  dfb_read_timing waits for the
-   recorded events, adds them up since the last reset and, if reset != 0,
-   starts a new sum.  For dfb_end_frames the batch is timed on its first
-   handle.  Errors: INVALID_ARG, CUDA. */
+   variance kernels that follow the composite are not included).  The events
+   sit between kernels that otherwise start while the kernel before them
+   drains (programmatic launches), so a frame takes a few microseconds longer
+   while timing is on.  dfb_read_timing waits for the recorded events, adds
+   them up since the last reset and, if reset != 0, starts a new sum.  For
+   dfb_end_frames the batch is timed on its first handle.  Errors:
+   INVALID_ARG, CUDA. */
 typedef struct dfb_timing {
   int32_t launches;     /* end-of-frame launches timed                        */
   float bucket_ms;      /* total time of the bucketing kernel (K1)            */

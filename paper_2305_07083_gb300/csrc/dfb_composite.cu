@@ -46,6 +46,8 @@
 // drains its own bulk copies and returns.
 #include <string.h>
 
+#include <utility>
+
 #include "dfb_device.cuh"
 #include "dfb_internal.h"
 
@@ -884,6 +886,10 @@ __global__ void __launch_bounds__(Shape<G>::threads, PER)
     *abort = 0;
     fence_barrier_init();
   }
+  // The set-up above reads nothing that earlier kernels write; with a
+  // programmatic launch it overlaps the end of the kernel before.
+  grid_dependency_wait();
+  allow_dependents();
   __syncthreads();
   if (threadIdx.x >= G * kP)
     producer<DT, G, FR>(frames, itemBase, nFrames, totalItems, ctl, ring, ringBytes, metas, queue, qLoc,
@@ -944,6 +950,8 @@ __global__ void __launch_bounds__(kP, 2) k_composite_redo(const FrameArgs* __res
 // partials in slot order.
 __global__ void k_tile_variance(const FrameArgs* __restrict__ frames, int nFrames,
                                 int totalTiles) {
+  grid_dependency_wait();  // the composite's partials
+  allow_dependents();
   const int gt = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (gt >= totalTiles) return;
@@ -966,6 +974,25 @@ __global__ void k_tile_variance(const FrameArgs* __restrict__ frames, int nFrame
     const int w = min(T, A->W - tx * T), h = min(T, A->H - ty * T);
     A->tileVar[tile] = sum / (3.0f * (float)(w * h));
   }
+}
+
+// Launch with programmatic stream serialisation: the kernel's blocks may be
+// scheduled before the previous kernel in the stream has finished; the
+// kernel's grid_dependency_wait() keeps its dependent accesses after it.
+template <typename... Params, typename... Args>
+cudaError_t launch_programmatic(void (*kernel)(Params...), int grid, int threads, size_t smem,
+                                cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 template <int DT, int G, int PER>
@@ -1011,20 +1038,18 @@ cudaError_t launch_shape(const FrameArgs* frames, const int* itemBase, int nFram
   if (grid > totalItems) grid = totalItems;
   if (grid < 1) return cudaSuccess;
   const size_t smem = kHeader + ring;
-  if (hostFrames && nFrames == 1) {
-    kOne<<<grid, Shape<G>::threads, smem, s>>>(frames, itemBase, nFrames, totalItems, ring, ctl,
-                                               hostFrames[0]);
-  } else if (hostFrames && hostItemBase && nFrames <= kParamFrames) {
+  if (hostFrames && nFrames == 1)
+    return launch_programmatic(kOne, grid, Shape<G>::threads, smem, s, frames, itemBase, nFrames,
+                               totalItems, ring, ctl, hostFrames[0]);
+  if (hostFrames && hostItemBase && nFrames <= kParamFrames) {
     FrameTable tab;
     memcpy(tab.itemBase, hostItemBase, sizeof(int) * (nFrames + 1));
     memcpy(tab.f, hostFrames, sizeof(FrameArgs) * nFrames);
-    kParam<<<grid, Shape<G>::threads, smem, s>>>(frames, itemBase, nFrames, totalItems, ring, ctl,
-                                                 tab);
-  } else {
-    kTable<<<grid, Shape<G>::threads, smem, s>>>(frames, itemBase, nFrames, totalItems, ring, ctl,
-                                                 0);
+    return launch_programmatic(kParam, grid, Shape<G>::threads, smem, s, frames, itemBase,
+                               nFrames, totalItems, ring, ctl, tab);
   }
-  return cudaGetLastError();
+  return launch_programmatic(kTable, grid, Shape<G>::threads, smem, s, frames, itemBase, nFrames,
+                             totalItems, ring, ctl, 0);
 }
 
 template <int DT>
@@ -1124,8 +1149,8 @@ cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int n
     e = cudaGetLastError();
   }
   if (e != cudaSuccess || !accumulate || totalTiles < 1) return e;
-  k_tile_variance<<<(totalTiles * 32 + 255) / 256, 256, 0, s>>>(frames, nFrames, totalTiles);
-  return cudaGetLastError();
+  return launch_programmatic(k_tile_variance, (totalTiles * 32 + 255) / 256, 256, 0, s, frames,
+                             nFrames, totalTiles);
 }
 
 }  // namespace dfb

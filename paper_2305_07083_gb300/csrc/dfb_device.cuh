@@ -203,6 +203,20 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation may start while the kernel before it in the stream is still
+// running; grid_dependency_wait() returns once that kernel has completed and
+// its memory operations are visible (at once for a plain launch), so it comes
+// before the first global access that depends on earlier work.
+// allow_dependents() lets the next such kernel in the stream be scheduled
+// (its blocks then wait in their own grid_dependency_wait()).
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void allow_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // One-dimensional bulk copy global -> shared, completing on `bar`.
 // Both addresses 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
