@@ -407,6 +407,16 @@ DFB_API int dfb_composite_noalloc(int width, int height, int tile_size, int mode
                                   const float* scales, const float* background,
                                   float* color_out, uint32_t* rgba8_out, void* stream);
 
+/* Failure detection of dfb_composite_noalloc, for tests of its timeout path
+   (process-wide settings, like the call's scratch).  dfb_noalloc_set_wait_limit
+   bounds every wait inside its kernels (default 2 s); dfb_noalloc_inject_stall
+   makes the next call leave work item `item` unfilled (-1: off), so that its
+   consumers' wait runs out after the limit and the call returns
+   DFB_ERR_TIMEOUT with incomplete outputs; the setting is used up by that
+   call.  Errors: INVALID_ARG (a limit <= 0 or > 3600 s, item < -1). */
+DFB_API int dfb_noalloc_set_wait_limit(double seconds);
+DFB_API int dfb_noalloc_inject_stall(int item);
+
 /* ---- Batched frames replayed from a CUDA graph ------------------------------
    A dfb_graph holds the device work of compositing the open frames of several
    handles -- record upload done once, then per launch: the bucketing kernel

@@ -15,12 +15,18 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
 #include <vector>
 
 #include "dfb_internal.h"
 
 namespace {
+
+// Failure-detection settings of the calls (process-wide): the bound on every
+// device-side wait, and a work item that the next call leaves unfilled.
+std::atomic<unsigned long long> g_waitNs{2000000000ull};
+std::atomic<int> g_stallItem{-1};
 
 using dfb::FragRec;
 using dfb::FrameArgs;
@@ -296,7 +302,7 @@ int composite_noalloc(int width, int height, int tile_size, int mode, int dtype,
   e = cudaMemcpyAsync(dHdr, &hdr, sizeof(Header), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return DFB_ERR_CUDA;
-  const dfb::LaunchCtl ctl{2000000000ull, -1, &dHdr->err, redo};
+  const dfb::LaunchCtl ctl{g_waitNs.load(), g_stallItem.exchange(-1), &dHdr->err, redo};
   e = dfb::launch_composite(&dHdr->fa, dHdr->itemBase, 1, hdr.itemBase[1], nTiles, false, dtype,
                            dfb::default_tune(dtype), ctl, lng, &hdr.fa, hdr.itemBase, nullptr, s);
   if (e != cudaSuccess) return DFB_ERR_CUDA;
@@ -313,6 +319,18 @@ int composite_noalloc(int width, int height, int tile_size, int mode, int dtype,
 }
 
 }  // namespace
+
+extern "C" int dfb_noalloc_set_wait_limit(double seconds) {
+  if (!(seconds > 0.0) || seconds > 3600.0) return DFB_ERR_INVALID_ARG;
+  g_waitNs.store((unsigned long long)(seconds * 1e9));
+  return DFB_OK;
+}
+
+extern "C" int dfb_noalloc_inject_stall(int item) {
+  if (item < -1) return DFB_ERR_INVALID_ARG;
+  g_stallItem.store(item);
+  return DFB_OK;
+}
 
 extern "C" int dfb_composite_noalloc(int width, int height, int tile_size, int mode, int dtype,
                                      int n, const int* tile_ids, const float* order_keys,

@@ -115,6 +115,8 @@ def lib():
         "dfb_set_tuning": (C.c_int, [H, C.c_int, C.c_int, C.c_int]),
         "dfb_set_wait_limit": (C.c_int, [H, C.c_double]),
         "dfb_inject_stall": (C.c_int, [H, C.c_int]),
+        "dfb_noalloc_set_wait_limit": (C.c_int, [C.c_double]),
+        "dfb_noalloc_inject_stall": (C.c_int, [C.c_int]),
         "dfb_graph_create": (C.c_int, [P, C.c_int, C.POINTER(H)]),
         "dfb_graph_launch": (C.c_int, [H, P]),
         "dfb_graph_set_tuning": (C.c_int, [H, C.c_int, C.c_int, C.c_int]),
@@ -394,6 +396,14 @@ def dfb_set_wait_limit(h, seconds):
 
 def dfb_inject_stall(h, item):
     return _check(lib().dfb_inject_stall(h, int(item)), "dfb_inject_stall")
+
+
+def dfb_noalloc_set_wait_limit(seconds):
+    return _check(lib().dfb_noalloc_set_wait_limit(float(seconds)), "dfb_noalloc_set_wait_limit")
+
+
+def dfb_noalloc_inject_stall(item):
+    return _check(lib().dfb_noalloc_inject_stall(int(item)), "dfb_noalloc_inject_stall")
 
 
 def dfb_set_tuning(h, ring_kb=0, ctas_per_sm=0, groups=0):

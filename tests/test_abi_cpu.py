@@ -222,6 +222,13 @@ def test_wait_limit_and_stall_arguments():
         assert code_of(D.dfb_inject_stall, h, -5) == D.DFB_ERR_INVALID_ARG
     finally:
         D.dfb_destroy(h)
+    # the allocation-free call's process-wide settings
+    assert code_of(D.dfb_noalloc_set_wait_limit, 0.0) == D.DFB_ERR_INVALID_ARG
+    assert code_of(D.dfb_noalloc_set_wait_limit, -1.0) == D.DFB_ERR_INVALID_ARG
+    assert code_of(D.dfb_noalloc_set_wait_limit, 4000.0) == D.DFB_ERR_INVALID_ARG
+    assert code_of(D.dfb_noalloc_inject_stall, -2) == D.DFB_ERR_INVALID_ARG
+    D.dfb_noalloc_set_wait_limit(2.0)
+    D.dfb_noalloc_inject_stall(-1)
 
 
 def test_null_handle_and_pointers():

@@ -127,6 +127,38 @@ def test_refuses_host_tiles_and_a_capturing_stream():
     assert np.max(np.abs(out.cpu().numpy().astype(np.float64) - ref)) <= TOL
 
 
+def test_a_wait_that_runs_out_is_reported_and_the_next_call_is_correct():
+    """Failure detection without a GPU fault: the next call leaves work item 0
+    unfilled (injected on the host), so its consumers' bounded wait (50 ms
+    here) runs out and the kernel gives up; the call returns DFB_ERR_TIMEOUT.
+    The following call, on the same context and scratch, matches the
+    oracle."""
+    import torch
+    sc = scenes.random_scene(128, 96, 32, np.full(12, 3), seed=25, alpha_max=0.6)
+    dev_r, dev_d = to_dev(sc.rgba), to_dev(sc.depth)
+    out = torch.empty((sc.H, sc.W, 4), dtype=torch.float32, device="cuda")
+    tb = sc.T * sc.T
+
+    def call():
+        D.dfb_composite_noalloc(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH, D.DFB_F32, sc.tile_ids,
+                                sc.keys, D.pool_pointers(dev_r, sc.n, tb * 16),
+                                D.pool_pointers(dev_d, sc.n, tb * 4), None, None, out, None)
+
+    D.dfb_noalloc_set_wait_limit(0.05)
+    try:
+        D.dfb_noalloc_inject_stall(0)
+        with pytest.raises(D.DfbError) as e:
+            call()
+        assert e.value.code == D.DFB_ERR_TIMEOUT
+        call()                                   # the injected stall was used up
+        ref = o.composite_frame(sc.W, sc.H, sc.T, D.DFB_BLEND_DEPTH, sc.tile_ids, sc.keys,
+                                sc.rgba.astype(np.float64), sc.depth)
+        assert np.max(np.abs(out.cpu().numpy().astype(np.float64) - ref)) <= TOL
+    finally:
+        D.dfb_noalloc_inject_stall(-1)
+        D.dfb_noalloc_set_wait_limit(2.0)
+
+
 def test_rejects_requests_beyond_the_fixed_scratch():
     import torch
     out = torch.empty((64, 64, 4), dtype=torch.float32, device="cuda")
