@@ -102,6 +102,7 @@ class ServerStats:
     fragment_pixels: int = 0
     wall_s: float = 0.0
     latencies_ms: list = field(default_factory=list)
+    latencies_by_kind: dict = field(default_factory=dict)  # kind -> latencies (ms)
     batch_sizes: list = field(default_factory=list)
     peak_active: int = 0
     peak_footprint: int = 0
@@ -117,6 +118,10 @@ class ServerStats:
                 "latency_ms_p50": float(np.percentile(lat, 50)),
                 "latency_ms_p99": float(np.percentile(lat, 99)),
                 "latency_ms_max": float(lat.max()),
+                "latency_ms_by_kind": {
+                    k: {"jobs": len(v), "p50": float(np.percentile(v, 50)),
+                        "p99": float(np.percentile(v, 99))}
+                    for k, v in sorted(self.latencies_by_kind.items()) if v},
                 "mean_batch": float(np.mean(self.batch_sizes)) if self.batch_sizes else 0.0,
                 "max_batch": int(max(self.batch_sizes)) if self.batch_sizes else 0,
                 "peak_active_jobs": self.peak_active,
@@ -218,6 +223,7 @@ class Server:
                         ev.synchronize()
                     job.finished = time.perf_counter() - t0
                     st.latencies_ms.append(1e3 * (job.finished - job.arrival))
+                    st.latencies_by_kind.setdefault(job.kind, []).append(st.latencies_ms[-1])
                     st.jobs += 1
                     if self.keep_results:
                         job.result = host.numpy().view(np.uint32).copy()

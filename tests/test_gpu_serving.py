@@ -52,6 +52,9 @@ def test_mix_equals_alone_under_continuous_batching():
     summ = st.summary()
     assert summ["jobs"] == len(jobs)
     assert summ["max_batch"] > 1                     # jobs shared launches
+    by_kind = summ["latency_ms_by_kind"]
+    assert sorted(by_kind) == ["accumulate", "blend"]
+    assert sum(v["jobs"] for v in by_kind.values()) == len(jobs)
     assert any(j.admitted > j.arrival for j in jobs)  # some had to wait for room
     for j in jobs:
         mixed = j.result

@@ -52,3 +52,15 @@ def test_admission_order_budget_and_slots():
     # ... but not while anything is active
     q = [("big", 50)]
     assert S.admit(q, 1, 0, 10, 8, fp) == [] and q == [("big", 50)]
+
+
+def test_summary_splits_latency_by_job_kind():
+    st = S.ServerStats()
+    for kind, v in [("blend", 1.0), ("blend", 3.0), ("accumulate", 40.0), ("blend", 2.0)]:
+        st.latencies_ms.append(v)
+        st.latencies_by_kind.setdefault(kind, []).append(v)
+    summ = st.summary()
+    assert summ["latency_ms_p50"] == 2.5
+    assert summ["latency_ms_by_kind"]["blend"] == {"jobs": 3, "p50": 2.0,
+                                                   "p99": float(np.percentile([1, 3, 2], 99))}
+    assert summ["latency_ms_by_kind"]["accumulate"] == {"jobs": 1, "p50": 40.0, "p99": 40.0}
