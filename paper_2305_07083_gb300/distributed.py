@@ -24,9 +24,15 @@ Order of equal keys: the owner submits the fragments it receives in
 breaks ties is the fragment's position in the ranks' lists taken in rank
 order.
 
-The exchange and the gather use torch.distributed: on an NCCL group the
-device buffers travel as they are; on a gloo group (CPU ranks, tests) they
-are staged through host memory.
+The exchange runs in two steps, as the paper's producers send their tiles
+asynchronously: the counts and the 16-byte headers (tile id, key, scale) go
+first, over a host (gloo) group, so the owner knows what it will receive;
+the RGBA and depth tiles follow as asynchronous all-to-alls while the
+caller goes on producing (DistributedFrameBuffer.post); the owner's
+composite is ordered after their arrival on the GPU stream
+(composite_received).  The exchange and the gather use torch.distributed:
+on an NCCL group the device buffers travel as they are; on a gloo group
+(CPU ranks, tests) they are staged through host memory.
 """
 
 from __future__ import annotations
@@ -37,7 +43,7 @@ import numpy as np
 
 from . import dfb as D
 
-HEADER_BYTES = 16  # tile id (int32), order key (f32), FP8 scale (f32), spare
+HEADER_BYTES = 16  # per fragment: tile id (int32), order key (f32), FP8 scale (f32), spare
 
 
 class TileOwnership:
@@ -100,52 +106,73 @@ def route(tile_ids, own: TileOwnership):
     return order, counts
 
 
-def pack_records(tile_ids, keys, rgba, depth, scales, order):
-    """Fixed-size byte records of the fragments in `order`: header (tile id,
-    key, scale), then the T*T RGBA values and T*T depths.  `rgba` and
-    `depth` are tensors of shape (n, ...) on any device; the result is on
-    the same device."""
-    import torch
+def pack_headers(tile_ids, keys, scales, order):
+    """Header records of the fragments in `order`: (tile id, order key bits,
+    scale bits, 0) as an (n, 4) int32 array."""
+    order = np.asarray(order, dtype=np.int64)
     n = len(order)
-    dev = rgba.device
-    rb = int(np.prod(rgba.shape[1:])) * rgba.element_size()
-    db = int(np.prod(depth.shape[1:])) * depth.element_size()
-    rec = HEADER_BYTES + rb + db
-    out = torch.empty((n, rec), dtype=torch.uint8, device=dev)
-    if n == 0:
-        return out, rec
-    idx = torch.as_tensor(np.ascontiguousarray(order), dtype=torch.long, device=dev)
-    hdr = np.zeros((n, 4), np.float32)
-    hdr.view(np.int32)[:, 0] = np.asarray(tile_ids, np.int32)[order]
-    hdr[:, 1] = np.asarray(keys, np.float32)[order]
-    hdr[:, 2] = 1.0 if scales is None else np.asarray(scales, np.float32)[order]
-    out[:, :HEADER_BYTES] = torch.from_numpy(hdr.view(np.uint8).reshape(n, HEADER_BYTES)).to(dev)
-    out[:, HEADER_BYTES:HEADER_BYTES + rb] = rgba.index_select(0, idx).reshape(n, -1).view(torch.uint8)
-    out[:, HEADER_BYTES + rb:] = depth.index_select(0, idx).reshape(n, -1).view(torch.uint8)
-    return out, rec
+    hdr = np.zeros((n, 4), np.int32)
+    hdr[:, 0] = np.asarray(tile_ids, np.int32)[order]
+    hdr[:, 1] = np.asarray(keys, np.float32)[order].view(np.int32)
+    sc = np.ones(n, np.float32) if scales is None else np.asarray(scales, np.float32)[order]
+    hdr[:, 2] = sc.view(np.int32)
+    return hdr
 
 
-def unpack_records(buf, rgba_shape, rgba_dtype, depth_shape):
-    """Inverse of pack_records: (tile ids, keys, scales) as numpy arrays and
-    (rgba, depth) tensors on the buffer's device."""
-    import torch
-    n = buf.shape[0]
-    hdr = buf[:, :HEADER_BYTES].cpu().numpy().reshape(n, 4 * 4).view(np.float32).reshape(n, 4)
-    tile_ids = hdr.view(np.int32)[:, 0].copy()
-    keys = hdr[:, 1].copy()
-    scales = hdr[:, 2].copy()
-    esz = torch.empty((), dtype=rgba_dtype).element_size()
-    rb = int(np.prod(rgba_shape)) * esz
-    rgba = buf[:, HEADER_BYTES:HEADER_BYTES + rb].contiguous().view(rgba_dtype).reshape(n, *rgba_shape)
-    depth = buf[:, HEADER_BYTES + rb:].contiguous().view(torch.float32).reshape(n, *depth_shape)
-    return tile_ids, keys, scales, rgba, depth
+def unpack_headers(hdr):
+    """Inverse of pack_headers: (tile ids, keys, scales) as numpy arrays."""
+    hdr = np.ascontiguousarray(hdr, dtype=np.int32).reshape(-1, 4)
+    return (hdr[:, 0].copy(), hdr[:, 1].copy().view(np.float32),
+            hdr[:, 2].copy().view(np.float32))
 
 
-def exchange(tile_ids, keys, rgba, depth, own: TileOwnership, scales=None, group=None):
-    """One all-to-all of fragment tiles: every rank sends each fragment to its
-    tile's owner.  Returns the fragments this rank owns, in (source rank,
-    source order) order, with their global tile ids: (tile ids, keys,
-    scales, rgba, depth), rgba/depth on the device of the inputs."""
+class PendingExchange:
+    """The fragments this rank owns after an exchange was started: their
+    tile ids, keys and scales (host arrays, final at once) and their RGBA
+    and depth tiles (device tensors, valid once wait() has returned; on an
+    NCCL group wait() only orders the caller's current stream after the
+    transfer, so the host does not block)."""
+
+    def __init__(self, tile_ids, keys, scales, rgba, depth, works=(), device=None):
+        self.tile_ids, self.keys, self.scales = tile_ids, keys, scales
+        self.rgba, self.depth = rgba, depth
+        self._works = list(works)
+        self._device = device
+
+    def wait(self, stream=None):
+        """Wait for the tiles.  Work that reads them afterwards on the
+        caller's current stream, or on `stream` (a torch stream or a raw
+        cudaStream_t), is ordered after the transfer."""
+        import torch
+        moved = bool(self._works)
+        for w in self._works:
+            w.wait()
+        self._works = []
+        if self._device is not None and self.rgba.device != self._device:
+            # a gloo group received into host memory
+            self.rgba = self.rgba.to(self._device)
+            self.depth = self.depth.to(self._device)
+        if moved and stream is not None and self.rgba.is_cuda:
+            s = stream if isinstance(stream, torch.cuda.Stream) else torch.cuda.ExternalStream(stream)
+            cur = torch.cuda.current_stream(self.rgba.device)
+            if s.cuda_stream != cur.cuda_stream:
+                s.wait_stream(cur)
+        return self
+
+
+def exchange_async(tile_ids, keys, rgba, depth, own: TileOwnership, scales=None, group=None,
+                   meta_group=None):
+    """Start the all-to-all of fragment tiles: every rank sends each fragment
+    to its tile's owner.  The 16-byte headers (tile id, key, scale) and the
+    counts travel first, over `meta_group` (default: `group`; a gloo group
+    keeps this step off the GPU streams), and are known when the call
+    returns; the RGBA and depth tiles follow as two asynchronous
+    all-to-alls on `group`, so the caller can go on producing the next
+    frame.  The owned fragments come in (source rank, source order) order.
+    With more than one rank the tiles are copied into send buffers before
+    the call returns (in stream order on an NCCL group), so the sources may
+    be reused; with one rank nothing moves and the PendingExchange holds
+    the sources themselves.  Returns a PendingExchange."""
     import torch
     import torch.distributed as dist
     rank, world = _rank_world(group)
@@ -153,21 +180,46 @@ def exchange(tile_ids, keys, rgba, depth, own: TileOwnership, scales=None, group
         raise ValueError("ownership is for %d ranks, the group has %d" % (own.world, world))
     if world == 1:  # every tile is this rank's: nothing moves
         sc = np.ones(len(tile_ids), np.float32) if scales is None else np.asarray(scales, np.float32)
-        return (np.asarray(tile_ids, np.int32), np.asarray(keys, np.float32), sc, rgba, depth)
+        return PendingExchange(np.asarray(tile_ids, np.int32), np.asarray(keys, np.float32), sc,
+                               rgba, depth)
+    meta = group if meta_group is None else meta_group
     order, counts = route(tile_ids, own)
-    packed, rec = pack_records(tile_ids, keys, rgba, depth, scales, order)
+    # headers and counts
+    mdev = torch.device("cpu") if _staged(meta) else rgba.device
+    send_counts = torch.as_tensor(counts, dtype=torch.int64, device=mdev)
+    recv_counts = torch.empty(world, dtype=torch.int64, device=mdev)
+    dist.all_to_all_single(recv_counts, send_counts, group=meta)
+    rc = [int(v) for v in recv_counts.cpu().numpy()]
+    sc_ = [int(v) for v in counts]
+    hdr_out = torch.from_numpy(pack_headers(tile_ids, keys, scales, order)).to(mdev)
+    hdr_in = torch.empty((sum(rc), 4), dtype=torch.int32, device=mdev)
+    dist.all_to_all_single(hdr_in, hdr_out, rc, sc_, group=meta)
+    tid, key, scl = unpack_headers(hdr_in.cpu().numpy())
+    # tile payloads, in destination order, as byte rows
+    n = len(order)
+    idx = torch.as_tensor(np.ascontiguousarray(order), dtype=torch.long, device=rgba.device)
+    r_out = rgba.index_select(0, idx).reshape(n, int(np.prod(rgba.shape[1:]))).view(torch.uint8)
+    d_out = depth.index_select(0, idx).reshape(n, int(np.prod(depth.shape[1:]))).view(torch.uint8)
     staged = _staged(group)
-    dev = torch.device("cpu") if staged else packed.device
-    send_counts = torch.as_tensor(counts, dtype=torch.int64, device=dev)
-    recv_counts = torch.empty(world, dtype=torch.int64, device=dev)
-    dist.all_to_all_single(recv_counts, send_counts, group=group)
-    rc = recv_counts.cpu().numpy()
-    src = packed.cpu() if staged else packed
-    buf = torch.empty((int(rc.sum()), rec), dtype=torch.uint8, device=src.device)
-    dist.all_to_all_single(buf, src, [int(v) for v in rc], [int(v) for v in counts],
-                           group=group)
-    buf = buf.to(rgba.device)
-    return unpack_records(buf, tuple(rgba.shape[1:]), rgba.dtype, tuple(depth.shape[1:]))
+    pdev = torch.device("cpu") if staged else rgba.device
+    if staged:
+        r_out, d_out = r_out.cpu(), d_out.cpu()
+    r_in = torch.empty((sum(rc), r_out.shape[1]), dtype=torch.uint8, device=pdev)
+    d_in = torch.empty((sum(rc), d_out.shape[1]), dtype=torch.uint8, device=pdev)
+    works = [dist.all_to_all_single(r_in, r_out, rc, sc_, group=group, async_op=True),
+             dist.all_to_all_single(d_in, d_out, rc, sc_, group=group, async_op=True)]
+    m = sum(rc)
+    r_in = r_in.view(rgba.dtype).reshape(m, *rgba.shape[1:])
+    d_in = d_in.view(torch.float32).reshape(m, *depth.shape[1:])
+    return PendingExchange(tid, key, scl, r_in, d_in, works, rgba.device)
+
+
+def exchange(tile_ids, keys, rgba, depth, own: TileOwnership, scales=None, group=None,
+             meta_group=None):
+    """exchange_async, waited for: (tile ids, keys, scales, rgba, depth) of
+    the fragments this rank owns, rgba/depth on the device of the inputs."""
+    p = exchange_async(tile_ids, keys, rgba, depth, own, scales, group, meta_group).wait()
+    return p.tile_ids, p.keys, p.scales, p.rgba, p.depth
 
 
 def gather_tiles(local, own: TileOwnership, group=None, dst=0):
@@ -229,17 +281,42 @@ class DistributedFrameBuffer:
         self.h = D.dfb_create_ex(lw, lh, T, mode, dtype, flags, kahan_after)
         D.dfb_set_background(self.h, *background)
         self.keep = []
+        # headers and counts go over a host (gloo) group when the tiles travel
+        # over NCCL, so that starting an exchange never waits on a GPU stream
+        self.meta_group = group
+        if self.world > 1:
+            import torch.distributed as dist
+            if not _staged(group):
+                self.meta_group = dist.new_group(
+                    ranks=dist.get_process_group_ranks(group) if group is not None else None,
+                    backend="gloo")
 
     def close(self):
         if self.h is not None:
             D.dfb_destroy(self.h)
             self.h = None
 
+    def post(self, tile_ids, keys, rgba, depth, scales=None):
+        """Start sending this rank's fragment tiles of a frame (global tile
+        ids; rgba and depth device tensors of shape (n, T*T, 4) and (n, T*T))
+        to their owners; returns the PendingExchange of the fragments this
+        rank owns.  The caller may produce the next frame's tiles (into other
+        buffers) before passing it to composite_received."""
+        return exchange_async(tile_ids, keys, rgba, depth, self.own, scales, self.group,
+                              self.meta_group)
+
     def composite(self, tile_ids, keys, rgba, depth, scales=None, accumulate=False, stream=None):
-        """One frame: this rank's fragment tiles (global tile ids; rgba and
-        depth device tensors of shape (n, T*T, 4) and (n, T*T)) go to their
-        owners; this rank composites the fragments it owns."""
-        tid, key, scl, r, d = exchange(tile_ids, keys, rgba, depth, self.own, scales, self.group)
+        """One frame: post() and composite_received() in one call."""
+        return self.composite_received(self.post(tile_ids, keys, rgba, depth, scales),
+                                       accumulate, stream)
+
+    def composite_received(self, pending, accumulate=False, stream=None):
+        """Composite the fragments this rank owns for one frame, once their
+        transfer is done (on an NCCL group the composite is ordered after it
+        on the stream; the host does not wait)."""
+        pending.wait(stream)
+        tid, key, scl, r, d = (pending.tile_ids, pending.keys, pending.scales, pending.rgba,
+                               pending.depth)
         if self.keep and (self.keep[0] is not r or self.keep[1] is not d):
             D.dfb_sync(self.h)  # the previous frame's tiles are released below
         self.keep = [r, d]  # the library borrows the device tiles until the frame is done

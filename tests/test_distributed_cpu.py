@@ -1,7 +1,8 @@
 """Tile ownership across ranks (Sec. 3, 3.2, 4.1.1) on CPU ranks: the
-partition of the tiles, the routing of fragment tiles to their owners in one
-all-to-all exchange (gloo, world size 2 and 3), and the gather of the
-owners' tiles into the display rank's frame.
+partition of the tiles, the routing of fragment tiles to their owners
+(headers first, then the tiles as asynchronous all-to-alls; gloo, world
+size 2 and 3), and the gather of the owners' tiles into the display rank's
+frame.
 
 In these CPU tests the owners composite their tiles with the oracle (test
 code); the library's own compositing on each owner is covered by
@@ -68,24 +69,19 @@ def test_route_is_stable_by_destination():
     assert counts.tolist() == [int((dest == r).sum()) for r in range(3)]
 
 
-def test_pack_unpack_round_trip_all_dtypes():
-    for dt in (0, 1, 2, 3):
-        sc = scenes.random_scene(32, 32, 16, np.array([2, 0, 3, 1]), seed=4)
-        stored, scales = scenes.store_rgba(sc.rgba, dt)
-        st = np.ascontiguousarray(stored)
-        rgba = torch.from_numpy(st.view(np.int16) if st.dtype == np.uint16 else st)
-        depth = torch.from_numpy(sc.depth)
-        order = np.arange(sc.n)[::-1].copy()
-        buf, rec = DD.pack_records(sc.tile_ids, sc.keys, rgba, depth, scales, order)
-        assert rec == DD.HEADER_BYTES + rgba[0].numel() * rgba.element_size() + 16 * 16 * 4
-        tid, key, scl, r2, d2 = DD.unpack_records(buf, tuple(rgba.shape[1:]), rgba.dtype,
-                                                  tuple(depth.shape[1:]))
+def test_header_round_trip():
+    sc = scenes.random_scene(32, 32, 16, np.array([2, 0, 3, 1]), seed=4, special_depths=True)
+    scales = np.linspace(0.5, 2.0, sc.n).astype(np.float32)
+    order = np.arange(sc.n)[::-1].copy()
+    for sc_in in (None, scales):
+        hdr = DD.pack_headers(sc.tile_ids, sc.keys, sc_in, order)
+        assert hdr.shape == (sc.n, 4) and hdr.dtype == np.int32
+        assert hdr.nbytes == sc.n * DD.HEADER_BYTES
+        tid, key, scl = DD.unpack_headers(hdr)
         np.testing.assert_array_equal(tid, sc.tile_ids[order])
-        np.testing.assert_array_equal(key, sc.keys[order])
-        if scales is not None:
-            np.testing.assert_array_equal(scl, np.asarray(scales, np.float32)[order])
-        assert torch.equal(r2, rgba[order])
-        assert torch.equal(d2, depth[order])
+        np.testing.assert_array_equal(key.view(np.int32), sc.keys[order].view(np.int32))
+        want = np.ones(sc.n, np.float32) if sc_in is None else scales[order]
+        np.testing.assert_array_equal(scl, want)
 
 
 def _owner_composite(own, rank, tid, key, rgba, depth, mode):
@@ -108,8 +104,17 @@ def _rank_main(rank, world, port, scheme, mode, q):
     try:
         own = DD.TileOwnership(W, H, T, world, scheme)
         sc = rank_fragments(rank, own.n_tiles, 7)
-        tid, key, scl, r, d = DD.exchange(sc.tile_ids, sc.keys, torch.from_numpy(sc.rgba),
-                                          torch.from_numpy(sc.depth), own)
+        src_r, src_d = torch.from_numpy(sc.rgba.copy()), torch.from_numpy(sc.depth.copy())
+        # the headers over a group of their own, as a DistributedFrameBuffer
+        # on an NCCL group does
+        meta = dist.new_group(backend="gloo")
+        pend = DD.exchange_async(sc.tile_ids, sc.keys, src_r, src_d, own, meta_group=meta)
+        # the headers are known at once; the sources may be reused at once
+        # (the next frame produced into them) while the tiles travel
+        src_r.fill_(-7.0)
+        src_d.fill_(-7.0)
+        pend.wait()
+        tid, key, scl, r, d = pend.tile_ids, pend.keys, pend.scales, pend.rgba, pend.depth
         # every received fragment is owned here, and nothing owned is missing
         assert (own.owner[tid] == rank).all()
         allfr = [rank_fragments(s, own.n_tiles, 7) for s in range(world)]

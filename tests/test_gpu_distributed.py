@@ -5,7 +5,8 @@ its GPU through the C ABI, and the display rank gathers the frame.
 
 One GPU serves here: the single-rank case, and two ranks (two processes on
 the same GPU, a gloo group whose exchange is staged through host memory;
-their kernels never wait on one another).  The gathered colour, RGBA8 and
+their kernels never wait on one another).  The second frame goes through
+post() / composite_received() with the next frame produced in between.  The gathered colour, RGBA8 and
 accumulation are compared with the oracle's composite of the union of the
 ranks' fragments in rank order."""
 
@@ -50,13 +51,24 @@ def run_rank(rank, world, mode, dtype, scheme):
     torch.cuda.set_device(0)
     fb = DD.DistributedFrameBuffer(W, H, T, mode, dtype, scheme=scheme)
     frames = rank_frames(rank, fb.own.n_tiles)
-    for f, sc in enumerate(frames):
+
+    def produce(sc):
         stored, scales = scenes.store_rgba(sc.rgba, dtype)
         st = np.ascontiguousarray(stored)
         r = torch.from_numpy(st.view(np.int16) if st.dtype == np.uint16 else st).cuda()
-        d = torch.from_numpy(sc.depth).cuda()
-        fb.composite(sc.tile_ids, sc.keys, r, d, scales, accumulate=f > 0)
-        D.dfb_sync(fb.h)
+        return r, torch.from_numpy(sc.depth).cuda(), scales
+
+    # frame 0 in one call; frame 1 posted, then the next frame's tiles are
+    # produced into other buffers while the tiles travel, then composited
+    r, d, scales = produce(frames[0])
+    fb.composite(frames[0].tile_ids, frames[0].keys, r, d, scales, accumulate=False)
+    D.dfb_sync(fb.h)
+    r, d, scales = produce(frames[1])
+    pend = fb.post(frames[1].tile_ids, frames[1].keys, r, d, scales)
+    nxt = produce(frames[0])
+    fb.composite_received(pend, accumulate=True)
+    D.dfb_sync(fb.h)
+    del nxt
     res = (fb.gather("color"), fb.gather("rgba8"), fb.gather("accum"))
     fb.close()
     return res
