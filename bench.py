@@ -900,19 +900,25 @@ def main():
         out8 = torch.empty((sc.H, sc.W), dtype=torch.int32).pin_memory()
         e_steps = max(1, min(args.steps, 4))
         h2d = N_FRAMES * (host_frames[0].numel() * 4 + host_depth.numel() * 4)
-        # The two host-pointer modes alternate over three rounds each, so
-        # that a slow spell of the shared host link does not land on one mode
-        # only; each mode reports its median round (the step time of one
-        # round was seen to double on a box, in either mode).
+        # The two host-pointer modes alternate over five rounds each (one
+        # handle per mode, kept across its rounds), so that a slow spell of
+        # the shared host link does not land on one mode only; each mode
+        # reports its median round (the step time of one round was seen to
+        # double on a box, in either mode).
+        e_rounds = 5
         e2e_ms = {"borrowed": [], "host": []}
-        for where in ("host", "borrowed", "borrowed", "host", "host", "borrowed"):
-            hrun = Runner(sc, host_frames, host_depth, D.DFB_F32, where=where)
+        hruns = {w: Runner(sc, host_frames, host_depth, D.DFB_F32, where=w)
+                 for w in ("host", "borrowed")}
+        for r in range(e_rounds):
+            for where in (("host", "borrowed") if r % 2 == 0 else ("borrowed", "host")):
+                hrun = hruns[where]
 
-            def read_back():
-                D.dfb_read_rgba8(hrun.h, out8)
-            ems, _, _, _ = timed(hrun, e_steps, 1, stream, dist, None, read_back,
-                                 kernel_pass=False)
-            e2e_ms[where].append(max_over_ranks(ems, dist, dev) / e_steps)   # slowest rank
+                def read_back():
+                    D.dfb_read_rgba8(hrun.h, out8)
+                ems, _, _, _ = timed(hrun, e_steps, 1, stream, dist, None, read_back,
+                                     kernel_pass=False)
+                e2e_ms[where].append(max_over_ranks(ems, dist, dev) / e_steps)   # slowest rank
+        for hrun in hruns.values():
             hrun.close()
         # every rank copies and composites its own replica: whole-job units
         e2e = {w: (whole_job_value(fpx_frame * N_FRAMES, world, float(np.median(v))),
@@ -920,7 +926,7 @@ def main():
         out["e2e"] = {"value": e2e["borrowed"][0], "unit": UNIT,
                       "h2d_bytes_per_step": h2d * world,
                       "d2h_bytes_per_step": sc.W * sc.H * 4 * world,
-                      "steps": e_steps, "rounds": 3, "ms_per_step": e2e["borrowed"][1],
+                      "steps": e_steps, "rounds": e_rounds, "ms_per_step": e2e["borrowed"][1],
                       "ms_per_step_rounds": e2e["borrowed"][2],
                       "path": "dfb_submit_tiles(pinned host pointers, DFB_PTR_HOST_BORROWED: "
                               "copies queued on the handle's copy stream, sources lent until "
@@ -952,15 +958,15 @@ def main():
             e_steps = max(1, min(args.steps, 4))
             h2d16 = N_FRAMES * (host16[0].numel() * 2 + host_depth16.numel() * 4)
             rounds = []
-            for _ in range(3):
-                hrun = Runner(sc, host16, host_depth16, D.DFB_F16, where="borrowed")
+            hrun = Runner(sc, host16, host_depth16, D.DFB_F16, where="borrowed")
 
-                def read_back16():
-                    D.dfb_read_rgba8(hrun.h, out8)
+            def read_back16():
+                D.dfb_read_rgba8(hrun.h, out8)
+            for _ in range(5):
                 ems, _, _, _ = timed(hrun, e_steps, 1, stream, dist, None, read_back16,
                                      kernel_pass=False)
                 rounds.append(max_over_ranks(ems, dist, dev) / e_steps)
-                hrun.close()
+            hrun.close()
             med = float(np.median(rounds))
             e2e16 = {"value": whole_job_value(fpx_frame * N_FRAMES, world, med), "unit": UNIT,
                      "h2d_bytes_per_step": h2d16 * world,

@@ -17,9 +17,9 @@
 // is to keep enough bytes in flight:
 //   * CTA = G consumer groups of 8 warps (one pixel per thread, 256 pixels =
 //     one work item; the groups take alternate items) + 1 producer warp, PER
-//     CTAs per SM (FP32: G = 2, PER = 2; narrower formats: G = 1, PER = 3;
-//     the kernel needs 56 registers).  CTAs are persistent and walk the work
-//     items of all frames of the launch with a static stride.
+//     CTAs per SM (by default G = 1, PER = 2).  CTAs are persistent and walk
+//     the work items of all frames of the launch with a static stride, which
+//     keeps the chunks of a tile on neighbouring CTAs that run in step.
 //   * The producer warp fetches each item's tile block (fragment count,
 //     list offset and sorted records, written by the bucketing) with one bulk
 //     copy kMetaQ items ahead, so locating an item's fragments needs no
@@ -36,10 +36,14 @@
 //     fragment as a short one.  The rare 32-pixel units whose depths turn
 //     out to be out of list order are redone exactly by k_composite_redo.
 //   * The accumulation state (sum, M2, Kahan compensation) is stored
-//     tile-major, so an item's state is one contiguous run per buffer that
-//     the producer streams into the item's last fill; consumers read every
-//     input from shared memory, sort and blend, take the state into
-//     registers and release the ring space before the epilogue.
+//     tile-major, so an item's state is one contiguous run per buffer.  In
+//     frames with few fragments per tile the producer streams it into the
+//     item's last fill; in the others the consumers load it into registers
+//     before they wait for the fragments, so that the ring holds fragments
+//     only (the state's bytes would occupy it for the item's whole stay and
+//     leave room for fewer items in flight).  Consumers read the fragments
+//     from shared memory, sort and blend, and release the ring space before
+//     the epilogue.
 //   * The epilogue writes one variance partial per warp with plain stores;
 //     a small second kernel sums each tile's partials in a fixed order.
 // Every wait is bounded in time; on expiry the kernel sets an error bit,
@@ -86,15 +90,15 @@ constexpr int kMetaQ = 8;                // tile blocks fetched ahead
 constexpr uint32_t kWindowBytes = kSortWindow * kP * 8;
 
 // Descriptor of one fill of the ring: up to kN fragments of one work item
-// (all of them for an item of at most kN fragments, else kFill), plus the
-// item's state rows in its last fill.
+// (all of them for an item of at most kN fragments, else kFill), and the
+// item's state rows in its last fill when the frame streams them.
 struct ItemMeta {
   int n;               // fragments in this fill
   int total;           // fragments of the item
   int first;           // list index of the fill's first fragment
   int pad;
   uint32_t start;      // byte offset of the fill's data in the ring
-  uint32_t stateOff;   // offset of the state rows from `start` (last fill)
+  uint32_t bytes;      // bytes of the fill's fragments from `start` (state rows follow)
   unsigned long long end;  // producer's head position after this fill
   const void* rgba[kN];
   float scale[kN];
@@ -264,7 +268,7 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
     const int n = blk->n;
     const int4 loc = qLoc[q];
     const FrameArgs* A = frames + loc.x;
-    const int P = A->P, mode = A->mode, T = A->T;
+    const int P = A->P, mode = A->mode;
     const size_t p0 = (size_t)loc.z * P;  // the item's first pixel in its tile
     // An item of more than kN fragments is streamed in fills of kFill; its
     // records past the tile block come from the sorted list.
@@ -272,8 +276,9 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
     const int fills = n > kN ? (n + kFill - 1) / kFill : 1;
     const uint32_t dBytes = mode == DFB_BLEND_DEPTH || mode == DFB_ZCOMPOSITE ? (uint32_t)P * 4u : 0u;
     const uint32_t cBytes = mode != DFB_ZCOMPOSITE ? (uint32_t)P * px : 0u;
-    // accumulation state of the item's pixels: one contiguous run per buffer
-    const bool loadState = (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1;
+    // accumulation state of the item's pixels, one contiguous run per
+    // buffer, when the frame streams it with the fragments
+    const bool loadState = (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1 && A->stateInRing;
     const int nState = loadState ? (A->kahan && !A->kahanFirst ? 3 : 2) : 0;
     const int g = G == 1 ? 0 : k % G;
     for (int f = 0; f < fills; ++f) {
@@ -303,7 +308,7 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
       if (tailFill == curFill) tail = head;  // nothing outstanding: the padding is free too
       if (!DFB_CHECK((uint64_t)(head % ringBytes) + need <= ringBytes &&
                          head + need - tail <= ringBytes && nf <= kN &&
-                         (loc.z + 1) * P <= T * T,
+                         (loc.z + 1) * P <= A->T * A->T,
                      ctl.err)) {
         ok = false;
         break;
@@ -328,7 +333,7 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
         meta->total = n;
         meta->first = i0;
         meta->start = start;
-        meta->stateOff = fragBytes;
+        meta->bytes = fragBytes;
         meta->end = head;
       }
       if (lane == curFill % kSlots) {
@@ -355,7 +360,7 @@ __device__ void producer(const FrameArgs* __restrict__ frames, const int* __rest
           // state runs: [sum | M2 | comp], P pixels of 16 bytes each
           const float4* src = lane == 0 ? A->accum : (lane == 1 ? A->m2 : A->comp);
           bulk_g2s(base + fragBytes + lane * (uint32_t)P * 16u,
-                   src + (size_t)loc.y * T * T + p0, (uint32_t)P * 16u, &fullB[s]);
+                   src + (size_t)loc.y * A->T * A->T + p0, (uint32_t)P * 16u, &fullB[s]);
         }
       }
     }
@@ -660,8 +665,7 @@ __device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& 
 
 // A multi-fill item's fills, for one blend mode: the consumer group takes
 // them from its slots in order (jg counts its fills) and carries the
-// per-pixel blend across them; the item's state rows come with the last
-// fill.  BLEND_DEPTH blends speculatively in list order; `exact` turns false
+// per-pixel blend across them.  BLEND_DEPTH blends speculatively in list order; `exact` turns false
 // for a pixel whose finite depths are out of list order or that has a
 // non-zero empty fragment.  Returns false when a wait ran out.
 template <int DT, int MODE, int G>
@@ -693,7 +697,7 @@ __device__ __forceinline__ bool multi_fill(int total, const PixWork& w, int t, i
     const int nf = meta->n;
     const bool lastFill = f == fills - 1;
     const bool inRing = DFB_CHECK(
-        nf <= kN && (uint64_t)meta->start + meta->stateOff +
+        nf <= kN && (uint64_t)meta->start + meta->bytes +
                             (uint64_t)(lastFill ? stateRows : 0u) * P * 16u <=
                         ringBytes,
         ctl.err);
@@ -735,7 +739,7 @@ __device__ __forceinline__ bool multi_fill(int total, const PixWork& w, int t, i
       }
     }
     if (lastFill && stateRows && inRing) {
-      const float4* sState = reinterpret_cast<const float4*>(base + meta->stateOff);
+      const float4* sState = reinterpret_cast<const float4*>(base + meta->bytes);
       S0 = sState[t];
       M = sState[P + t];
       if (stateRows == 3u) CP = sState[2 * P + t];
@@ -776,6 +780,21 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
     if (item >= totalItems) break;
     const PixWork w = prepare<FR>(frames, itemBase, nFrames, item, t);
     const FrameArgs* A = w.A;
+    // The pixel's accumulation state comes with the item's last fill, or,
+    // in frames that do not stream it, is loaded here (tile-major: each warp
+    // reads 512 contiguous bytes per buffer) before the wait for the fill,
+    // so that it arrives while the fragments do.
+    const bool accRead = w.active && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1 &&
+                         DFB_CHECK(w.sidx < (size_t)A->nTiles * A->T * A->T, ctl.err);
+    const uint32_t stateRows =
+        accRead && A->stateInRing ? ((A->kahan && !A->kahanFirst) ? 3u : 2u) : 0u;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 S0 = zero4, M = zero4, CP = zero4;
+    if (accRead && !A->stateInRing) {
+      S0 = A->accum[w.sidx];
+      M = A->m2[w.sidx];
+      if (A->kahan && !A->kahanFirst) CP = A->comp[w.sidx];
+    }
     int s = group * S + jg % S;
     if (!wait_phase(&fullB[s], (uint32_t)(jg / S) & 1u, ctl, abort)) {
       if (lane == 0) give_up(ctl, abort);
@@ -784,26 +803,21 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
     const ItemMeta* meta = metas + s;
     const int total = meta->total;
     const int P = w.P;
-    const bool accRead = w.active && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1;
-    const uint32_t stateRows = accRead ? ((A->kahan && !A->kahanFirst) ? 3u : 2u) : 0u;
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 S0 = zero4, M = zero4, CP = zero4;
     float c0 = 0.f, c1 = 0.f, c2 = 0.f, al = 0.f;
     bool covered = true;
     if (total <= kN) {
       const unsigned char* base = ring + meta->start;
       // checked build: the item's fragments and state rows lie inside the ring
       const bool inRing = DFB_CHECK(
-          meta->n <= kN && (uint64_t)meta->start + meta->stateOff + (uint64_t)stateRows * P * 16u <=
+          meta->n <= kN && (uint64_t)meta->start + meta->bytes + (uint64_t)stateRows * P * 16u <=
                                ringBytes,
           ctl.err);
       if (w.active && inRing)
         covered = composite_staged<DT>(A->mode, total, P, base, meta, t, w.p, c0, c1, c2, al);
-      // the item's accumulation state: from the ring into registers, then the
-      // ring space goes back to the producer before the epilogue's math and
-      // stores
-      if (accRead && inRing) {
-        const float4* sState = reinterpret_cast<const float4*>(base + meta->stateOff);
+      // streamed state: from the ring into registers; then the ring space
+      // goes back to the producer before the epilogue's math and stores
+      if (stateRows && inRing) {
+        const float4* sState = reinterpret_cast<const float4*>(base + meta->bytes);
         S0 = sState[t];
         M = sState[P + t];
         if (stateRows == 3u) CP = sState[2 * P + t];
@@ -812,7 +826,7 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
       if (lane == 0) mbar_arrive(&emptyB[s]);  // ring space free for the producer
       ++jg;
     } else {
-      // multi-fill item: kFill fragments per fill, the state rows in the last
+      // multi-fill item: kFill fragments per fill
       bool ok, exact = true;
       switch (A->mode) {
         case DFB_BLEND_DEPTH:
@@ -832,8 +846,8 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
           break;
         default:
           ok = multi_fill<DT, DFB_AVERAGE, G>(total, w, t, lane, ctl, ring, metas, fullB, emptyB,
-                                              abort, ringBytes, group, jg, stateRows, c0, c1, c2,
-                                              al, covered, exact, S0, M, CP);
+                                              abort, ringBytes, group, jg, stateRows, c0, c1,
+                                              c2, al, covered, exact, S0, M, CP);
           break;
       }
       if (!ok) break;
@@ -1072,11 +1086,16 @@ cudaError_t launch_dt(const FrameArgs* frames, const int* itemBase, int nFrames,
 
 }  // namespace
 
-// Measured on the 2048x2048 brick workload: FP32 fills need the larger ring
-// of 2 CTAs per SM (one consumer group each measured faster than two); the
-// narrower formats fit a full fill into the ring of 3 CTAs per SM.
-TuneParams default_tune(int dtype) {
-  if (dtype == DFB_F32) return TuneParams{110, 2, 1};
+// Measured (composite launch, 16-frame accumulation): FP32 takes 2 CTAs per
+// SM with one consumer group each and the largest ring they share.  The
+// narrower formats fit their fills into the rings of 3 CTAs per SM, which is
+// faster unless the frames are fragment-heavy: FP16 at 5.5 fragments per
+// tile 0.1058 ms with 2 CTAs against 0.1095 ms with 3; at 4.4 fragments per
+// tile 0.1028 against 0.0945 ms; at one fragment per tile 3 CTAs are faster
+// too.  One CTA per SM is slower everywhere: its single producer warp sets
+// the pace.
+TuneParams default_tune(int dtype, double fragmentsPerTile) {
+  if (dtype == DFB_F32 || fragmentsPerTile >= 5.0) return TuneParams{110, 2, 1};
   return TuneParams{72, 3, 1};
 }
 

@@ -77,6 +77,8 @@ struct FrameArgs {
   int frameN;                  // frames in the accumulation including this one
   int kahan;                   // 1: compensated running sum this frame
   int kahanFirst;              // 1: first compensated frame (comp reads as 0)
+  int stateInRing;             // 1: the accumulation state comes with the item's last
+                               // fill; 0: the consumers load it themselves
   float invN, invNm1;          // 1/n and 1/(n-1) (0 when n == 1)
   float bgR, bgG, bgB, bgA;    // premultiplied background colour and coverage
   int pixelOp;                 // enum dfb_pixel_op applied before the RGBA8 pack
@@ -164,7 +166,14 @@ cudaError_t launch_composite(const FrameArgs* frames, const int* itemBase, int n
                              cudaEvent_t afterMain, cudaStream_t s);
 
 // Default launch shape for a dtype.
-TuneParams default_tune(int dtype);
+// Default launch shape for a launch whose frames have `fragmentsPerTile`
+// fragment tiles per image tile on average.
+TuneParams default_tune(int dtype, double fragmentsPerTile);
+
+// Mean fragments per tile from which the composite's consumers load a
+// frame's accumulation state themselves instead of receiving it through the
+// shared-memory ring with the fragments.
+constexpr double kStateLoadFragmentsPerTile = 2.0;
 
 // Tile-major state -> row-major image `out` (device):
 //   out = (a - b) * scale  when b is given, else a * scale.

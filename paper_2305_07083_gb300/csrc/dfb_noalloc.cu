@@ -279,6 +279,7 @@ int composite_noalloc(int width, int height, int tile_size, int mode, int dtype,
   // no accumulation: the per-tile variance scratch of the handle path is unused
   a.flags = (color_out ? DFB_FLAG_WRITE_COLOR : 0u) | (rgba8_out ? DFB_FLAG_PACK_RGBA8 : 0u);
   a.frameN = 1;
+  a.stateInRing = 0;  // no accumulation state
   a.invN = 1.0f;
   a.invNm1 = 0.0f;
   a.bgR = bg[0] * bg[3];
@@ -304,7 +305,8 @@ int composite_noalloc(int width, int height, int tile_size, int mode, int dtype,
   if (e != cudaSuccess) return DFB_ERR_CUDA;
   const dfb::LaunchCtl ctl{g_waitNs.load(), g_stallItem.exchange(-1), &dHdr->err, redo};
   e = dfb::launch_composite(&dHdr->fa, dHdr->itemBase, 1, hdr.itemBase[1], nTiles, false, dtype,
-                           dfb::default_tune(dtype), ctl, lng, &hdr.fa, hdr.itemBase, nullptr, s);
+                           dfb::default_tune(dtype, (double)n / (double)nTiles), ctl, lng,
+                           &hdr.fa, hdr.itemBase, nullptr, s);
   if (e != cudaSuccess) return DFB_ERR_CUDA;
   // The launch's error word: a wait that ran out (the frame is then
   // incomplete) or, in the checked build, a failed device-side check.  The

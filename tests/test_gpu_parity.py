@@ -108,6 +108,29 @@ def test_long_tiles_of_many_items_with_accumulation(mode):
     np.testing.assert_allclose(tv, o.tile_variance(o.variance(imgs), 64), rtol=1e-4, atol=1e-9)
 
 
+@pytest.mark.parametrize("mode", [D.DFB_BLEND_DEPTH, D.DFB_ZCOMPOSITE])
+def test_long_tile_in_a_sparse_frame_with_accumulation(mode):
+    """A frame of few fragments per tile (below 2) streams its accumulation
+    state through the composite's ring, with the last fill of each item; one
+    long tile there spans several fills."""
+    counts = np.zeros(32, int)
+    counts[[0, 5, 9, 30]] = [1, 2, 1, 1]
+    counts[17] = 21
+    assert counts.sum() / counts.size < 2.0
+    fb = GpuFrameBuffer(512, 256, 64, mode)
+    imgs = []
+    for f in range(3):
+        sc = scenes.random_scene(512, 256, 64, counts, seed=90 + f, alpha_max=0.4)
+        fb.begin(accumulate=f > 0)
+        fb.submit_pool(sc.tile_ids, sc.keys, sc.rgba, sc.depth)
+        fb.end()
+        imgs.append(oracle_frame(sc, mode))
+        check_color(fb.color(), imgs[-1], mode)
+    assert np.max(np.abs(fb.accum() - o.accumulate(imgs))) <= TOL
+    px, _ = fb.variance()
+    assert np.max(np.abs(px - o.variance(imgs))) <= 1e-6
+
+
 def test_empty_frame_shows_background():
     sc = scenes.random_scene(64, 64, 16, np.zeros(16, int), seed=1)
     for mode in MODES:
@@ -245,10 +268,15 @@ def test_accumulate_reset_and_single_frame_variance():
         assert np.max(np.abs(got8 - o.unpack_rgba8(o.pack_rgba8(want)))) <= 1
 
 
-def test_kahan_compensated_sum():
+@pytest.mark.parametrize("grid", [(1, 1, 1), (2, 2, 2)])
+def test_kahan_compensated_sum(grid):
     """Past the threshold the running sum is compensated; results stay within
-    tolerance of the exact mean (threshold lowered to 2 to exercise it)."""
-    sc = scenes.scene_data_parallel(128, 128, 32, (2, 2, 2), seed=8, jitter_sigma=0.05)
+    tolerance of the exact mean (threshold lowered to 2 to exercise it).  One
+    brick gives one fragment per tile, whose frames stream the accumulation
+    state through the composite's ring; eight bricks give 3.4 per tile, whose
+    frames have the consumers load it: both paths, with the compensation."""
+    sc = scenes.scene_data_parallel(128, 128, 32, grid, seed=8, jitter_sigma=0.05)
+    assert (sc.n / 16 >= 2.0) == (grid == (2, 2, 2))
     nf = 7
     fb = GpuFrameBuffer(sc.W, sc.H, sc.T, D.DFB_BLEND_ORDERED, kahan_after=2)
     imgs = []
