@@ -461,7 +461,9 @@ DFB_API int dfb_graph_destroy(dfb_graph g);
    CTA in KB (how many work items are in flight), persistent CTAs per SM, and
    consumer groups per CTA (work items composited at once by one CTA).  The
    shapes built are (groups, CTAs per SM) = (1, 2), (2, 2), (1, 3), (2, 1)
-   and (3, 1).  0, 0, 0 restores the library default.  A ring larger
+   and (3, 1).  0, 0, 0 restores the library default, chosen per launch:
+   2 CTAs per SM with one group for FP32 and for frames of 5 or more
+   fragment tiles per image tile, else 3 CTAs per SM.  A ring larger
    than the CTAs can share is clamped at launch; one too small for the
    largest work item of the dtype makes the launch fail with DFB_ERR_CUDA.
    Errors: INVALID_ARG (a shape not in the list). */
