@@ -262,7 +262,14 @@ def gather_tiles(local, own: TileOwnership, group=None, dst=0):
         by_tile.index_copy_(0, idx, parts[r][:len(own.owned[r])])
     frame = by_tile.reshape(own.tiles_y, own.tiles_x, T, T, C).permute(0, 2, 1, 3, 4)
     frame = frame.reshape(own.tiles_y * T, own.tiles_x * T, C)[:own.H, :own.W]
-    out = frame.contiguous().cpu().numpy()
+    if frame.is_cuda:
+        # into pinned host memory (torch caches the block across calls): the
+        # read-back runs at the host link's speed, not a pageable copy's
+        host = torch.empty(frame.shape, dtype=frame.dtype, pin_memory=True)
+        host.copy_(frame)
+        out = host.numpy()
+    else:
+        out = frame.contiguous().numpy()
     return out[..., 0] if flat else out
 
 
