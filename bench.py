@@ -901,11 +901,9 @@ def main():
         e_steps = max(1, min(args.steps, 4))
         h2d = N_FRAMES * (host_frames[0].numel() * 4 + host_depth.numel() * 4)
         # Each host-pointer mode runs five rounds in a row on one handle and
-        # reports its median round. The first round after the other mode's
-        # handle was busy runs at half the host link's speed (70 ms against
-        # 36 ms per step, in either mode) and the next ones at full speed,
-        # as a caller that keeps one mode sees; the median leaves that
-        # transient out.
+        # reports its median round: the host link's speed varies from round
+        # to round on a shared box (rounds of 35.7 ms and of 70-85 ms per
+        # step were seen to alternate, in either mode).
         e_rounds = 5
         e2e_ms = {"borrowed": [], "host": []}
         for where in ("borrowed", "host"):

@@ -765,7 +765,7 @@ __device__ __forceinline__ bool multi_fill(int total, const PixWork& w, int t, i
 
 // Consumer group: one pixel per thread.  Its items' fills come from its own
 // slots, in order.
-template <int DT, int G, int FR>
+template <int DT, int G, int PER, int FR>
 __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __restrict__ itemBase,
                          int nFrames, int totalItems, const LaunchCtl& ctl, unsigned char* ring,
                          ItemMeta* metas, uint64_t* fullB, uint64_t* emptyB, volatile int* abort,
@@ -775,25 +775,56 @@ __device__ void consumer(const FrameArgs* __restrict__ frames, const int* __rest
   const int t = threadIdx.x - group * kP;  // pixel of the item, 0 .. kP-1
   const int lane = t & 31, warp = t >> 5;
   int jg = 0;  // this group's fills taken
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  // The pixel's accumulation state comes with the item's last fill, or, in
+  // frames that do not stream it, is loaded by the consumer itself
+  // (tile-major: each warp reads 512 contiguous bytes per buffer) at the
+  // item's start, before the wait for its fragments.  For the narrow
+  // storage formats in single-frame launches of 2 CTAs per SM with one
+  // group, the loads are issued one item ahead -- while the group waits
+  // for, blends and finishes the item before -- so that their latency is
+  // hidden (FP16 at 5.5 fragments per tile: 0.1029 against 0.1058 ms).
+  // Elsewhere that costs more than it hides: FP32 gains nothing, the
+  // multi-frame launches pay a second frame search per item (batched graph
+  // 1.99 against 1.74 ms), 3 CTAs per SM lose registers, and several groups
+  // per CTA would spill.
+  constexpr bool ahead = G == 1 && PER == 2 && FR == kOneFrame && DT != DFB_F32;
+  auto load_state = [&](int it, float4& s0, float4& m2, float4& cp) {
+    s0 = m2 = cp = zero4;
+    if (it >= totalItems) return;
+    const PixWork v = prepare<FR>(frames, itemBase, nFrames, it, t);
+    const FrameArgs* B = v.A;
+    if (v.active && (B->flags & DFB_FLAG_ACCUMULATE) && B->frameN != 1 && !B->stateInRing &&
+        DFB_CHECK(v.sidx < (size_t)B->nTiles * B->T * B->T, ctl.err)) {
+      s0 = B->accum[v.sidx];
+      m2 = B->m2[v.sidx];
+      if (B->kahan && !B->kahanFirst) cp = B->comp[v.sidx];
+    }
+  };
+  float4 nS0, nM, nCP;  // the next item's state (loads one item ahead)
+  if constexpr (ahead) load_state(blockIdx.x, nS0, nM, nCP);
   for (int k = group; ; k += G) {
     const int item = blockIdx.x + k * (int)gridDim.x;
     if (item >= totalItems) break;
     const PixWork w = prepare<FR>(frames, itemBase, nFrames, item, t);
     const FrameArgs* A = w.A;
-    // The pixel's accumulation state comes with the item's last fill, or,
-    // in frames that do not stream it, is loaded here (tile-major: each warp
-    // reads 512 contiguous bytes per buffer) before the wait for the fill,
-    // so that it arrives while the fragments do.
     const bool accRead = w.active && (A->flags & DFB_FLAG_ACCUMULATE) && A->frameN != 1 &&
                          DFB_CHECK(w.sidx < (size_t)A->nTiles * A->T * A->T, ctl.err);
     const uint32_t stateRows =
         accRead && A->stateInRing ? ((A->kahan && !A->kahanFirst) ? 3u : 2u) : 0u;
-    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 S0 = zero4, M = zero4, CP = zero4;
-    if (accRead && !A->stateInRing) {
-      S0 = A->accum[w.sidx];
-      M = A->m2[w.sidx];
-      if (A->kahan && !A->kahanFirst) CP = A->comp[w.sidx];
+    float4 S0, M, CP;
+    if constexpr (ahead) {
+      S0 = nS0;
+      M = nM;
+      CP = nCP;
+      load_state(item + (int)gridDim.x, nS0, nM, nCP);
+    } else {
+      S0 = M = CP = zero4;
+      if (accRead && !A->stateInRing) {
+        S0 = A->accum[w.sidx];
+        M = A->m2[w.sidx];
+        if (A->kahan && !A->kahanFirst) CP = A->comp[w.sidx];
+      }
     }
     int s = group * S + jg % S;
     if (!wait_phase(&fullB[s], (uint32_t)(jg / S) & 1u, ctl, abort)) {
@@ -909,7 +940,7 @@ __global__ void __launch_bounds__(Shape<G>::threads, PER)
     producer<DT, G, FR>(frames, itemBase, nFrames, totalItems, ctl, ring, ringBytes, metas, queue, qLoc,
                  fullB, emptyB, queueB, abort);
   else
-    consumer<DT, G, FR>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
+    consumer<DT, G, PER, FR>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
                     tb, ringBytes);
 }
 
