@@ -665,9 +665,10 @@ __device__ __forceinline__ void finish_pixel(const FrameArgs* A, const PixWork& 
 
 // A multi-fill item's fills, for one blend mode: the consumer group takes
 // them from its slots in order (jg counts its fills) and carries the
-// per-pixel blend across them.  BLEND_DEPTH blends speculatively in list order; `exact` turns false
-// for a pixel whose finite depths are out of list order or that has a
-// non-zero empty fragment.  Returns false when a wait ran out.
+// per-pixel blend across them; streamed state rows come with the last fill.
+// BLEND_DEPTH blends speculatively in list order; `exact` turns false for a
+// pixel whose finite depths are out of list order or that has a non-zero
+// empty fragment.  Returns false when a wait ran out.
 template <int DT, int MODE, int G>
 __device__ __forceinline__ bool multi_fill(int total, const PixWork& w, int t, int lane,
                                            const LaunchCtl& ctl, unsigned char* ring,
@@ -940,8 +941,8 @@ __global__ void __launch_bounds__(Shape<G>::threads, PER)
     producer<DT, G, FR>(frames, itemBase, nFrames, totalItems, ctl, ring, ringBytes, metas, queue, qLoc,
                  fullB, emptyB, queueB, abort);
   else
-    consumer<DT, G, PER, FR>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB, emptyB, abort,
-                    tb, ringBytes);
+    consumer<DT, G, PER, FR>(frames, itemBase, nFrames, totalItems, ctl, ring, metas, fullB,
+                             emptyB, abort, tb, ringBytes);
 }
 
 // Exact re-do of the 32-pixel units (work item, warp) that the persistent
