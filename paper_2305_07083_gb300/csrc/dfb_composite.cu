@@ -1072,7 +1072,8 @@ cudaError_t launch_shape(const FrameArgs* frames, const int* itemBase, int nFram
       sms[dev] = 0;
       return e;
     }
-    // per CTA: what `per` CTAs can share, less the 1 KB the driver reserves per CTA
+    // per CTA: what `per` CTAs can share, less the 1 KB of shared memory CUDA
+    // reserves for each CTA
     const int share = perSm / per - 1024;
     smemMax[dev] = share < optin ? share : optin;
   }
