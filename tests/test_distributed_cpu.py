@@ -162,3 +162,40 @@ def test_exchange_and_gather_equal_the_single_process_frame(world, scheme, mode)
     errs = [v for k, v in got if k == "frame"]
     assert len(errs) == 1 and errs[0] == 0.0      # same oracle arithmetic on the same lists
     assert sorted(v for k, v in got if k == "ok") == list(range(world))
+
+
+def _empty_rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        own = DD.TileOwnership(W, H, T, world)
+        full = rank_fragments(0, own.n_tiles, 5)
+        if rank == 0:
+            sc = full
+        else:                                   # this rank rendered nothing this frame
+            sc = scenes.Scene(W, H, T, full.tile_ids[:0], full.keys[:0], full.rgba[:0],
+                              full.depth[:0])
+        pend = DD.exchange_async(sc.tile_ids, sc.keys, torch.from_numpy(sc.rgba),
+                                 torch.from_numpy(sc.depth), own).wait()
+        mine = np.nonzero(own.owner[full.tile_ids] == rank)[0]
+        np.testing.assert_array_equal(pend.tile_ids, full.tile_ids[mine])
+        np.testing.assert_array_equal(pend.rgba.numpy(), full.rgba[mine])
+        assert pend.depth.shape == (len(mine),) + full.depth.shape[1:]
+        q.put(("ok", rank))
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_exchange_with_a_rank_that_sends_nothing():
+    world, port = 2, 29871
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_empty_rank_main, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=180) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert sorted(v for _, v in got) == [0, 1]
